@@ -1,0 +1,193 @@
+"""Pins of the oracle's mesh, nodal-force, regularisation and shape-observable
+parts.  CPU only."""
+import numpy as np
+import pytest
+
+import oracle as O
+
+
+@pytest.mark.parametrize("level", [0, 1, 2, 3, 4])
+def test_icosphere_topology(level):
+    r, t = O.icosphere(level, 2.5, (1.0, -2.0, 3.0))
+    nv, nt = r.shape[0], t.shape[0]
+    assert nv == 10 * 4 ** level + 2 and nt == 20 * 4 ** level
+    # closed orientable 2-manifold: each directed edge once, its reverse once
+    de = {(int(a), int(b)) for tri in t for a, b in ((tri[0], tri[1]), (tri[1], tri[2]), (tri[2], tri[0]))}
+    assert len(de) == 3 * nt
+    assert all((b, a) in de for (a, b) in de)
+    ne = len(de) // 2
+    assert nv - ne + nt == 2
+    assert np.allclose(np.linalg.norm(r - [1.0, -2.0, 3.0], axis=1), 2.5, atol=1e-14)
+    # counter-clockwise seen from outside
+    n = np.cross(r[t[:, 1]] - r[t[:, 0]], r[t[:, 2]] - r[t[:, 0]])
+    assert (np.einsum("ij,ij->i", n, r[t].mean(1) - [1.0, -2.0, 3.0]) > 0).all()
+    ptr, idx = O.one_ring(t, nv)
+    val = np.diff(ptr)
+    assert (val == 5).sum() == 12 and ((val == 5) | (val == 6)).all()
+    for i in range(nv):
+        for j in idx[ptr[i]:ptr[i + 1]]:
+            assert i in idx[ptr[j]:ptr[j + 1]]
+
+
+def _area(r, t):
+    return 0.5 * np.linalg.norm(np.cross(r[t[:, 1]] - r[t[:, 0]], r[t[:, 2]] - r[t[:, 0]]), axis=1).sum()
+
+
+def _jittered(level=2, R=4.0, amp=0.15, seed=0):
+    rng = np.random.default_rng(seed)
+    r, t = O.icosphere(level, R, (10.0, 11.0, 12.0))
+    r = r + amp * rng.standard_normal(r.shape)
+    return r, t
+
+
+def test_nodal_forces_are_minus_sigma_area_gradient():
+    """Eq. (pi_drop): for Pi = sigma I_2 the nodal force is -sigma dA/dx_i,
+    checked against central finite differences of the area (brute force)."""
+    r, t = _jittered(level=1)
+    sigma = 0.37
+    F = O.nodal_forces(r, t, sigma)
+    h = 1e-6
+    G = np.zeros_like(r)
+    for i in range(r.shape[0]):
+        for a in range(3):
+            rp = r.copy()
+            rm = r.copy()
+            rp[i, a] += h
+            rm[i, a] -= h
+            G[i, a] = (_area(rp, t) - _area(rm, t)) / (2 * h)
+    assert np.allclose(F, -sigma * G, rtol=0, atol=1e-8)
+
+
+def test_nodal_force_invariants():
+    """On a closed mesh: sum F = 0, sum x x F = 0 and sum x.F = -2 sigma A
+    (A is homogeneous of degree 2: Euler's theorem)."""
+    r, t = _jittered(level=3, seed=4)
+    sigma = 0.05
+    F = O.nodal_forces(r, t, sigma)
+    A = _area(r, t)
+    scale = sigma * A
+    assert np.abs(F.sum(0)).max() < 1e-13 * scale
+    assert np.abs(np.cross(r, F).sum(0)).max() < 1e-12 * scale * 10
+    assert abs((r * F).sum() + 2 * sigma * A) < 1e-12 * scale
+
+
+def _tetra_recurrence(s, alpha, gamma, plus):
+    """One iteration of Sec. 3.3 on a regular tetrahedron centred at 0, where
+    every node stays a multiple s of its start: the neighbour sum of node i is
+    -x_i, so each step is a scalar map (derived by hand, not by the oracle)."""
+    p = alpha - (1 - alpha) * s / 3
+    b = p - alpha - (1 - alpha) * s
+    k = (gamma - (1 - gamma) / 3) if plus else (gamma + (1 - gamma) / 3)
+    return p - k * b
+
+
+@pytest.mark.parametrize("plus", [True, False])
+def test_regularization_tetrahedron_closed_form(plus, golden):
+    reg = golden["regularization"]["value"]
+    alpha, gamma, tol = reg["alpha"], reg["gamma"], reg["tol"]
+    x0 = 3.0 * np.array([[1, 1, 1], [1, -1, -1], [-1, 1, -1], [-1, -1, 1]], dtype=float) / np.sqrt(3)
+    t = np.array([[0, 1, 2], [0, 2, 3], [0, 3, 1], [1, 3, 2]], dtype=np.int32)
+    ptr, idx = O.one_ring(t, 4)
+    x, it, conv = O.regularize(x0, ptr, idx, alpha, gamma, tol, 100, plus)
+    s, n = 1.0, 0
+    while True:
+        n += 1
+        s_new = _tetra_recurrence(s, alpha, gamma, plus)
+        done = abs(s_new - s) * 3.0 < tol
+        s = s_new
+        if done:
+            break
+    assert conv and it == n
+    assert np.allclose(x, s * x0, atol=1e-14)
+
+
+def test_regularization_properties(golden):
+    """Sec. 3.3 on a stretched, jittered level-3 icosphere: the exit test holds
+    (one more iteration from the result moves every node by < tol in the
+    first pass), the motion is translation/rotation equivariant, and the
+    volume-preserving reading of Eq. (HC_algo_full) keeps the volume within
+    0.5% while the sign as printed loses far more."""
+    reg = golden["regularization"]["value"]
+    rng = np.random.default_rng(2)
+    r, t = O.icosphere(3, 5.0)
+    r = r * [1.6, 0.8, 0.8] + 0.2 * rng.standard_normal(r.shape)
+    ptr, idx = O.one_ring(t, r.shape[0])
+    x, it, conv = O.regularize(r, ptr, idx, reg["alpha"], reg["gamma"], reg["tol"], 100, True)
+    assert conv and 1 < it < 100
+    V0 = O.observables(r, t)["V"]
+    V1 = O.observables(x, t)["V"]
+    assert abs(V1 / V0 - 1) < 5e-3
+    xp, _, _ = O.regularize(r, ptr, idx, reg["alpha"], reg["gamma"], reg["tol"], 100, False)
+    Vp = O.observables(xp, t)["V"]
+    assert abs(Vp / V0 - 1) > 5 * abs(V1 / V0 - 1)
+    # equivariance
+    Qm, _ = np.linalg.qr(rng.standard_normal((3, 3)))
+    shift = np.array([3.0, -1.0, 7.0])
+    y, it2, _ = O.regularize(r @ Qm.T + shift, ptr, idx, reg["alpha"], reg["gamma"], reg["tol"], 100,
+                             True)
+    assert it2 == it
+    assert np.allclose(y, x @ Qm.T + shift, atol=1e-11)
+
+
+def _box(a, b, c):
+    v = np.array([[x, y, z] for z in (0, c) for y in (0, b) for x in (0, a)], dtype=float)
+    quads = [(0, 2, 3, 1), (4, 5, 7, 6), (0, 1, 5, 4), (2, 6, 7, 3), (0, 4, 6, 2), (1, 3, 7, 5)]
+    tris = []
+    for q in quads:
+        tris += [(q[0], q[1], q[2]), (q[0], q[2], q[3])]
+    t = np.array(tris, dtype=np.int32)
+    n = np.cross(v[t[:, 1]] - v[t[:, 0]], v[t[:, 2]] - v[t[:, 0]])
+    assert (np.einsum("ij,ij->i", n, v[t].mean(1) - [a / 2, b / 2, c / 2]) > 0).all()
+    return v, t
+
+
+def test_shape_tensor_rotated_box():
+    """S = (5/V) int (x - x_c)(x - x_c)^T dV is exact for a polyhedron: for an
+    a x b x c box it is (5/12) Q diag(a^2, b^2, c^2) Q^T after a rotation Q."""
+    a, b, c = 2.0, 3.0, 5.0
+    v, t = _box(a, b, c)
+    rng = np.random.default_rng(9)
+    Qm, _ = np.linalg.qr(rng.standard_normal((3, 3)))
+    if np.linalg.det(Qm) < 0:
+        Qm[:, 0] *= -1
+    shift = np.array([4.0, 5.0, 6.0])
+    w = (v - [a / 2, b / 2, c / 2]) @ Qm.T + shift
+    ob = O.observables(w, t)
+    assert abs(ob["V"] - a * b * c) < 1e-12
+    assert abs(ob["area"] - 2 * (a * b + b * c + c * a)) < 1e-12
+    assert np.allclose(ob["xc"], shift, atol=1e-13)
+    assert np.allclose(ob["S"], 5 / 12 * Qm @ np.diag([a * a, b * b, c * c]) @ Qm.T, atol=1e-12)
+    assert np.allclose(ob["lam"], 5 / 12 * np.array([a * a, b * b, c * c]), atol=1e-12)
+    assert abs(abs(ob["vmax"] @ Qm[:, 2]) - 1) < 1e-12
+
+
+def test_shape_tensor_ellipsoid_convergence():
+    """Sec. 2: for an ellipsoid sqrt(lambda_max) is the major semi-axis; a
+    stretched icosphere converges to eig(S) = {a^2, b^2, c^2} with level."""
+    ax = np.array([3.0, 5.0, 7.0])
+    errs = []
+    for level in (2, 3, 4):
+        r, t = O.icosphere(level, 1.0)
+        ob = O.observables(r * ax, t)
+        errs.append(np.abs(ob["lam"] / ax ** 2 - 1).max())
+        assert abs(abs(ob["vmax"][2]) - 1) < 1e-9
+    assert errs[2] < 0.01 and errs[1] < errs[0] and errs[2] < errs[1] / 3
+
+
+def test_beta_steady_shear(golden):
+    """Eq. (beta): in simple shear beta = +1/sqrt(2) for a droplet elongated
+    along the extensional axis and -1/sqrt(2) along the compressional axis."""
+    A = np.zeros((3, 3))
+    A[0, 2] = 1e-3
+    r, t = O.icosphere(3, 1.0)
+    for axis, sgn in (((1, 0, 1), 1), ((1, 0, -1), -1)):
+        e = np.array(axis, float) / np.sqrt(2)
+        P = np.outer(e, e)
+        x = r + 0.3 * (r @ P)
+        ob = O.observables(x, t, A)
+        assert abs(ob["beta"] - sgn * golden["beta_steady_shear"]["value"]) < 1e-10
+    ob = O.observables(r * [1.2, 1.0, 0.9], t, A)
+    assert abs(ob["D"] - (np.sqrt(ob["lam"][2]) - np.sqrt(ob["lam"][0]))
+               / (np.sqrt(ob["lam"][2]) + np.sqrt(ob["lam"][0]))) < 1e-15
+    assert abs(ob["D"] - (1.2 - 0.9) / (1.2 + 0.9)) < 5e-3
+    assert np.isnan(O.observables(r, t, np.zeros((3, 3)))["beta"])
