@@ -1,0 +1,239 @@
+/*
+ * iblb.h -- C ABI of libiblb, a GB300 (sm_103a) implementation of one time
+ * step of the immersed-boundary lattice Boltzmann (IBLB) droplet method of
+ * Taglienti, Guglietta and Sbragaglia, arXiv:2403.01161:
+ *
+ *   1. surface-tension nodal forces F_i = -sigma dA/dx_i of the triangulated
+ *      droplet (Sec. 3.1, Eq. (pi_drop)), FP64;
+ *   2. spreading onto the lattice with the Peskin 4-point delta
+ *      (Eq. (ibm_force_d)(a));
+ *   3. D3Q19 BGK stream-collide with Guo forcing and half-force momentum
+ *      (Eqs. (LBMEQ), (collision), (equilibriumLB), (density_velocity_LB)),
+ *      with the Zou-He box boundary imposing u = A(t)(l - L/2) on all wet
+ *      boundary nodes (Eqs. (velo_facce_cubo_da_gradiente), (ZH_bulk),
+ *      (ZH_edges), (zh-buried-links-edges), (zh-buried-links-corners));
+ *   4. interpolation of the fluid velocity to the nodes and forward-Euler
+ *      advection (Eq. (ibm_force_d)(b), Eq. (fwd_euler));
+ *   5. optional mesh regularisation (Sec. 3.3) and shape readout (Sec. 2,
+ *      morphological tensor, lambda_max, Eq. (beta)).
+ * Velocity-gradient frames are held a fixed number of steps each (Sec. 3.2).
+ *
+ * Conventions
+ *   - Lattice nodes sit at integer positions 0..n_a-1 per axis; on a Zou-He
+ *     axis the planes 0 and n_a-1 are the wet boundary nodes and the box
+ *     centre used in the wall velocity is (n_a-1)/2.
+ *   - Host arrays are row-major C arrays of double unless stated.  A frame is
+ *     9 doubles, A[3*a+b] = du_a/dx_b in lattice units.
+ *   - Fields are laid out [component][z][y][x] (x fastest).
+ *   - Every call returns an int status: IBL_OK (0) or a negative IBL_E* code;
+ *     ibl_last_error() returns a message for the calling thread's last
+ *     failure.  Kernel launches are asynchronous on the stream bound at
+ *     creation; device-side errors (instability, wall contact,
+ *     regularisation not converged) are sticky bits reported by the next
+ *     synchronising call (ibl_sync, ibl_readout, ibl_copy_*).
+ *   - Ownership: the library never allocates device memory.  Each handle
+ *     lives in a caller-provided device workspace (size from the matching
+ *     *_workspace_size call, 256-byte aligned, owned by the caller, which
+ *     must keep it alive until the handle is destroyed).  Host outputs are
+ *     caller-owned.  Handles are not thread safe.
+ */
+#ifndef IBLB_H
+#define IBLB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define IBL_ABI_VERSION 1
+
+/* status codes */
+#define IBL_OK 0
+#define IBL_EINVAL (-1)    /* invalid argument or state */
+#define IBL_ENOMEM (-2)    /* workspace smaller than required */
+#define IBL_ECUDA (-3)     /* a CUDA runtime call failed */
+#define IBL_EUNSTABLE (-4) /* NaN density or |u| > 0.3 on some node */
+#define IBL_ENOCONV (-5)   /* mesh regularisation reached max_iter */
+#define IBL_EWALL (-6)     /* a droplet node's 4x4x4 stencil reached a wet boundary node */
+
+/* sticky device error bits, as in ibl_observables.err */
+#define IBL_ERRBIT_UNSTABLE 1
+#define IBL_ERRBIT_NOCONV 2
+#define IBL_ERRBIT_WALL 4
+
+enum { IBL_BC_ZOU_HE = 0, IBL_BC_PERIODIC = 1 };
+/* Edge/corner rule with a moving wall: the printed rule of Eq. (ZH_edges)
+ * plus the moving-wall term -2 w_i (c_i.u_w)/c_s^2 (default), or literally
+ * as printed (no velocity term at edges and corners). */
+enum { IBL_EDGE_PAPER_PLUS_WALL = 0, IBL_EDGE_PAPER_LITERAL = 1 };
+/* Population storage: FP32 deviations f_i - w_i, or FP64 deviations. */
+enum { IBL_FP32_DEV = 0, IBL_FP64 = 1 };
+
+typedef struct ibl_lb ibl_lb;
+typedef struct ibl_mesh ibl_mesh;
+
+typedef struct {
+    int version;       /* IBL_ABI_VERSION */
+    int n[3];          /* lattice nodes per axis, each >= 4 */
+    double tau;        /* BGK relaxation time tau_f > 1/2 (nu = (tau - 1/2)/3) */
+    int bc[3];         /* IBL_BC_ZOU_HE or IBL_BC_PERIODIC per axis */
+    int edge_rule;     /* IBL_EDGE_* */
+    int precision;     /* IBL_FP32_DEV or IBL_FP64 */
+    int record_fields; /* nonzero: reserve buffers so that ibl_step_record can
+                          store density, velocity and force of a step */
+} ibl_lb_params;
+
+/* Shape record of the droplet (Sec. 2).  S = (5/V) int (x - x_c)(x - x_c)^T dV
+ * over the enclosed polyhedron; lam ascending; vmax the unit eigenvector of
+ * lam[2]; D = (sqrt(lam2) - sqrt(lam0))/(sqrt(lam2) + sqrt(lam0)); beta =
+ * vmax.E.vmax/|E|_F with E the symmetric part of the frame applied in the
+ * last completed step (NaN when |E| = 0). */
+typedef struct {
+    long long step;    /* steps completed when the record was taken */
+    int frame;         /* frame index used for beta */
+    int reg_iters;     /* iterations of the latest regularisation, 0 if none */
+    int err;           /* IBL_ERRBIT_* at the time of the record */
+    int pad_;
+    double volume, area;
+    double centroid[3];
+    double S[6];       /* xx, yy, zz, xy, xz, yz */
+    double lam[3];
+    double vmax[3];
+    double D, beta;
+} ibl_observables;
+
+/* ---- lattice --------------------------------------------------------- */
+
+/* Device bytes needed by a lattice with these parameters and n_frames frames. */
+int ibl_lb_workspace_size(const ibl_lb_params *p, int n_frames, size_t *bytes);
+
+/* Creates a lattice in `workspace` (device, `bytes` long) bound to `stream`
+ * (a cudaStream_t, NULL for the legacy default stream).  A_frames: host,
+ * n_frames x 9 doubles, frame k is applied in steps k*steps_per_frame ..
+ * (k+1)*steps_per_frame - 1, the last frame held beyond the end (Sec. 3.2
+ * trajectory loop).  The initial state is f = f_eq(rho = 1, u = A_0(x - c))
+ * at every node.  Copies the frames; the host array may be freed after. */
+int ibl_lb_create(const ibl_lb_params *p, const double *A_frames, int n_frames, int steps_per_frame,
+                  void *workspace, size_t bytes, void *stream, ibl_lb **out);
+void ibl_lb_destroy(ibl_lb *lb);
+
+/* Replaces frame k (0 <= k < n_frames) by 9 host doubles; asynchronous
+ * (stream-ordered), so the host array must stay valid until the stream
+ * reaches the copy (ibl_sync). */
+int ibl_set_frame(ibl_lb *lb, int k, const double *A);
+
+/* ---- droplet mesh ---------------------------------------------------- */
+
+/* Node and triangle counts of an icosphere of subdivision level `level`:
+ * 10*4^level + 2 nodes, 20*4^level triangles. */
+int ibl_icosphere_size(int level, int *n_nodes, int *n_tris);
+
+/* Host-only: writes the icosphere used by ibl_mesh_create_icosphere (radius
+ * R, centre `center`, 3 doubles, not NULL) into caller-owned host arrays r
+ * (n_nodes x 3 doubles) and tris (n_tris x 3 int32).  No device work. */
+int ibl_icosphere(int level, double R, const double *center, double *r, int32_t *tris);
+
+/* Device bytes of a closed triangle mesh with these counts. */
+int ibl_mesh_workspace_size(int n_nodes, int n_tris, size_t *bytes);
+
+/* Attaches a droplet to `lb` (one per lattice).  The icosphere variant
+ * builds the structured spherical mesh of Sec. 3.2 (subdivided icosahedron,
+ * midpoints projected on the sphere at every level, triangles
+ * counter-clockwise seen from outside) of radius R centred at `center`
+ * (host, 3 doubles; NULL = box centre).  The generic variant takes host
+ * positions (n_nodes x 3 doubles) and triangles (n_tris x 3 int32, outward
+ * counter-clockwise) of a closed mesh.  sigma: surface tension (lattice
+ * units). */
+int ibl_mesh_create_icosphere(ibl_lb *lb, int level, double R, double sigma, const double *center,
+                              void *workspace, size_t bytes, ibl_mesh **out);
+int ibl_mesh_create(ibl_lb *lb, int n_nodes, const double *r, int n_tris, const int32_t *tris,
+                    double sigma, void *workspace, size_t bytes, ibl_mesh **out);
+void ibl_mesh_destroy(ibl_mesh *m);
+
+/* Mesh regularisation of Sec. 3.3 (extended Laplacian smoothing), applied
+ * after the advection of every `every`-th step (0 = off).  plus_sign = 1
+ * uses x_p <- x_p - (gamma b_i + (1-gamma)/N_i sum_j b_j) (the volume
+ * preserving form), 0 the sign as printed in Eq. (HC_algo_full).  The loop
+ * stops when max_i |x_p - x_q| < tol or after max_iter iterations
+ * (IBL_ERRBIT_NOCONV).  Paper values: alpha 0.1, gamma 0.51, tol 0.01. */
+int ibl_set_regularization(ibl_mesh *m, double alpha, double gamma, double tol, int max_iter,
+                           int every, int plus_sign);
+
+/* Take a shape record every `every` steps (0 = off) into a device ring of
+ * 4096 records, read with ibl_read_series. */
+int ibl_set_readout(ibl_mesh *m, int every);
+
+/* ---- stepping -------------------------------------------------------- */
+
+/* Enqueues n IBLB steps on the bound stream (asynchronous). */
+int ibl_step(ibl_lb *lb, long long n);
+
+/* Enqueues one step that also stores rho, u and F_ext of every node
+ * (needs record_fields); read them with ibl_copy_fields. */
+int ibl_step_record(ibl_lb *lb);
+
+/* Waits for the stream and reports the sticky device error bits as a status. */
+int ibl_sync(ibl_lb *lb);
+
+/* Number of steps enqueued so far. */
+long long ibl_steps_done(const ibl_lb *lb);
+
+/* ---- readout (synchronising) ----------------------------------------- */
+
+/* Computes a shape record of the current mesh now and copies it to *out. */
+int ibl_readout(ibl_mesh *m, ibl_observables *out);
+
+/* Copies up to `max` records of the ring, oldest first; *count = number copied. */
+int ibl_read_series(ibl_mesh *m, ibl_observables *out, int max, int *count);
+
+/* Fields of the last ibl_step_record step: rho (nodes), u and F (3 x nodes),
+ * host, [c][z][y][x]; any pointer may be NULL. */
+int ibl_copy_fields(ibl_lb *lb, double *rho, double *u, double *F);
+
+/* Pre-collision populations f_i(x) of the next step in the library's
+ * velocity order (ibl_velocity_set), host, 19 x nodes doubles, [i][z][y][x],
+ * full values (not deviations); populations a wet boundary node has no
+ * source for are 0. */
+int ibl_copy_populations(ibl_lb *lb, double *f);
+
+/* Node positions (n x 3), nodal forces of the last step (n x 3) and
+ * triangles (m x 3 int32); any pointer may be NULL. */
+int ibl_copy_mesh(ibl_mesh *m, double *r, double *F, int32_t *tris);
+
+/* One-ring neighbour lists as CSR (ptr: n+1 int32, idx: ptr[n] int32,
+ * ascending); either pointer may be NULL; *nnz receives ptr[n]. */
+int ibl_copy_neighbours(ibl_mesh *m, int32_t *ptr, int32_t *idx, int *nnz);
+
+/* Runs the regularisation once now on the current mesh (synchronising);
+ * *iters receives the iteration count. */
+int ibl_regularize_now(ibl_mesh *m, int *iters);
+
+/* The paper's trajectory loop with host buffers (Sec. 3.2, steps 1-4): for
+ * each of n_frames frames, copy the frame (host, 9 doubles) to the device,
+ * run steps_per_frame IBLB steps, and copy the droplet's shape record back
+ * to out[k] (host).  steps_per_frame must equal the lattice's value and
+ * the step count must be a multiple of it. */
+int ibl_run_frames(ibl_lb *lb, ibl_mesh *m, const double *A_frames, int n_frames,
+                   int steps_per_frame, ibl_observables *out);
+
+/* ---- introspection --------------------------------------------------- */
+
+/* The library's D3Q19 velocities (19 x 3 int32) and weights (19 doubles). */
+int ibl_velocity_set(int32_t *c, double *w);
+
+/* Kernel timing with CUDA events on the bound stream: enable (1) records an
+ * event pair around every launch of the lattice kernel and of the IB
+ * kernels; ibl_profile_read synchronises and returns the summed durations
+ * (ms) and launch counts [lattice, spread, interpolate] since enabling.
+ * At most 65536 launches are recorded. */
+int ibl_profile_enable(ibl_lb *lb, int enable);
+int ibl_profile_read(ibl_lb *lb, double ms[3], long long launches[3]);
+
+const char *ibl_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IBLB_H */

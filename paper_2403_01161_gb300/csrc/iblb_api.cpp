@@ -1,0 +1,837 @@
+// iblb_api.cpp -- host side of the libiblb C ABI (include/iblb.h): workspace
+// layout, mesh construction, the step schedule and the synchronising
+// readouts.  All device work is launched through iblb_kernels.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "iblb_internal.h"
+
+using iblb::Ctl;
+using iblb::LbView;
+using iblb::MeshView;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg)
+{
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(IBL_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+struct Layout {
+    size_t ctl = 0, frames = 0, f = 0, force = 0, vel = 0, rec = 0, total = 0;
+};
+
+long long pop_stride(long long nodes) { return (nodes + 63) / 64 * 64; }
+
+bool lb_layout(const ibl_lb_params *p, int n_frames, Layout &L)
+{
+    if (!p || p->version != IBL_ABI_VERSION) return false;
+    for (int a = 0; a < 3; ++a)
+        if (p->n[a] < 4 || (p->bc[a] != IBL_BC_ZOU_HE && p->bc[a] != IBL_BC_PERIODIC)) return false;
+    if (p->precision != IBL_FP32_DEV && p->precision != IBL_FP64) return false;
+    if (n_frames < 1) return false;
+    const long long nodes = (long long)p->n[0] * p->n[1] * p->n[2];
+    if (nodes > 0x7fffffffLL / 8) return false;
+    const size_t es = p->precision == IBL_FP64 ? 8 : 4;
+    size_t off = 0;
+    auto take = [&](size_t b) {
+        const size_t o = off;
+        off = align256(off + b);
+        return o;
+    };
+    L.ctl = take(sizeof(Ctl));
+    L.frames = take(sizeof(double) * 9 * (size_t)n_frames);
+    L.f = take(es * 19 * (size_t)pop_stride(nodes));
+    L.force = take(es * 3 * (size_t)nodes);
+    L.vel = take(es * 3 * (size_t)nodes);
+    L.rec = p->record_fields ? take(es * 7 * (size_t)nodes) : 0;
+    L.total = off;
+    return true;
+}
+
+struct MeshLayout {
+    size_t r = 0, fn = 0, tris = 0, n2t_ptr = 0, n2t = 0, nb_ptr = 0, nb_idx = 0, s0 = 0, s1 = 0, s2 = 0,
+           ring = 0, total = 0;
+};
+
+bool mesh_layout(int nv, int nt, MeshLayout &L)
+{
+    if (nv < 4 || nt < 4 || nv > (1 << 26) || nt > (1 << 26)) return false;
+    size_t off = 0;
+    auto take = [&](size_t b) {
+        const size_t o = off;
+        off = align256(off + b);
+        return o;
+    };
+    L.r = take(sizeof(double) * 3 * nv);
+    L.fn = take(sizeof(double) * 3 * nv);
+    L.tris = take(sizeof(int) * 3 * nt);
+    L.n2t_ptr = take(sizeof(int) * (nv + 1));
+    L.n2t = take(sizeof(int) * 3 * nt);
+    L.nb_ptr = take(sizeof(int) * (nv + 1));
+    L.nb_idx = take(sizeof(int) * 3 * nt);
+    L.s0 = take(sizeof(double) * 3 * nv);
+    L.s1 = take(sizeof(double) * 3 * nv);
+    L.s2 = take(sizeof(double) * 3 * nv);
+    L.ring = take(sizeof(ibl_observables) * iblb::kRingCap);
+    L.total = off;
+    return true;
+}
+
+enum { PROF_LB = 0, PROF_SPREAD = 1, PROF_INTERP = 2 };
+
+struct Profiler {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    std::vector<std::pair<int, int>> marks;  // (kind, first event index)
+    size_t used = 0;
+    static constexpr size_t kMax = 65536;
+
+    cudaEvent_t take()
+    {
+        if (used == pool.size()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+            pool.push_back(e);
+        }
+        return pool[used++];
+    }
+    void clear()
+    {
+        used = 0;
+        marks.clear();
+    }
+    ~Profiler()
+    {
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+
+}  // namespace
+
+struct ibl_lb {
+    ibl_lb_params p;
+    LbView v;
+    Layout lay;
+    char *ws = nullptr;
+    cudaStream_t stream = nullptr;
+    long long host_step = 0;
+    bool recorded = false;
+    ibl_mesh *mesh = nullptr;
+    Profiler prof;
+};
+
+struct ibl_mesh {
+    ibl_lb *lb = nullptr;
+    MeshView v;
+    MeshLayout lay;
+    std::vector<int> tris, nb_ptr, nb_idx;
+    iblb::RegParams reg{0.1, 0.51, 0.01, 100, 1};
+    int reg_every = 0;
+    int readout_every = 0;
+};
+
+namespace {
+
+int lb_status_from_device(ibl_lb *lb)
+{
+    Ctl c;
+    cudaError_t e = cudaMemcpyAsync(&c, lb->ws + lb->lay.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, lb->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "read control block");
+    e = cudaStreamSynchronize(lb->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    if (c.err & IBL_ERRBIT_UNSTABLE) return fail(IBL_EUNSTABLE, "NaN density or |u| > 0.3 on some lattice node");
+    if (c.err & IBL_ERRBIT_WALL)
+        return fail(IBL_EWALL, "a droplet node's stencil reached a wet boundary node (or its position is invalid)");
+    if (c.err & IBL_ERRBIT_NOCONV) return fail(IBL_ENOCONV, "mesh regularisation did not converge within max_iter");
+    return IBL_OK;
+}
+
+void prof_begin(ibl_lb *lb, int kind)
+{
+    if (!lb->prof.on || lb->prof.marks.size() >= Profiler::kMax) return;
+    cudaEvent_t a = lb->prof.take();
+    cudaEvent_t b = lb->prof.take();
+    if (!a || !b) return;
+    lb->prof.marks.push_back({kind, (int)lb->prof.used - 2});
+    cudaEventRecord(a, lb->stream);
+}
+
+void prof_end(ibl_lb *lb)
+{
+    if (!lb->prof.on || lb->prof.marks.empty()) return;
+    const int idx = lb->prof.marks.back().second;
+    if ((size_t)idx + 2 != lb->prof.used) return;  // begin was skipped
+    cudaEventRecord(lb->prof.pool[idx + 1], lb->stream);
+}
+
+int one_step(ibl_lb *lb, bool record)
+{
+    cudaError_t e;
+    ibl_mesh *m = lb->mesh;
+    const bool odd = (lb->host_step & 1) != 0;
+    if (m) {
+        prof_begin(lb, PROF_SPREAD);
+        e = iblb::launch_spread(lb->v, m->v, lb->stream);
+        prof_end(lb);
+        if (e != cudaSuccess) return cuda_fail(e, "spread launch");
+    }
+    prof_begin(lb, PROF_LB);
+    e = iblb::launch_lattice(lb->v, odd, record, lb->stream);
+    prof_end(lb);
+    if (e != cudaSuccess) return cuda_fail(e, "lattice launch");
+    const long long next = lb->host_step + 1;
+    if (m) {
+        prof_begin(lb, PROF_INTERP);
+        e = iblb::launch_interp(lb->v, m->v, lb->stream);
+        prof_end(lb);
+        if (e != cudaSuccess) return cuda_fail(e, "interpolation launch");
+        if (m->reg_every > 0 && next % m->reg_every == 0) {
+            e = iblb::launch_regularize(lb->v, m->v, m->reg, lb->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "regularisation launch");
+        }
+        if (m->readout_every > 0 && next % m->readout_every == 0) {
+            e = iblb::launch_observables(lb->v, m->v, lb->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "observables launch");
+        }
+    }
+    lb->host_step = next;
+    return IBL_OK;
+}
+
+// ---- mesh construction (library's own implementation) ---------------------
+void unit(double v[3])
+{
+    const double n = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    v[0] /= n;
+    v[1] /= n;
+    v[2] /= n;
+}
+
+// Subdivided icosahedron: base vertices (+-1, +-p, 0) cyclically in the
+// order below, base faces = mutually adjacent triples sorted ascending and
+// oriented outward; each level splits every face into four through the edge
+// midpoints (created on first use, projected to the unit sphere).
+void icosphere(int level, std::vector<double> &xyz, std::vector<int> &tri)
+{
+    const double p = (1.0 + std::sqrt(5.0)) / 2.0;
+    const double raw[12][3] = {{-1, p, 0}, {1, p, 0}, {-1, -p, 0}, {1, -p, 0}, {0, -1, p}, {0, 1, p},
+                               {0, -1, -p}, {0, 1, -p}, {p, 0, -1}, {p, 0, 1}, {-p, 0, -1}, {-p, 0, 1}};
+    auto dist = [&](int a, int b) {
+        double s = 0;
+        for (int k = 0; k < 3; ++k) s += (raw[a][k] - raw[b][k]) * (raw[a][k] - raw[b][k]);
+        return std::sqrt(s);
+    };
+    tri.clear();
+    for (int a = 0; a < 12; ++a)
+        for (int b = a + 1; b < 12; ++b)
+            for (int c = b + 1; c < 12; ++c) {
+                if (std::fabs(dist(a, b) - 2) > 1e-9 || std::fabs(dist(b, c) - 2) > 1e-9 ||
+                    std::fabs(dist(c, a) - 2) > 1e-9)
+                    continue;
+                double e1[3], e2[3], n[3];
+                for (int k = 0; k < 3; ++k) {
+                    e1[k] = raw[b][k] - raw[a][k];
+                    e2[k] = raw[c][k] - raw[a][k];
+                }
+                n[0] = e1[1] * e2[2] - e1[2] * e2[1];
+                n[1] = e1[2] * e2[0] - e1[0] * e2[2];
+                n[2] = e1[0] * e2[1] - e1[1] * e2[0];
+                const double out = n[0] * (raw[a][0] + raw[b][0] + raw[c][0]) +
+                                   n[1] * (raw[a][1] + raw[b][1] + raw[c][1]) +
+                                   n[2] * (raw[a][2] + raw[b][2] + raw[c][2]);
+                if (out > 0) tri.insert(tri.end(), {a, b, c});
+                else tri.insert(tri.end(), {a, c, b});
+            }
+    xyz.clear();
+    for (int i = 0; i < 12; ++i) {
+        double v[3] = {raw[i][0], raw[i][1], raw[i][2]};
+        unit(v);
+        xyz.insert(xyz.end(), {v[0], v[1], v[2]});
+    }
+    for (int l = 0; l < level; ++l) {
+        std::map<std::pair<int, int>, int> mid;
+        std::vector<int> nt;
+        nt.reserve(tri.size() * 4);
+        auto midpoint = [&](int i, int j) {
+            const auto key = std::make_pair(std::min(i, j), std::max(i, j));
+            auto it = mid.find(key);
+            if (it != mid.end()) return it->second;
+            const int id = (int)(xyz.size() / 3);
+            double v[3] = {(xyz[3 * i] + xyz[3 * j]) * 0.5, (xyz[3 * i + 1] + xyz[3 * j + 1]) * 0.5,
+                           (xyz[3 * i + 2] + xyz[3 * j + 2]) * 0.5};
+            unit(v);
+            xyz.insert(xyz.end(), {v[0], v[1], v[2]});
+            mid[key] = id;
+            return id;
+        };
+        for (size_t t = 0; t < tri.size(); t += 3) {
+            const int a = tri[t], b = tri[t + 1], c = tri[t + 2];
+            const int mab = midpoint(a, b);
+            const int mbc = midpoint(b, c);
+            const int mca = midpoint(c, a);
+            nt.insert(nt.end(), {a, mab, mca, b, mbc, mab, c, mca, mbc, mab, mbc, mca});
+        }
+        tri.swap(nt);
+    }
+}
+
+// Closed, consistently oriented 2-manifold: every directed edge once and its
+// reverse once.  Builds one-ring neighbour CSR (ascending) and node-to-
+// triangle CSR (entries 3*t + slot, in triangle order).
+bool build_topology(int nv, const std::vector<int> &tri, std::vector<int> &nb_ptr, std::vector<int> &nb_idx,
+                    std::vector<int> &n2t_ptr, std::vector<int> &n2t, std::string &why)
+{
+    const int nt = (int)(tri.size() / 3);
+    std::vector<std::pair<int, int>> de;
+    de.reserve(3 * nt);
+    for (int t = 0; t < nt; ++t)
+        for (int k = 0; k < 3; ++k) {
+            const int a = tri[3 * t + k], b = tri[3 * t + (k + 1) % 3];
+            if (a < 0 || a >= nv || b < 0 || b >= nv || a == b) {
+                why = "triangle index out of range or degenerate";
+                return false;
+            }
+            de.push_back({a, b});
+        }
+    std::vector<std::pair<int, int>> sorted = de;
+    std::sort(sorted.begin(), sorted.end());
+    for (size_t k = 1; k < sorted.size(); ++k)
+        if (sorted[k] == sorted[k - 1]) {
+            why = "directed edge used twice (inconsistent orientation or non-manifold)";
+            return false;
+        }
+    for (auto &e : de)
+        if (!std::binary_search(sorted.begin(), sorted.end(), std::make_pair(e.second, e.first))) {
+            why = "mesh is not closed";
+            return false;
+        }
+    std::vector<std::vector<int>> nb(nv);
+    for (auto &e : de) nb[e.first].push_back(e.second);
+    nb_ptr.assign(nv + 1, 0);
+    nb_idx.clear();
+    for (int i = 0; i < nv; ++i) {
+        std::sort(nb[i].begin(), nb[i].end());
+        if (nb[i].empty()) {
+            why = "node without triangles";
+            return false;
+        }
+        nb_ptr[i + 1] = nb_ptr[i] + (int)nb[i].size();
+        nb_idx.insert(nb_idx.end(), nb[i].begin(), nb[i].end());
+    }
+    std::vector<std::vector<int>> inc(nv);
+    for (int t = 0; t < nt; ++t)
+        for (int k = 0; k < 3; ++k) inc[tri[3 * t + k]].push_back(3 * t + k);
+    n2t_ptr.assign(nv + 1, 0);
+    n2t.clear();
+    for (int i = 0; i < nv; ++i) {
+        n2t_ptr[i + 1] = n2t_ptr[i] + (int)inc[i].size();
+        n2t.insert(n2t.end(), inc[i].begin(), inc[i].end());
+    }
+    return true;
+}
+
+int mesh_attach(ibl_lb *lb, int nv, const double *r, int nt, const int *tri_in, double sigma, void *ws,
+                size_t bytes, ibl_mesh **out)
+{
+    if (!lb || !r || !tri_in || !out) return fail(IBL_EINVAL, "null argument");
+    if (lb->mesh) return fail(IBL_EINVAL, "the lattice already carries a droplet");
+    MeshLayout L;
+    if (!mesh_layout(nv, nt, L)) return fail(IBL_EINVAL, "bad mesh size");
+    if (!ws || bytes < L.total) return fail(IBL_ENOMEM, "mesh workspace too small");
+    if (((uintptr_t)ws & 255) != 0) return fail(IBL_EINVAL, "workspace must be 256-byte aligned");
+    if (!(sigma >= 0) || !std::isfinite(sigma)) return fail(IBL_EINVAL, "sigma must be finite and >= 0");
+    std::vector<int> tri(tri_in, tri_in + 3 * (size_t)nt);
+    std::vector<int> nb_ptr, nb_idx, n2t_ptr, n2t;
+    std::string why;
+    if (!build_topology(nv, tri, nb_ptr, nb_idx, n2t_ptr, n2t, why)) return fail(IBL_EINVAL, "mesh: " + why);
+    if ((int)nb_idx.size() != 3 * nt) return fail(IBL_EINVAL, "mesh: unexpected neighbour count");
+    for (int i = 0; i < 3 * nv; ++i)
+        if (!std::isfinite(r[i])) return fail(IBL_EINVAL, "mesh: non-finite position");
+    ibl_mesh *m = new ibl_mesh();
+    m->lb = lb;
+    m->lay = L;
+    char *w = static_cast<char *>(ws);
+    m->v.nv = nv;
+    m->v.nt = nt;
+    m->v.sigma = sigma;
+    m->v.r = reinterpret_cast<double *>(w + L.r);
+    m->v.fn = reinterpret_cast<double *>(w + L.fn);
+    m->v.tris = reinterpret_cast<const int *>(w + L.tris);
+    m->v.n2t_ptr = reinterpret_cast<const int *>(w + L.n2t_ptr);
+    m->v.n2t = reinterpret_cast<const int *>(w + L.n2t);
+    m->v.nb_ptr = reinterpret_cast<const int *>(w + L.nb_ptr);
+    m->v.nb_idx = reinterpret_cast<const int *>(w + L.nb_idx);
+    m->v.s0 = reinterpret_cast<double *>(w + L.s0);
+    m->v.s1 = reinterpret_cast<double *>(w + L.s1);
+    m->v.s2 = reinterpret_cast<double *>(w + L.s2);
+    m->v.ring = reinterpret_cast<ibl_observables *>(w + L.ring);
+    m->v.ring_cap = iblb::kRingCap;
+    m->tris = tri;
+    m->nb_ptr = nb_ptr;
+    m->nb_idx = nb_idx;
+    cudaStream_t s = lb->stream;
+    cudaError_t e = cudaSuccess;
+    auto up = [&](size_t off, const void *src, size_t n) {
+        if (e == cudaSuccess) e = cudaMemcpyAsync(w + off, src, n, cudaMemcpyHostToDevice, s);
+    };
+    up(L.r, r, sizeof(double) * 3 * nv);
+    up(L.tris, tri.data(), sizeof(int) * 3 * nt);
+    up(L.n2t_ptr, n2t_ptr.data(), sizeof(int) * (nv + 1));
+    up(L.n2t, n2t.data(), sizeof(int) * n2t.size());
+    up(L.nb_ptr, nb_ptr.data(), sizeof(int) * (nv + 1));
+    up(L.nb_idx, nb_idx.data(), sizeof(int) * nb_idx.size());
+    if (e == cudaSuccess) e = cudaMemsetAsync(w + L.fn, 0, sizeof(double) * 3 * nv, s);
+    if (e == cudaSuccess) e = iblb::launch_patch_from_mesh(lb->v, m->v, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host vectors above are pageable temporaries
+    if (e != cudaSuccess) {
+        delete m;
+        return cuda_fail(e, "mesh upload");
+    }
+    lb->mesh = m;
+    *out = m;
+    return IBL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ibl_last_error(void) { return g_err.c_str(); }
+
+int ibl_velocity_set(int32_t *c, double *w)
+{
+    int cc[19][3];
+    double ww[19];
+    iblb::velocity_table(cc, ww);
+    for (int i = 0; i < 19; ++i) {
+        if (c)
+            for (int a = 0; a < 3; ++a) c[3 * i + a] = cc[i][a];
+        if (w) w[i] = ww[i];
+    }
+    return IBL_OK;
+}
+
+int ibl_lb_workspace_size(const ibl_lb_params *p, int n_frames, size_t *bytes)
+{
+    Layout L;
+    if (!bytes) return fail(IBL_EINVAL, "null argument");
+    if (!lb_layout(p, n_frames, L)) return fail(IBL_EINVAL, "invalid lattice parameters");
+    *bytes = L.total;
+    return IBL_OK;
+}
+
+int ibl_lb_create(const ibl_lb_params *p, const double *A_frames, int n_frames, int steps_per_frame, void *workspace,
+                  size_t bytes, void *stream, ibl_lb **out)
+{
+    Layout L;
+    if (!out || !A_frames) return fail(IBL_EINVAL, "null argument");
+    if (!lb_layout(p, n_frames, L)) return fail(IBL_EINVAL, "invalid lattice parameters (version, sizes, bc, precision)");
+    if (!(p->tau > 0.5) || !std::isfinite(p->tau)) return fail(IBL_EINVAL, "tau must be > 1/2");
+    if (p->edge_rule != IBL_EDGE_PAPER_PLUS_WALL && p->edge_rule != IBL_EDGE_PAPER_LITERAL)
+        return fail(IBL_EINVAL, "unknown edge rule");
+    if (steps_per_frame < 1) return fail(IBL_EINVAL, "steps_per_frame must be >= 1");
+    for (int k = 0; k < 9 * n_frames; ++k)
+        if (!std::isfinite(A_frames[k])) return fail(IBL_EINVAL, "non-finite velocity gradient");
+    if (!workspace || bytes < L.total) return fail(IBL_ENOMEM, "lattice workspace too small");
+    if (((uintptr_t)workspace & 255) != 0) return fail(IBL_EINVAL, "workspace must be 256-byte aligned");
+    ibl_lb *lb = new ibl_lb();
+    lb->p = *p;
+    lb->lay = L;
+    lb->ws = static_cast<char *>(workspace);
+    lb->stream = static_cast<cudaStream_t>(stream);
+    const long long nodes = (long long)p->n[0] * p->n[1] * p->n[2];
+    LbView &v = lb->v;
+    for (int a = 0; a < 3; ++a) {
+        v.n[a] = p->n[a];
+        v.bc[a] = p->bc[a];
+    }
+    v.nodes = (int)nodes;
+    v.qs = pop_stride(nodes);
+    v.precision = p->precision;
+    v.rule = p->edge_rule;
+    v.omega = 1.0 / p->tau;
+    v.f = lb->ws + L.f;
+    v.force = lb->ws + L.force;
+    v.vel = lb->ws + L.vel;
+    v.rec = p->record_fields ? lb->ws + L.rec : nullptr;
+    v.frames = reinterpret_cast<const double *>(lb->ws + L.frames);
+    v.n_frames = n_frames;
+    v.n_hold = steps_per_frame;
+    v.ctl = reinterpret_cast<Ctl *>(lb->ws + L.ctl);
+    Ctl c;
+    std::memset(&c, 0, sizeof c);
+    for (int a = 0; a < 4; ++a) {
+        c.patch_lo[a] = 0;
+        c.patch_ext[a] = -1;
+        c.key_min[a] = ~0ull;
+        c.key_max[a] = 0ull;
+    }
+    const size_t es = p->precision == IBL_FP64 ? 8 : 4;
+    cudaError_t e = cudaMemcpyAsync(v.ctl, &c, sizeof c, cudaMemcpyHostToDevice, lb->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(lb->ws + L.frames, A_frames, sizeof(double) * 9 * n_frames, cudaMemcpyHostToDevice,
+                            lb->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v.force, 0, es * 3 * nodes, lb->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v.vel, 0, es * 3 * nodes, lb->stream);
+    if (e == cudaSuccess && v.rec) e = cudaMemsetAsync(v.rec, 0, es * 7 * nodes, lb->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v.f, 0, es * 19 * v.qs, lb->stream);
+    if (e == cudaSuccess) e = iblb::launch_init(v, lb->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(lb->stream);  // the host control block is a temporary
+    if (e != cudaSuccess) {
+        delete lb;
+        return cuda_fail(e, "lattice initialisation");
+    }
+    *out = lb;
+    return IBL_OK;
+}
+
+void ibl_lb_destroy(ibl_lb *lb)
+{
+    if (!lb) return;
+    cudaStreamSynchronize(lb->stream);
+    if (lb->mesh) lb->mesh->lb = nullptr;
+    delete lb;
+}
+
+int ibl_set_frame(ibl_lb *lb, int k, const double *A)
+{
+    if (!lb || !A) return fail(IBL_EINVAL, "null argument");
+    if (k < 0 || k >= lb->v.n_frames) return fail(IBL_EINVAL, "frame index out of range");
+    for (int i = 0; i < 9; ++i)
+        if (!std::isfinite(A[i])) return fail(IBL_EINVAL, "non-finite velocity gradient");
+    cudaError_t e = cudaMemcpyAsync(lb->ws + lb->lay.frames + sizeof(double) * 9 * (size_t)k, A, sizeof(double) * 9,
+                                    cudaMemcpyHostToDevice, lb->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "frame upload");
+    return IBL_OK;
+}
+
+int ibl_icosphere_size(int level, int *n_nodes, int *n_tris)
+{
+    if (level < 0 || level > 9) return fail(IBL_EINVAL, "icosphere level must be in 0..9");
+    long long p = 1;
+    for (int l = 0; l < level; ++l) p *= 4;
+    if (n_nodes) *n_nodes = (int)(10 * p + 2);
+    if (n_tris) *n_tris = (int)(20 * p);
+    return IBL_OK;
+}
+
+int ibl_icosphere(int level, double R, const double *center, double *r, int32_t *tris)
+{
+    if (level < 0 || level > 7 || !center || !r || !tris) return fail(IBL_EINVAL, "bad icosphere request");
+    std::vector<double> xyz;
+    std::vector<int> tri;
+    icosphere(level, xyz, tri);
+    for (size_t i = 0; i < xyz.size() / 3; ++i)
+        for (int a = 0; a < 3; ++a) r[3 * i + a] = xyz[3 * i + a] * R + center[a];
+    for (size_t k = 0; k < tri.size(); ++k) tris[k] = tri[k];
+    return IBL_OK;
+}
+
+int ibl_mesh_workspace_size(int n_nodes, int n_tris, size_t *bytes)
+{
+    MeshLayout L;
+    if (!bytes) return fail(IBL_EINVAL, "null argument");
+    if (!mesh_layout(n_nodes, n_tris, L)) return fail(IBL_EINVAL, "bad mesh size");
+    *bytes = L.total;
+    return IBL_OK;
+}
+
+int ibl_mesh_create_icosphere(ibl_lb *lb, int level, double R, double sigma, const double *center, void *workspace,
+                              size_t bytes, ibl_mesh **out)
+{
+    if (!lb) return fail(IBL_EINVAL, "null lattice");
+    if (level < 0 || level > 7) return fail(IBL_EINVAL, "icosphere level must be in 0..7");
+    if (!(R > 0) || !std::isfinite(R)) return fail(IBL_EINVAL, "radius must be > 0");
+    std::vector<double> xyz;
+    std::vector<int> tri;
+    icosphere(level, xyz, tri);
+    double c[3];
+    for (int a = 0; a < 3; ++a) c[a] = center ? center[a] : 0.5 * (lb->p.n[a] - 1);
+    for (size_t i = 0; i < xyz.size() / 3; ++i)
+        for (int a = 0; a < 3; ++a) xyz[3 * i + a] = xyz[3 * i + a] * R + c[a];
+    return mesh_attach(lb, (int)(xyz.size() / 3), xyz.data(), (int)(tri.size() / 3), tri.data(), sigma, workspace,
+                       bytes, out);
+}
+
+int ibl_mesh_create(ibl_lb *lb, int n_nodes, const double *r, int n_tris, const int32_t *tris, double sigma,
+                    void *workspace, size_t bytes, ibl_mesh **out)
+{
+    return mesh_attach(lb, n_nodes, r, n_tris, reinterpret_cast<const int *>(tris), sigma, workspace, bytes, out);
+}
+
+void ibl_mesh_destroy(ibl_mesh *m)
+{
+    if (!m) return;
+    if (m->lb) {
+        cudaStreamSynchronize(m->lb->stream);
+        m->lb->mesh = nullptr;
+    }
+    delete m;
+}
+
+int ibl_set_regularization(ibl_mesh *m, double alpha, double gamma, double tol, int max_iter, int every, int plus_sign)
+{
+    if (!m) return fail(IBL_EINVAL, "null mesh");
+    if (!(alpha >= 0 && alpha <= 1) || !(gamma >= 0 && gamma <= 1) || !(tol > 0) || max_iter < 1 || every < 0)
+        return fail(IBL_EINVAL, "regularisation parameters out of range");
+    m->reg = iblb::RegParams{alpha, gamma, tol, max_iter, plus_sign ? 1 : 0};
+    m->reg_every = every;
+    return IBL_OK;
+}
+
+int ibl_set_readout(ibl_mesh *m, int every)
+{
+    if (!m || every < 0) return fail(IBL_EINVAL, "bad readout interval");
+    m->readout_every = every;
+    return IBL_OK;
+}
+
+int ibl_step(ibl_lb *lb, long long n)
+{
+    if (!lb || n < 0) return fail(IBL_EINVAL, "bad step request");
+    for (long long k = 0; k < n; ++k) {
+        const int st = one_step(lb, false);
+        if (st != IBL_OK) return st;
+    }
+    return IBL_OK;
+}
+
+int ibl_step_record(ibl_lb *lb)
+{
+    if (!lb) return fail(IBL_EINVAL, "null lattice");
+    if (!lb->v.rec) return fail(IBL_EINVAL, "lattice created without record_fields");
+    const int st = one_step(lb, true);
+    if (st == IBL_OK) lb->recorded = true;
+    return st;
+}
+
+int ibl_sync(ibl_lb *lb)
+{
+    if (!lb) return fail(IBL_EINVAL, "null lattice");
+    return lb_status_from_device(lb);
+}
+
+long long ibl_steps_done(const ibl_lb *lb) { return lb ? lb->host_step : -1; }
+
+int ibl_readout(ibl_mesh *m, ibl_observables *out)
+{
+    if (!m || !m->lb || !out) return fail(IBL_EINVAL, "null argument");
+    ibl_lb *lb = m->lb;
+    cudaError_t e = iblb::launch_observables(lb->v, m->v, lb->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "observables launch");
+    Ctl c;
+    e = cudaMemcpyAsync(&c, lb->v.ctl, sizeof c, cudaMemcpyDeviceToHost, lb->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(lb->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "observables readout");
+    const int slot = (c.n_records - 1) % m->v.ring_cap;
+    e = cudaMemcpyAsync(out, m->v.ring + slot, sizeof(ibl_observables), cudaMemcpyDeviceToHost, lb->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(lb->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "observables copy");
+    return lb_status_from_device(lb);
+}
+
+int ibl_read_series(ibl_mesh *m, ibl_observables *out, int max, int *count)
+{
+    if (!m || !m->lb || !out || !count || max < 0) return fail(IBL_EINVAL, "null argument");
+    ibl_lb *lb = m->lb;
+    Ctl c;
+    cudaError_t e = cudaMemcpyAsync(&c, lb->v.ctl, sizeof c, cudaMemcpyDeviceToHost, lb->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(lb->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "series readout");
+    const int cap = m->v.ring_cap;
+    const int have = std::min(c.n_records, cap);
+    const int first = c.n_records - have;
+    std::vector<ibl_observables> ring(cap);
+    e = cudaMemcpyAsync(ring.data(), m->v.ring, sizeof(ibl_observables) * cap, cudaMemcpyDeviceToHost, lb->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(lb->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "series copy");
+    const int n = std::min(have, max);
+    for (int k = 0; k < n; ++k) out[k] = ring[(first + k) % cap];
+    *count = n;
+    return lb_status_from_device(lb);
+}
+
+int ibl_copy_fields(ibl_lb *lb, double *rho, double *u, double *F)
+{
+    if (!lb) return fail(IBL_EINVAL, "null lattice");
+    if (!lb->v.rec || !lb->recorded) return fail(IBL_EINVAL, "no recorded step (use ibl_step_record)");
+    const size_t nodes = (size_t)lb->v.nodes;
+    const bool dbl = lb->p.precision == IBL_FP64;
+    const size_t es = dbl ? 8 : 4;
+    std::vector<char> h(es * 7 * nodes);
+    cudaError_t e = cudaMemcpyAsync(h.data(), lb->v.rec, h.size(), cudaMemcpyDeviceToHost, lb->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(lb->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "field copy");
+    auto at = [&](size_t k) -> double {
+        return dbl ? reinterpret_cast<const double *>(h.data())[k] : (double)reinterpret_cast<const float *>(h.data())[k];
+    };
+    for (size_t i = 0; i < nodes; ++i) {
+        if (rho) rho[i] = 1.0 + at(i);
+        for (int a = 0; a < 3; ++a) {
+            if (u) u[a * nodes + i] = at((1 + a) * nodes + i);
+            if (F) F[a * nodes + i] = at((4 + a) * nodes + i);
+        }
+    }
+    return lb_status_from_device(lb);
+}
+
+int ibl_copy_populations(ibl_lb *lb, double *f)
+{
+    if (!lb || !f) return fail(IBL_EINVAL, "null argument");
+    const int nx = lb->p.n[0], ny = lb->p.n[1], nz = lb->p.n[2];
+    const size_t nodes = (size_t)lb->v.nodes, qs = (size_t)lb->v.qs;
+    const bool dbl = lb->p.precision == IBL_FP64;
+    const size_t es = dbl ? 8 : 4;
+    std::vector<char> h(es * 19 * qs);
+    cudaError_t e = cudaMemcpyAsync(h.data(), lb->v.f, h.size(), cudaMemcpyDeviceToHost, lb->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(lb->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "population copy");
+    auto at = [&](size_t k) -> double {
+        return dbl ? reinterpret_cast<const double *>(h.data())[k] : (double)reinterpret_cast<const float *>(h.data())[k];
+    };
+    int c[19][3];
+    double w[19];
+    iblb::velocity_table(c, w);
+    const bool swapped = (lb->host_step & 1) != 0;
+    const int nn[3] = {nx, ny, nz};
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                const size_t id = (size_t)x + (size_t)nx * ((size_t)y + (size_t)ny * z);
+                const int xyz[3] = {x, y, z};
+                for (int i = 0; i < 19; ++i) {
+                    int s[3];
+                    bool inside = true;
+                    for (int a = 0; a < 3; ++a) {
+                        s[a] = xyz[a] - c[i][a];
+                        if (lb->p.bc[a] == IBL_BC_PERIODIC) s[a] = (s[a] + nn[a]) % nn[a];
+                        else if (s[a] < 0 || s[a] >= nn[a]) inside = false;
+                    }
+                    double v = 0.0;
+                    if (inside) {
+                        if (!swapped) {
+                            v = w[i] + at((size_t)i * qs + id);
+                        } else {
+                            const int o = i == 0 ? 0 : (i <= 9 ? i + 9 : i - 9);
+                            const size_t sid = (size_t)s[0] + (size_t)nx * ((size_t)s[1] + (size_t)ny * s[2]);
+                            v = w[i] + at((size_t)o * qs + sid);
+                        }
+                    }
+                    f[(size_t)i * nodes + id] = v;
+                }
+            }
+    return IBL_OK;
+}
+
+int ibl_copy_mesh(ibl_mesh *m, double *r, double *F, int32_t *tris)
+{
+    if (!m || !m->lb) return fail(IBL_EINVAL, "null mesh");
+    cudaStream_t s = m->lb->stream;
+    cudaError_t e = cudaSuccess;
+    if (r) e = cudaMemcpyAsync(r, m->v.r, sizeof(double) * 3 * m->v.nv, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && F) e = cudaMemcpyAsync(F, m->v.fn, sizeof(double) * 3 * m->v.nv, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "mesh copy");
+    if (tris) std::memcpy(tris, m->tris.data(), sizeof(int) * m->tris.size());
+    return IBL_OK;
+}
+
+int ibl_copy_neighbours(ibl_mesh *m, int32_t *ptr, int32_t *idx, int *nnz)
+{
+    if (!m) return fail(IBL_EINVAL, "null mesh");
+    if (ptr) std::memcpy(ptr, m->nb_ptr.data(), sizeof(int) * m->nb_ptr.size());
+    if (idx) std::memcpy(idx, m->nb_idx.data(), sizeof(int) * m->nb_idx.size());
+    if (nnz) *nnz = (int)m->nb_idx.size();
+    return IBL_OK;
+}
+
+int ibl_regularize_now(ibl_mesh *m, int *iters)
+{
+    if (!m || !m->lb) return fail(IBL_EINVAL, "null mesh");
+    ibl_lb *lb = m->lb;
+    cudaError_t e = iblb::launch_regularize(lb->v, m->v, m->reg, lb->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "regularisation launch");
+    Ctl c;
+    e = cudaMemcpyAsync(&c, lb->v.ctl, sizeof c, cudaMemcpyDeviceToHost, lb->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(lb->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "regularisation readout");
+    if (iters) *iters = c.reg_iters;
+    return lb_status_from_device(lb);
+}
+
+int ibl_run_frames(ibl_lb *lb, ibl_mesh *m, const double *A_frames, int n_frames, int steps_per_frame,
+                   ibl_observables *out)
+{
+    if (!lb || !m || m->lb != lb || !A_frames || !out || n_frames < 0) return fail(IBL_EINVAL, "bad arguments");
+    if (steps_per_frame != lb->v.n_hold) return fail(IBL_EINVAL, "steps_per_frame differs from the lattice's");
+    if (lb->host_step % lb->v.n_hold != 0) return fail(IBL_EINVAL, "step count is not at a frame boundary");
+    for (int k = 0; k < n_frames; ++k) {
+        const long long fk = lb->host_step / lb->v.n_hold;
+        if (fk >= lb->v.n_frames) return fail(IBL_EINVAL, "frame capacity of the lattice exceeded");
+        int st = ibl_set_frame(lb, (int)fk, A_frames + 9 * (size_t)k);
+        if (st != IBL_OK) return st;
+        st = ibl_step(lb, steps_per_frame);
+        if (st != IBL_OK) return st;
+        cudaError_t e = iblb::launch_observables(lb->v, m->v, lb->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "observables launch");
+        Ctl c;
+        e = cudaMemcpyAsync(&c, lb->v.ctl, sizeof c, cudaMemcpyDeviceToHost, lb->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(lb->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "frame readout");
+        const int slot = (c.n_records - 1) % m->v.ring_cap;
+        e = cudaMemcpyAsync(out + k, m->v.ring + slot, sizeof(ibl_observables), cudaMemcpyDeviceToHost, lb->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(lb->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "frame record copy");
+        if (c.err) return lb_status_from_device(lb);
+    }
+    return IBL_OK;
+}
+
+int ibl_profile_enable(ibl_lb *lb, int enable)
+{
+    if (!lb) return fail(IBL_EINVAL, "null lattice");
+    cudaStreamSynchronize(lb->stream);
+    lb->prof.clear();
+    lb->prof.on = enable != 0;
+    return IBL_OK;
+}
+
+int ibl_profile_read(ibl_lb *lb, double ms[3], long long launches[3])
+{
+    if (!lb || !ms || !launches) return fail(IBL_EINVAL, "null argument");
+    cudaError_t e = cudaStreamSynchronize(lb->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "profile synchronize");
+    for (int k = 0; k < 3; ++k) {
+        ms[k] = 0.0;
+        launches[k] = 0;
+    }
+    for (auto &mk : lb->prof.marks) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, lb->prof.pool[mk.second], lb->prof.pool[mk.second + 1]) == cudaSuccess) {
+            ms[mk.first] += t;
+            launches[mk.first] += 1;
+        }
+    }
+    return IBL_OK;
+}
+
+}  // extern "C"
