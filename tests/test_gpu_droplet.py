@@ -153,7 +153,7 @@ def test_run_frames_matches_stepping():
         assert x["step"] == y["step"] and abs(x["D"] - y["D"]) < 1e-9
     ra, _, _ = a.mesh()
     rb, _, _ = b.mesh()
-    assert np.abs(ra - rb).max() < 1e-9  # FP32 atomics: summation order may differ
+    assert np.abs(ra - rb).max() < 1e-7  # FP32 atomics: summation order may differ
 
 
 def test_wall_contact_is_reported():
