@@ -1,0 +1,302 @@
+"""Benchmark of the fused IB-LB droplet step (arXiv:2403.01161) on GB300.
+
+Workload: the single-droplet FP32 configuration -- 128^3 box with Zou-He
+walls imposing seeded traceless Ornstein-Uhlenbeck velocity gradients
+(correlation time 20 tau_eta, rms Ca 0.2, R/eta = 0.472), droplet R = 12
+on an icosphere of level 4 (2562 nodes, 5120 triangles), tau_f = 1, a shape
+record every 100 steps.  One "step" is one full IBLB time step (forces +
+spread, lattice stream-collide with the box boundary, interpolation +
+advection, scheduled readout).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload.  Under torchrun (N > 1) every rank runs an
+independent replica on its own GPU (the droplet problems do not exchange
+data); rank 0 prints the JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fused LB+IB MLUPS & % HBM roofline; ensemble droplet-steps/s; adjoint/forward time"
+UNIT = "MLUPS"
+BYTES_PER_NODE = 152  # 19 FP32 populations read + written per lattice node update
+L2_BYTES = 129 * 2 ** 20
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def workload():
+    from paper_2403_01161_gb300 import config
+
+    return config.single_droplet_128()
+
+
+def config_dict(w, extra=None):
+    d = {"workload": w.name, "box": list(w.n), "R": w.R, "icosphere_level": w.level, "mesh_nodes": 10 * 4 ** w.level + 2,
+         "triangles": 20 * 4 ** w.level, "tau": w.tau, "steps_per_frame": w.n_hold, "readout_every": 100,
+         "populations": "fp32 deviations, AA in place", "mesh": "fp64",
+         "l2": "no flush: population array %.0f MB > %d MB L2" % (19 * 4 * w.nodes / 1e6, L2_BYTES // 2 ** 20)}
+    if extra:
+        d.update(extra)
+    return d
+
+
+def traffic_from_profiles():
+    """Per-launch DRAM bytes of the lattice kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "lattice_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        d = json.load(fh)
+    import hashlib
+
+    src = os.path.join(ROOT, "paper_2403_01161_gb300", "csrc", "iblb_kernels.cu")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    if d.get("kernel_source_sha256") != h:
+        return None
+    return float(d["bytes_per_launch_full_size"])
+
+
+class ClockSampler:
+    """nvidia-smi clock samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_baseline(w, budget_s=15.0, max_steps=400):
+    """The FP64 oracle, as it stands, on this host's cores: a bounded number
+    of steps of the same workload (same box, mesh and gradients)."""
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    os.environ["OMP_NUM_THREADS"] = str(cores)
+    import oracle as O
+    from paper_2403_01161_gb300 import config
+
+    o = O.OracleSim(w.n, w.tau, w.frames, w.n_hold)
+    r, t = O.icosphere(w.level, w.R, config.box_center(w.n))
+    o.set_mesh(r, t, w.sigma)
+    t0 = time.perf_counter()
+    o.step(1)
+    first = time.perf_counter() - t0
+    n = max(1, min(max_steps, int(budget_s / max(first, 1e-3))))
+    t0 = time.perf_counter()
+    o.step(n)
+    dt = time.perf_counter() - t0
+    o.close()
+    return {"value": w.nodes * n / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d FP64 oracle steps of %s (steps 1..%d of the trajectory), %.1f s" % (n, w.name, n, dt)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return 0
+    w = workload()
+    # a step of the reference arm is a bounded sample of oracle steps
+    budget = max(2.0, min(20.0, 60.0 / max(1, args.steps + args.warmup)))
+    cb = cpu_baseline(w, budget_s=budget)
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": w.nodes / (cb["value"] * 1e6) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(w), "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2403_01161_gb300.sim import Sim
+
+    w = workload()
+    sim = Sim(w.n, w.tau, w.frames, w.n_hold, precision=w.precision, device=dev)
+    sim.add_icosphere(w.level, w.R, w.sigma)
+    sim.set_readout(100)
+    sim.step(args.warmup)
+    sim.sync()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    # event pairs around the lattice-kernel launches inside the replayed
+    # graph chunks; the last replay in the timed region is read back
+    sim.profile(True, mask=1 | 8)
+    sim.step(args.warmup)  # re-captures the chunk with its event nodes
+    sim.sync()
+    stream = torch.cuda.current_stream(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    prof = sim.profile_read()
+    sim.profile(False)
+    clk = clocks.stop()
+    st = sim.status()
+    if st != 0:
+        raise RuntimeError("device error status %d during the timed region" % st)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * w.nodes * args.steps / (ms * 1e-3) / 1e6
+    lb_ms, lb_n = prof["lattice"]
+    t_launch = lb_ms / lb_n * 1e-3 if lb_n else None
+    achieved = BYTES_PER_NODE * w.nodes / t_launch / 1e9 if t_launch else None
+    peak, peak_kind = measured_peaks()
+    launches = 3 * args.steps + (sim.steps_done // 100 - (sim.steps_done - args.steps) // 100)
+    sim.close()
+
+    # end to end through the C-ABI with host buffers: the Sec. 3.2 loop, per
+    # frame one pinned H2D gradient copy and one D2H shape record
+    n_fr = max(1, (args.steps + w.n_hold - 1) // w.n_hold)
+    pinned = torch.empty((n_fr, 9), dtype=torch.float64, pin_memory=True)
+    pinned.copy_(torch.from_numpy(np.ascontiguousarray(w.frames[:n_fr].reshape(n_fr, 9))))
+    sim2 = Sim(w.n, w.tau, w.frames[:n_fr], w.n_hold, precision=w.precision, device=dev)
+    sim2.add_icosphere(w.level, w.R, w.sigma)
+    sim2.sync()
+    barrier()
+    t0 = time.perf_counter()
+    recs = sim2.run_frames(pinned.numpy(), w.n_hold)
+    torch.cuda.synchronize(dev)
+    e2e_s = time.perf_counter() - t0
+    sim2.close()
+    assert len(recs) == n_fr
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_steps = n_fr * w.n_hold
+    import ctypes
+
+    from paper_2403_01161_gb300 import _lib
+
+    rec_bytes = ctypes.sizeof(_lib.Observables)
+    e2e = {"value": world * w.nodes * e2e_steps / e2e_s / 1e6, "unit": UNIT,
+           "h2d_bytes_per_step": 72.0 / w.n_hold, "d2h_bytes_per_step": rec_bytes / w.n_hold,
+           "steps": e2e_steps, "api": "ibl_run_frames (host gradients in, host shape records out)"}
+
+    if rank == 0:
+        cb = cpu_baseline(w) if world == 1 else None
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": config_dict(w, {"parallelism": "replicas" if world > 1 else "single"}),
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak if achieved else None, "traffic": traffic_from_profiles(),
+                             "kernel": "lattice stream-collide", "peak_kind": peak_kind,
+                             "kernel_us": t_launch * 1e6 if t_launch else None, "launches_timed": lb_n,
+                             "bytes_per_launch": BYTES_PER_NODE * w.nodes},
+                "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches * world, "clocks": clk,
+                "droplet_steps_per_s": world * args.steps / (ms * 1e-3),
+                "lagrangian_updates_per_s": world * (10 * 4 ** w.level + 2) * args.steps / (ms * 1e-3)}
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -174,6 +174,14 @@ int ibl_step(ibl_lb *lb, long long n);
  * (needs record_fields); read them with ibl_copy_fields. */
 int ibl_step_record(ibl_lb *lb);
 
+/* Graph replay (default on): ibl_step runs whole chunks of steps -- a
+ * multiple of 2 and of the regularisation and readout periods, at least 32
+ * -- as one captured CUDA graph launched on the bound stream, and the steps
+ * before the first chunk boundary and after the last one eagerly.  The
+ * chunk is captured on a private stream at the first use and again after
+ * any schedule change.  enable = 0 launches every kernel eagerly. */
+int ibl_set_graphs(ibl_lb *lb, int enable);
+
 /* Waits for the stream and reports the sticky device error bits as a status. */
 int ibl_sync(ibl_lb *lb);
 
@@ -223,12 +231,17 @@ int ibl_run_frames(ibl_lb *lb, ibl_mesh *m, const double *A_frames, int n_frames
 /* The library's D3Q19 velocities (19 x 3 int32) and weights (19 doubles). */
 int ibl_velocity_set(int32_t *c, double *w);
 
-/* Kernel timing with CUDA events on the bound stream: enable (1) records an
- * event pair around every launch of the lattice kernel and of the IB
- * kernels; ibl_profile_read synchronises and returns the summed durations
- * (ms) and launch counts [lattice, spread, interpolate] since enabling.
- * At most 65536 launches are recorded. */
-int ibl_profile_enable(ibl_lb *lb, int enable);
+/* Kernel timing with CUDA events on the bound stream.  `mask` selects the
+ * kernels bracketed by an event pair at every launch: bit 0 the lattice
+ * kernel, bit 1 the force/spread kernel, bit 2 the interpolation kernel (0
+ * turns timing off and clears it); bit 3 restricts timing to the launches
+ * inside captured graph chunks.  ibl_profile_read synchronises and
+ * returns the summed durations (ms) and launch counts [lattice, spread,
+ * interpolate] since enabling.  At most 65536 launches are recorded.  With
+ * graph replay the event pairs are nodes of the captured chunk, so each
+ * replay re-records them: the read covers the eager launches and the last
+ * replay of the chunk. */
+int ibl_profile_enable(ibl_lb *lb, int mask);
 int ibl_profile_read(ibl_lb *lb, double ms[3], long long launches[3]);
 
 const char *ibl_last_error(void);

@@ -69,6 +69,7 @@ SIGNATURES = [
     ("ibl_set_readout", ctypes.c_int, [_P, ctypes.c_int]),
     ("ibl_step", ctypes.c_int, [_P, ctypes.c_longlong]),
     ("ibl_step_record", ctypes.c_int, [_P]),
+    ("ibl_set_graphs", ctypes.c_int, [_P, ctypes.c_int]),
     ("ibl_sync", ctypes.c_int, [_P]),
     ("ibl_steps_done", ctypes.c_longlong, [_P]),
     ("ibl_readout", ctypes.c_int, [_P, ctypes.POINTER(Observables)]),

@@ -49,7 +49,7 @@ bool lb_layout(const ibl_lb_params *p, int n_frames, Layout &L)
     if (p->precision != IBL_FP32_DEV && p->precision != IBL_FP64) return false;
     if (n_frames < 1) return false;
     const long long nodes = (long long)p->n[0] * p->n[1] * p->n[2];
-    if (nodes > 0x7fffffffLL / 8) return false;
+    if (19 * pop_stride(nodes) + 64 > 0x7fffffffLL) return false;  // 32-bit population indices
     const size_t es = p->precision == IBL_FP64 ? 8 : 4;
     size_t off = 0;
     auto take = [&](size_t b) {
@@ -69,7 +69,7 @@ bool lb_layout(const ibl_lb_params *p, int n_frames, Layout &L)
 
 struct MeshLayout {
     size_t r = 0, fn = 0, tris = 0, n2t_ptr = 0, n2t = 0, nb_ptr = 0, nb_idx = 0, s0 = 0, s1 = 0, s2 = 0,
-           ring = 0, total = 0;
+           part = 0, ring = 0, total = 0;
 };
 
 bool mesh_layout(int nv, int nt, MeshLayout &L)
@@ -91,6 +91,7 @@ bool mesh_layout(int nv, int nt, MeshLayout &L)
     L.s0 = take(sizeof(double) * 3 * nv);
     L.s1 = take(sizeof(double) * 3 * nv);
     L.s2 = take(sizeof(double) * 3 * nv);
+    L.part = take(sizeof(double) * 6 * (((size_t)nv + 7) / 8 + 1));  // one row per interpolation block
     L.ring = take(sizeof(ibl_observables) * iblb::kRingCap);
     L.total = off;
     return true;
@@ -99,7 +100,7 @@ bool mesh_layout(int nv, int nt, MeshLayout &L)
 enum { PROF_LB = 0, PROF_SPREAD = 1, PROF_INTERP = 2 };
 
 struct Profiler {
-    bool on = false;
+    int mask = 0;
     std::vector<cudaEvent_t> pool;
     std::vector<std::pair<int, int>> marks;  // (kind, first event index)
     size_t used = 0;
@@ -137,6 +138,17 @@ struct ibl_lb {
     bool recorded = false;
     ibl_mesh *mesh = nullptr;
     Profiler prof;
+    // CUDA-graph replay of whole chunks of steps
+    bool graphs = true;
+    int chunk = 0;                       // steps per captured chunk (0 = none captured)
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t cap_stream = nullptr;   // private stream used only for capture
+    bool capturing = false;
+    ~ibl_lb()
+    {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+    }
 };
 
 struct ibl_mesh {
@@ -150,6 +162,8 @@ struct ibl_mesh {
 };
 
 namespace {
+
+void drop_graph(ibl_lb *lb);
 
 int lb_status_from_device(ibl_lb *lb)
 {
@@ -165,22 +179,23 @@ int lb_status_from_device(ibl_lb *lb)
     return IBL_OK;
 }
 
-void prof_begin(ibl_lb *lb, int kind)
+// Returns the index of the end event to record after the launch, or -1.
+int prof_begin(ibl_lb *lb, int kind)
 {
-    if (!lb->prof.on || lb->prof.marks.size() >= Profiler::kMax) return;
+    if (!((lb->prof.mask >> kind) & 1) || lb->prof.marks.size() >= Profiler::kMax) return -1;
+    if ((lb->prof.mask & 8) && !lb->capturing) return -1;  // graph replays only
     cudaEvent_t a = lb->prof.take();
     cudaEvent_t b = lb->prof.take();
-    if (!a || !b) return;
-    lb->prof.marks.push_back({kind, (int)lb->prof.used - 2});
+    if (!a || !b) return -1;
+    const int idx = (int)lb->prof.used - 2;
+    lb->prof.marks.push_back({kind, idx});
     cudaEventRecord(a, lb->stream);
+    return idx + 1;
 }
 
-void prof_end(ibl_lb *lb)
+void prof_end(ibl_lb *lb, int end_idx)
 {
-    if (!lb->prof.on || lb->prof.marks.empty()) return;
-    const int idx = lb->prof.marks.back().second;
-    if ((size_t)idx + 2 != lb->prof.used) return;  // begin was skipped
-    cudaEventRecord(lb->prof.pool[idx + 1], lb->stream);
+    if (end_idx >= 0) cudaEventRecord(lb->prof.pool[end_idx], lb->stream);
 }
 
 int one_step(ibl_lb *lb, bool record)
@@ -189,20 +204,24 @@ int one_step(ibl_lb *lb, bool record)
     ibl_mesh *m = lb->mesh;
     const bool odd = (lb->host_step & 1) != 0;
     if (m) {
-        prof_begin(lb, PROF_SPREAD);
+        const int pe = prof_begin(lb, PROF_SPREAD);
         e = iblb::launch_spread(lb->v, m->v, lb->stream);
-        prof_end(lb);
+        prof_end(lb, pe);
         if (e != cudaSuccess) return cuda_fail(e, "spread launch");
     }
-    prof_begin(lb, PROF_LB);
+    const int pl = prof_begin(lb, PROF_LB);
     e = iblb::launch_lattice(lb->v, odd, record, lb->stream);
-    prof_end(lb);
+    prof_end(lb, pl);
     if (e != cudaSuccess) return cuda_fail(e, "lattice launch");
     const long long next = lb->host_step + 1;
+    if (!m) {
+        e = iblb::launch_advance(lb->v, lb->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "step counter launch");
+    }
     if (m) {
-        prof_begin(lb, PROF_INTERP);
+        const int pi = prof_begin(lb, PROF_INTERP);
         e = iblb::launch_interp(lb->v, m->v, lb->stream);
-        prof_end(lb);
+        prof_end(lb, pi);
         if (e != cudaSuccess) return cuda_fail(e, "interpolation launch");
         if (m->reg_every > 0 && next % m->reg_every == 0) {
             e = iblb::launch_regularize(lb->v, m->v, m->reg, lb->stream);
@@ -383,6 +402,7 @@ int mesh_attach(ibl_lb *lb, int nv, const double *r, int nt, const int *tri_in, 
     m->v.s0 = reinterpret_cast<double *>(w + L.s0);
     m->v.s1 = reinterpret_cast<double *>(w + L.s1);
     m->v.s2 = reinterpret_cast<double *>(w + L.s2);
+    m->v.part = reinterpret_cast<double *>(w + L.part);
     m->v.ring = reinterpret_cast<ibl_observables *>(w + L.ring);
     m->v.ring_cap = iblb::kRingCap;
     m->tris = tri;
@@ -406,9 +426,72 @@ int mesh_attach(ibl_lb *lb, int nv, const double *r, int nt, const int *tri_in, 
         delete m;
         return cuda_fail(e, "mesh upload");
     }
+    drop_graph(lb);
     lb->mesh = m;
     *out = m;
     return IBL_OK;
+}
+
+}  // namespace
+
+namespace {
+
+void drop_graph(ibl_lb *lb)
+{
+    if (lb && lb->gexec) {
+        cudaGraphExecDestroy(lb->gexec);
+        lb->gexec = nullptr;
+    }
+    if (lb) lb->chunk = 0;
+}
+
+long long gcd_ll(long long a, long long b) { return b == 0 ? a : gcd_ll(b, a % b); }
+
+// Steps per chunk: a multiple of 2 (AA parity) and of the regularisation and
+// readout periods, at least 32; 0 when that would exceed 2048.
+int chunk_length(const ibl_lb *lb)
+{
+    long long c = 2;
+    const ibl_mesh *m = lb->mesh;
+    auto lcm = [&](long long a, long long b) { return a / gcd_ll(a, b) * b; };
+    if (m && m->reg_every > 0) c = lcm(c, m->reg_every);
+    if (m && m->readout_every > 0) c = lcm(c, m->readout_every);
+    if (c > 2048) return 0;
+    while (c < 32) c *= 2;
+    return (int)c;
+}
+
+// Captures one chunk starting at an aligned step (host_step % chunk == 0).
+int capture_chunk(ibl_lb *lb, int chunk)
+{
+    cudaError_t e = cudaSuccess;
+    if (!lb->cap_stream) e = cudaStreamCreateWithFlags(&lb->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "capture stream");
+    const long long saved = lb->host_step;
+    cudaStream_t bound = lb->stream;
+    lb->stream = lb->cap_stream;
+    e = cudaStreamBeginCapture(lb->cap_stream, cudaStreamCaptureModeThreadLocal);
+    int st = IBL_OK;
+    if (e == cudaSuccess) {
+        lb->capturing = true;
+        for (int k = 0; k < chunk && st == IBL_OK; ++k) st = one_step(lb, false);
+        lb->capturing = false;
+        cudaGraph_t g = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(lb->cap_stream, &g);
+        if (e2 != cudaSuccess && st == IBL_OK) st = cuda_fail(e2, "end capture");
+        if (st == IBL_OK) {
+            const cudaError_t e3 = cudaGraphInstantiate(&lb->gexec, g, 0);
+            if (e3 != cudaSuccess) st = cuda_fail(e3, "graph instantiate");
+        }
+        if (g) cudaGraphDestroy(g);
+    } else {
+        st = cuda_fail(e, "begin capture");
+    }
+    lb->stream = bound;
+    lb->host_step = saved;
+    if (st == IBL_OK) lb->chunk = chunk;
+    else drop_graph(lb);
+    return st;
 }
 
 }  // namespace
@@ -482,8 +565,6 @@ int ibl_lb_create(const ibl_lb_params *p, const double *A_frames, int n_frames, 
     for (int a = 0; a < 4; ++a) {
         c.patch_lo[a] = 0;
         c.patch_ext[a] = -1;
-        c.key_min[a] = ~0ull;
-        c.key_max[a] = 0ull;
     }
     const size_t es = p->precision == IBL_FP64 ? 8 : 4;
     cudaError_t e = cudaMemcpyAsync(v.ctl, &c, sizeof c, cudaMemcpyHostToDevice, lb->stream);
@@ -583,6 +664,7 @@ void ibl_mesh_destroy(ibl_mesh *m)
     if (!m) return;
     if (m->lb) {
         cudaStreamSynchronize(m->lb->stream);
+        drop_graph(m->lb);
         m->lb->mesh = nullptr;
     }
     delete m;
@@ -595,6 +677,10 @@ int ibl_set_regularization(ibl_mesh *m, double alpha, double gamma, double tol, 
         return fail(IBL_EINVAL, "regularisation parameters out of range");
     m->reg = iblb::RegParams{alpha, gamma, tol, max_iter, plus_sign ? 1 : 0};
     m->reg_every = every;
+    if (m->lb) {
+        cudaStreamSynchronize(m->lb->stream);
+        drop_graph(m->lb);
+    }
     return IBL_OK;
 }
 
@@ -602,16 +688,52 @@ int ibl_set_readout(ibl_mesh *m, int every)
 {
     if (!m || every < 0) return fail(IBL_EINVAL, "bad readout interval");
     m->readout_every = every;
+    if (m->lb) {
+        cudaStreamSynchronize(m->lb->stream);
+        drop_graph(m->lb);
+    }
     return IBL_OK;
 }
 
 int ibl_step(ibl_lb *lb, long long n)
 {
     if (!lb || n < 0) return fail(IBL_EINVAL, "bad step request");
-    for (long long k = 0; k < n; ++k) {
+    const int chunk = lb->graphs ? chunk_length(lb) : 0;
+    long long done = 0;
+    if (chunk > 0) {
+        // eager steps up to the next chunk boundary, then whole chunks by replay
+        while (done < n && lb->host_step % chunk != 0) {
+            const int st = one_step(lb, false);
+            if (st != IBL_OK) return st;
+            ++done;
+        }
+        if (n - done >= chunk) {
+            if (lb->chunk != chunk) {
+                drop_graph(lb);
+                const int st = capture_chunk(lb, chunk);
+                if (st != IBL_OK) return st;
+            }
+            while (n - done >= chunk) {
+                const cudaError_t e = cudaGraphLaunch(lb->gexec, lb->stream);
+                if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+                lb->host_step += chunk;
+                done += chunk;
+            }
+        }
+    }
+    for (; done < n; ++done) {
         const int st = one_step(lb, false);
         if (st != IBL_OK) return st;
     }
+    return IBL_OK;
+}
+
+int ibl_set_graphs(ibl_lb *lb, int enable)
+{
+    if (!lb) return fail(IBL_EINVAL, "null lattice");
+    cudaStreamSynchronize(lb->stream);
+    drop_graph(lb);
+    lb->graphs = enable != 0;
     return IBL_OK;
 }
 
@@ -806,12 +928,13 @@ int ibl_run_frames(ibl_lb *lb, ibl_mesh *m, const double *A_frames, int n_frames
     return IBL_OK;
 }
 
-int ibl_profile_enable(ibl_lb *lb, int enable)
+int ibl_profile_enable(ibl_lb *lb, int mask)
 {
-    if (!lb) return fail(IBL_EINVAL, "null lattice");
+    if (!lb || mask < 0 || mask > 15) return fail(IBL_EINVAL, "bad profiling mask");
     cudaStreamSynchronize(lb->stream);
+    drop_graph(lb);  // a captured chunk may hold event nodes of the pool
     lb->prof.clear();
-    lb->prof.on = enable != 0;
+    lb->prof.mask = mask;
     return IBL_OK;
 }
 

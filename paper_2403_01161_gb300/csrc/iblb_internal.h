@@ -14,16 +14,15 @@ namespace iblb {
 // Device control block of one lattice (lives in the lattice workspace).
 struct alignas(128) Ctl {
     long long step;              // steps completed (advanced by the lattice kernel)
-    unsigned int lb_blocks_done; // last-block tickets
-    unsigned int ib_blocks_done;
+    unsigned int lb_blocks_done; // unused
+    unsigned int ib_blocks_done; // last-block ticket of the interpolation kernel
     int err;                     // IBL_ERRBIT_* (sticky)
     int reg_iters;               // iterations of the latest regularisation
     int n_records;               // shape records written
     int pad0;
     int patch_lo[4];             // droplet patch: lower corner (normalised into the box)
     int patch_ext[4];            // extent (hi - lo), -1 = empty
-    unsigned long long key_min[4];  // order-preserving keys of the node bounding box
-    unsigned long long key_max[4];
+    unsigned long long pad1[8];
 };
 
 // Views handed to kernels by value.
@@ -56,6 +55,7 @@ struct MeshView {
     const int *nb_ptr;  // [nv+1]
     const int *nb_idx;  // [3 nt]
     double *s0, *s1, *s2;  // regularisation scratch, [nv][3] each
+    double *part;          // per-block bounding-box partials of the interpolation kernel, [blocks][6]
     ibl_observables *ring;
     int ring_cap;
 };
@@ -70,6 +70,7 @@ constexpr int kRingCap = 4096;
 
 cudaError_t launch_init(const LbView &L, cudaStream_t s);
 cudaError_t launch_lattice(const LbView &L, bool odd, bool record, cudaStream_t s);
+cudaError_t launch_advance(const LbView &L, cudaStream_t s);
 cudaError_t launch_spread(const LbView &L, const MeshView &M, cudaStream_t s);
 cudaError_t launch_interp(const LbView &L, const MeshView &M, cudaStream_t s);
 cudaError_t launch_regularize(const LbView &L, const MeshView &M, const RegParams &p, cudaStream_t s);

@@ -223,32 +223,41 @@ __device__ __forceinline__ int step_coord(int x, int d, int n, bool periodic)
 // ---------------------------------------------------------------------------
 // Lattice update: streaming (AA pattern) + boundary rebuild + moments with
 // half-force momentum + BGK + Guo source, Eqs. (LBMEQ)-(density_velocity_LB).
+// One thread per node; blocks tile (x, y) rows of one z plane, so no index
+// division is needed.  Indices are 32-bit (19 * stride < 2^31 is checked on
+// the host).  The collision works on opposite pairs (c_i, -c_i), whose
+// equilibrium and source terms share their even parts.
 template <typename T, bool ODD, bool REC>
-__global__ void __launch_bounds__(256) k_lattice(LbView L)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_lattice(LbView L)
 {
     const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
-    const int node = blockIdx.x * blockDim.x + threadIdx.x;
-    bool active = node < L.nodes;
-    int x = 0, y = 0, z = 0;
-    if (active) {
-        const int nxy = nx * ny;
-        z = node / nxy;
-        const int rem = node - z * nxy;
-        y = rem / nx;
-        x = rem - y * nx;
-    }
-    T *__restrict__ f = static_cast<T *>(L.f);
-    const long long qs = L.qs;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
     bool bad = false;
-    if (active) {
+    if (x < nx && y < ny) {
+        const int nxy = nx * ny;
+        const int node = x + nx * y + nxy * z;
+        T *__restrict__ f = static_cast<T *>(L.f);
+        const int qs = (int)L.qs;
         const bool px = L.bc[0] == IBL_BC_PERIODIC, py = L.bc[1] == IBL_BC_PERIODIC,
                    pz = L.bc[2] == IBL_BC_PERIODIC;
         const int sx = px ? 0 : (x == 0 ? -1 : (x == nx - 1 ? 1 : 0));
         const int sy = py ? 0 : (y == 0 ? -1 : (y == ny - 1 ? 1 : 0));
         const int sz = pz ? 0 : (z == 0 ? -1 : (z == nz - 1 ? 1 : 0));
-        const int xm = step_coord(x, -1, nx, px), xp = step_coord(x, 1, nx, px);
-        const int ym = step_coord(y, -1, ny, py), yp = step_coord(y, 1, ny, py);
-        const int zm = step_coord(z, -1, nz, pz), zp = step_coord(z, 1, nz, pz);
+        // offsets to the neighbours along each axis; periodic axes wrap,
+        // Zou-He axes mark the missing neighbour invalid (bits of `miss`:
+        // 1 x-1, 2 x+1, 4 y-1, 8 y+1, 16 z-1, 32 z+1)
+        int oxm = -1, oxp = 1, oym = -nx, oyp = nx, ozm = -nxy, ozp = nxy;
+        int miss = 0;
+        if constexpr (ODD) {
+            if (x == 0) { if (px) oxm = nx - 1; else miss |= 1; }
+            if (x == nx - 1) { if (px) oxp = -(nx - 1); else miss |= 2; }
+            if (y == 0) { if (py) oym = (ny - 1) * nx; else miss |= 4; }
+            if (y == ny - 1) { if (py) oyp = -(ny - 1) * nx; else miss |= 8; }
+            if (z == 0) { if (pz) ozm = (nz - 1) * nxy; else miss |= 16; }
+            if (z == nz - 1) { if (pz) ozp = -(nz - 1) * nxy; else miss |= 32; }
+        }
 
         T g[19];
         if constexpr (!ODD) {
@@ -260,34 +269,34 @@ __global__ void __launch_bounds__(256) k_lattice(LbView L)
             // source x - c_i, slot opp(i)
             sfor<19>([&](auto I) {
                 constexpr int i = decltype(I)::value;
-                const int ax = cxf(i) == 0 ? x : (cxf(i) > 0 ? xm : xp);
-                const int ay = cyf(i) == 0 ? y : (cyf(i) > 0 ? ym : yp);
-                const int az = czf(i) == 0 ? z : (czf(i) > 0 ? zm : zp);
-                if (ax >= 0 && ay >= 0 && az >= 0)
-                    g[i] = f[opp(i) * qs + (ax + nx * (ay + ny * az))];
-                else
-                    g[i] = T(0);
+                constexpr int cx = cxf(i), cy = cyf(i), cz = czf(i);
+                constexpr int need = (cx > 0 ? 1 : (cx < 0 ? 2 : 0)) | (cy > 0 ? 4 : (cy < 0 ? 8 : 0)) |
+                                     (cz > 0 ? 16 : (cz < 0 ? 32 : 0));
+                const int off = (cx > 0 ? oxm : (cx < 0 ? oxp : 0)) + (cy > 0 ? oym : (cy < 0 ? oyp : 0)) +
+                                (cz > 0 ? ozm : (cz < 0 ? ozp : 0));
+                g[i] = (miss & need) == 0 ? f[opp(i) * qs + node + off] : T(0);
             });
         }
 
         if (sx | sy | sz) {
+            // Eq. (velo_facce_cubo_da_gradiente) in the storage precision
             const double *A = frame_ptr(L, L.ctl->step);
-            const double lx = x - 0.5 * (nx - 1), ly = y - 0.5 * (ny - 1), lz = z - 0.5 * (nz - 1);
-            const T uw[3] = {T(A[0] * lx + A[1] * ly + A[2] * lz), T(A[3] * lx + A[4] * ly + A[5] * lz),
-                             T(A[6] * lx + A[7] * ly + A[8] * lz)};
+            const T lx = T(x) - T(0.5) * T(nx - 1), ly = T(y) - T(0.5) * T(ny - 1), lz = T(z) - T(0.5) * T(nz - 1);
+            const T uw[3] = {T(A[0]) * lx + T(A[1]) * ly + T(A[2]) * lz, T(A[3]) * lx + T(A[4]) * ly + T(A[5]) * lz,
+                             T(A[6]) * lx + T(A[7]) * ly + T(A[8]) * lz};
             bc_dispatch<T>(g, uw, L.rule, (sx + 1) + 3 * (sy + 1) + 9 * (sz + 1));
         }
 
         // droplet patch: read the spread force (and clear it), store u below
-        bool in_patch = false;
+        bool in_patch;
         {
             const Ctl *c = L.ctl;
             int dx = x - c->patch_lo[0], dy = y - c->patch_lo[1], dz = z - c->patch_lo[2];
             if (px && dx < 0) dx += nx;
             if (py && dy < 0) dy += ny;
             if (pz && dz < 0) dz += nz;
-            in_patch = dx >= 0 && dx <= c->patch_ext[0] && dy >= 0 && dy <= c->patch_ext[1] && dz >= 0 &&
-                       dz <= c->patch_ext[2];
+            in_patch = (unsigned)dx <= (unsigned)c->patch_ext[0] && (unsigned)dy <= (unsigned)c->patch_ext[1] &&
+                       (unsigned)dz <= (unsigned)c->patch_ext[2];
         }
         T Fx = T(0), Fy = T(0), Fz = T(0);
         T *__restrict__ force = static_cast<T *>(L.force);
@@ -318,16 +327,26 @@ __global__ void __launch_bounds__(256) k_lattice(LbView L)
         const T fpre = T(1) - T(0.5) * om;
         const T uF = ux * Fx + uy * Fy + uz * Fz;
         const T base = T(1.5) * uu;
-        sfor<19>([&](auto I) {
-            constexpr int i = decltype(I)::value;
+        {
+            constexpr double w0 = wgt(0);
+            const T geq = T(w0) * (drho - rho * base);
+            const T src = fpre * T(w0) * (T(-3) * uF);
+            g[0] = g[0] + om * (geq - g[0]) + src;
+        }
+        sfor<9>([&](auto I) {
+            constexpr int i = decltype(I)::value + 1;
+            constexpr int j = opp(i);
             T cu = T(0), cF = T(0);
             if constexpr (cxf(i) != 0) { cu += T(cxf(i)) * ux; cF += T(cxf(i)) * Fx; }
             if constexpr (cyf(i) != 0) { cu += T(cyf(i)) * uy; cF += T(cyf(i)) * Fy; }
             if constexpr (czf(i) != 0) { cu += T(czf(i)) * uz; cF += T(czf(i)) * Fz; }
             constexpr double w = wgt(i);
-            const T geq = T(w) * (drho + rho * (T(3) * cu + T(4.5) * cu * cu - base));
-            const T src = fpre * T(w) * (T(3) * (cF - uF) + T(9) * cu * cF);
-            g[i] = g[i] + om * (geq - g[i]) + src;
+            const T even_eq = T(w) * (drho + rho * (T(4.5) * cu * cu - base));
+            const T odd_eq = T(3.0 * w) * rho * cu;
+            const T even_src = fpre * T(w) * (T(9) * cu * cF - T(3) * uF);
+            const T odd_src = fpre * T(3.0 * w) * cF;
+            g[i] = g[i] + om * (even_eq + odd_eq - g[i]) + (even_src + odd_src);
+            g[j] = g[j] + om * (even_eq - odd_eq - g[j]) + (even_src - odd_src);
         });
 
         if constexpr (!ODD) {
@@ -339,10 +358,12 @@ __global__ void __launch_bounds__(256) k_lattice(LbView L)
             // destination x + c_i, slot i
             sfor<19>([&](auto I) {
                 constexpr int i = decltype(I)::value;
-                const int ax = cxf(i) == 0 ? x : (cxf(i) > 0 ? xp : xm);
-                const int ay = cyf(i) == 0 ? y : (cyf(i) > 0 ? yp : ym);
-                const int az = czf(i) == 0 ? z : (czf(i) > 0 ? zp : zm);
-                if (ax >= 0 && ay >= 0 && az >= 0) f[i * qs + (ax + nx * (ay + ny * az))] = g[i];
+                constexpr int cx = cxf(i), cy = cyf(i), cz = czf(i);
+                constexpr int need = (cx > 0 ? 2 : (cx < 0 ? 1 : 0)) | (cy > 0 ? 8 : (cy < 0 ? 4 : 0)) |
+                                     (cz > 0 ? 32 : (cz < 0 ? 16 : 0));
+                const int off = (cx > 0 ? oxp : (cx < 0 ? oxm : 0)) + (cy > 0 ? oyp : (cy < 0 ? oym : 0)) +
+                                (cz > 0 ? ozp : (cz < 0 ? ozm : 0));
+                if ((miss & need) == 0) f[i * qs + node + off] = g[i];
             });
         }
         if (in_patch) {
@@ -365,18 +386,10 @@ __global__ void __launch_bounds__(256) k_lattice(LbView L)
     // sticky instability flag, one atomic per warp at most
     const unsigned m = __ballot_sync(0xffffffffu, bad);
     if (m != 0u && (threadIdx.x & 31) == 0) atomicOr(&L.ctl->err, IBL_ERRBIT_UNSTABLE);
-    // the last block to finish advances the step counter
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned t = atomicAdd(&L.ctl->lb_blocks_done, 1u);
-        if (t == gridDim.x - 1) {
-            L.ctl->step += 1;
-            L.ctl->lb_blocks_done = 0u;
-            __threadfence();
-        }
-    }
 }
+
+// Advances the step counter when no droplet kernel follows the lattice kernel.
+__global__ void k_advance(Ctl *ctl) { ctl->step += 1; }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_init(LbView L)
@@ -403,34 +416,14 @@ __global__ void __launch_bounds__(256) k_init(LbView L)
 
 // ---------------------------------------------------------------------------
 // Immersed boundary.
-__device__ __forceinline__ double peskin_phi(double x)
+// Peskin 4-point stencil phi (Sec. 3.1), in the storage precision T.
+template <typename T>
+__device__ __forceinline__ T peskin_phi(T x)
 {
-    const double a = fabs(x);
-    if (a < 1.0) return 0.125 * (3.0 - 2.0 * a + sqrt(1.0 + 4.0 * a - 4.0 * a * a));
-    if (a < 2.0) return 0.125 * (5.0 - 2.0 * a - sqrt(-7.0 + 12.0 * a - 4.0 * a * a));
-    return 0.0;
-}
-
-// The four stencil nodes floor(r)-1 .. floor(r)+2 along one axis and their
-// weights; on a Zou-He axis all must be interior nodes (1..n-2), periodic
-// axes wrap.  Returns false for an invalid stencil (the caller flags it).
-__device__ __forceinline__ bool stencil(double ra, int n, bool periodic, int idx[4], double w[4])
-{
-    if (!(fabs(ra) < 1e8)) return false;
-    const int base = (int)floor(ra) - 1;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        int g = base + k;
-        w[k] = peskin_phi(ra - (double)g);
-        if (periodic) {
-            g %= n;
-            if (g < 0) g += n;
-        } else if (g < 1 || g > n - 2) {
-            return false;
-        }
-        idx[k] = g;
-    }
-    return true;
+    const T a = fabs(x);
+    if (a < T(1)) return T(0.125) * (T(3) - T(2) * a + sqrt(T(1) + T(4) * a - T(4) * a * a));
+    if (a < T(2)) return T(0.125) * (T(5) - T(2) * a - sqrt(T(-7) + T(12) * a - T(4) * a * a));
+    return T(0);
 }
 
 __device__ __forceinline__ void cross3(const double a[3], const double b[3], double o[3])
@@ -440,16 +433,45 @@ __device__ __forceinline__ void cross3(const double a[3], const double b[3], dou
     o[2] = a[0] * b[1] - a[1] * b[0];
 }
 
+// The 4-point stencil along one axis starts at base = floor(r) - 1.  On a
+// Zou-He axis all four nodes must be interior (1..n-2); periodic axes wrap.
+struct AxisStencil {
+    int base;
+    bool ok;
+};
+__device__ __forceinline__ AxisStencil axis_stencil(double ra, int n, bool periodic)
+{
+    AxisStencil A;
+    A.ok = fabs(ra) < 1e8;
+    A.base = A.ok ? (int)floor(ra) - 1 : 0;
+    if (A.ok && !periodic) A.ok = A.base >= 1 && A.base + 3 <= n - 2;
+    return A;
+}
+__device__ __forceinline__ int wrap_index(int g, int n, bool periodic)
+{
+    if (periodic) {
+        g %= n;
+        if (g < 0) g += n;
+    }
+    return g;
+}
+
+constexpr int kLanesPerNode = 16;  // lane = (b, c) row of the 4x4x4 stencil
+
 // Nodal force F_i = -sigma dA/dx_i (Eq. (pi_drop)) gathered over the
 // triangles around node i, then spread with the 4-point delta
-// (Eq. (ibm_force_d)(a)) by atomic adds into the Eulerian force.
+// (Eq. (ibm_force_d)(a)) by atomic adds into the Eulerian force.  Sixteen
+// lanes per node: the lanes split the incident triangles (reduced with
+// shuffles), then each lane adds one x-row of four stencil points.
 template <typename T>
 __global__ void __launch_bounds__(128) k_spread(LbView L, MeshView M)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= M.nv) return;
+    const int gid = blockIdx.x * (blockDim.x / kLanesPerNode) + threadIdx.x / kLanesPerNode;
+    const int lane = threadIdx.x % kLanesPerNode;
+    const bool valid = gid < M.nv;
+    const int i = valid ? gid : M.nv - 1;
     double F[3] = {0.0, 0.0, 0.0};
-    for (int k = M.n2t_ptr[i]; k < M.n2t_ptr[i + 1]; ++k) {
+    for (int k = M.n2t_ptr[i] + lane; k < M.n2t_ptr[i + 1]; k += kLanesPerNode) {
         const int e = M.n2t[k];
         const int t = e / 3, slot = e - 3 * t;
         const int v0 = M.tris[3 * t], v1 = M.tris[3 * t + 1], v2 = M.tris[3 * t + 2];
@@ -468,44 +490,40 @@ __global__ void __launch_bounds__(128) k_spread(LbView L, MeshView M)
         cross3(n, d, g);
         for (int a = 0; a < 3; ++a) F[a] += -M.sigma * 0.5 * g[a];
     }
-    M.fn[3 * i] = F[0];
-    M.fn[3 * i + 1] = F[1];
-    M.fn[3 * i + 2] = F[2];
-    const double r[3] = {M.r[3 * i], M.r[3 * i + 1], M.r[3 * i + 2]};
-    int ix[4], iy[4], iz[4];
-    double wx[4], wy[4], wz[4];
-    const bool ok = stencil(r[0], L.n[0], L.bc[0] == IBL_BC_PERIODIC, ix, wx) &&
-                    stencil(r[1], L.n[1], L.bc[1] == IBL_BC_PERIODIC, iy, wy) &&
-                    stencil(r[2], L.n[2], L.bc[2] == IBL_BC_PERIODIC, iz, wz);
-    if (!ok) {
-        atomicOr(&L.ctl->err, IBL_ERRBIT_WALL);
+    for (int o = kLanesPerNode / 2; o > 0; o >>= 1)
+        for (int a = 0; a < 3; ++a) F[a] += __shfl_xor_sync(0xffffffffu, F[a], o, kLanesPerNode);
+    if (valid && lane == 0) {
+        M.fn[3 * i] = F[0];
+        M.fn[3 * i + 1] = F[1];
+        M.fn[3 * i + 2] = F[2];
+    }
+    const double r0 = M.r[3 * i], r1 = M.r[3 * i + 1], r2 = M.r[3 * i + 2];
+    const bool perx = L.bc[0] == IBL_BC_PERIODIC, pery = L.bc[1] == IBL_BC_PERIODIC,
+               perz = L.bc[2] == IBL_BC_PERIODIC;
+    const AxisStencil ax = axis_stencil(r0, L.n[0], perx), ay = axis_stencil(r1, L.n[1], pery),
+                      az = axis_stencil(r2, L.n[2], perz);
+    if (!valid) return;
+    if (!(ax.ok && ay.ok && az.ok)) {
+        if (lane == 0) atomicOr(&L.ctl->err, IBL_ERRBIT_WALL);
         return;
     }
+    // weights in the storage precision (the offsets r - x are formed in FP64)
+    const int b = lane & 3, c = lane >> 2;
+    const T wy = peskin_phi<T>(T(r1 - (double)(ay.base + b)));
+    const T wz = peskin_phi<T>(T(r2 - (double)(az.base + c)));
+    const int nx = L.n[0], nxy = L.n[0] * L.n[1], nodes = L.nodes;
+    const int row = wrap_index(ay.base + b, L.n[1], pery) * nx + wrap_index(az.base + c, L.n[2], perz) * nxy;
     T *force = static_cast<T *>(L.force);
-    const int nodes = L.nodes, nx = L.n[0], nxy = L.n[0] * L.n[1];
-    for (int c = 0; c < 4; ++c)
-        for (int b = 0; b < 4; ++b) {
-            const int row = iy[b] * nx + iz[c] * nxy;
-            for (int a = 0; a < 4; ++a) {
-                const double dl = wx[a] * wy[b] * wz[c];
-                const int id = row + ix[a];
-                atomicAdd(force + id, T(F[0] * dl));
-                atomicAdd(force + nodes + id, T(F[1] * dl));
-                atomicAdd(force + 2 * nodes + id, T(F[2] * dl));
-            }
-        }
-}
-
-// order-preserving unsigned keys of doubles, for atomic min/max
-__device__ __forceinline__ unsigned long long dkey(double v)
-{
-    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-    return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
-}
-__device__ __forceinline__ double dkey_inv(unsigned long long k)
-{
-    const unsigned long long b = (k & 0x8000000000000000ull) ? (k & ~0x8000000000000000ull) : ~k;
-    return __longlong_as_double((long long)b);
+    const T Fx = T(F[0]), Fy = T(F[1]), Fz = T(F[2]);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const T wx = peskin_phi<T>(T(r0 - (double)(ax.base + a)));
+        const T dl = wx * wy * wz;
+        const int id = row + wrap_index(ax.base + a, nx, perx);
+        atomicAdd(force + id, Fx * dl);
+        atomicAdd(force + nodes + id, Fy * dl);
+        atomicAdd(force + 2 * nodes + id, Fz * dl);
+    }
 }
 
 // Patch of lattice nodes the droplet's stencils can touch, from the node
@@ -542,90 +560,120 @@ __device__ void write_patch(const LbView &L, const double mn[3], const double mx
 }
 
 // u at r_i by the 4-point delta (Eq. (ibm_force_d)(b)) and forward Euler
-// (Eq. (fwd_euler)); then the bounding box of the advected nodes sets the
-// patch of the next step (last block).
+// (Eq. (fwd_euler)), sixteen lanes per node (one x-row of four stencil
+// points each, reduced with shuffles); then the bounding box of the advected
+// nodes sets the patch of the next step and the last block closes the step.
 template <typename T>
 __global__ void __launch_bounds__(128) k_interp(LbView L, MeshView M)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    double r[3] = {0.0, 0.0, 0.0};
-    bool have = false;
-    if (i < M.nv) {
-        r[0] = M.r[3 * i];
-        r[1] = M.r[3 * i + 1];
-        r[2] = M.r[3 * i + 2];
-        have = true;
-        int ix[4], iy[4], iz[4];
-        double wx[4], wy[4], wz[4];
-        const bool ok = stencil(r[0], L.n[0], L.bc[0] == IBL_BC_PERIODIC, ix, wx) &&
-                        stencil(r[1], L.n[1], L.bc[1] == IBL_BC_PERIODIC, iy, wy) &&
-                        stencil(r[2], L.n[2], L.bc[2] == IBL_BC_PERIODIC, iz, wz);
+    const int gid = blockIdx.x * (blockDim.x / kLanesPerNode) + threadIdx.x / kLanesPerNode;
+    const int lane = threadIdx.x % kLanesPerNode;
+    const bool valid = gid < M.nv;
+    const int i = valid ? gid : M.nv - 1;
+    double r[3] = {M.r[3 * i], M.r[3 * i + 1], M.r[3 * i + 2]};
+    const bool perx = L.bc[0] == IBL_BC_PERIODIC, pery = L.bc[1] == IBL_BC_PERIODIC,
+               perz = L.bc[2] == IBL_BC_PERIODIC;
+    const AxisStencil ax = axis_stencil(r[0], L.n[0], perx), ay = axis_stencil(r[1], L.n[1], pery),
+                      az = axis_stencil(r[2], L.n[2], perz);
+    const bool ok = ax.ok && ay.ok && az.ok;
+    T v[3] = {T(0), T(0), T(0)};
+    if (ok) {
+        const int b = lane & 3, c = lane >> 2;
+        const T wy = peskin_phi<T>(T(r[1] - (double)(ay.base + b)));
+        const T wz = peskin_phi<T>(T(r[2] - (double)(az.base + c)));
+        const int nx = L.n[0], nxy = L.n[0] * L.n[1], nodes = L.nodes;
+        const int row = wrap_index(ay.base + b, L.n[1], pery) * nx + wrap_index(az.base + c, L.n[2], perz) * nxy;
+        const T *vel = static_cast<const T *>(L.vel);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const T wx = peskin_phi<T>(T(r[0] - (double)(ax.base + a)));
+            const T dl = wx * wy * wz;
+            const int id = row + wrap_index(ax.base + a, nx, perx);
+            v[0] += vel[id] * dl;
+            v[1] += vel[nodes + id] * dl;
+            v[2] += vel[2 * nodes + id] * dl;
+        }
+    }
+    for (int o = kLanesPerNode / 2; o > 0; o >>= 1)
+        for (int a = 0; a < 3; ++a) v[a] += __shfl_xor_sync(0xffffffffu, v[a], o, kLanesPerNode);
+    const bool have = valid && lane == 0;
+    if (have) {
         if (!ok) {
             atomicOr(&L.ctl->err, IBL_ERRBIT_WALL);
         } else {
-            const T *vel = static_cast<const T *>(L.vel);
-            const int nodes = L.nodes, nx = L.n[0], nxy = L.n[0] * L.n[1];
-            double v[3] = {0.0, 0.0, 0.0};
-            for (int c = 0; c < 4; ++c)
-                for (int b = 0; b < 4; ++b) {
-                    const int row = iy[b] * nx + iz[c] * nxy;
-                    for (int a = 0; a < 4; ++a) {
-                        const double dl = wx[a] * wy[b] * wz[c];
-                        const int id = row + ix[a];
-                        v[0] += (double)vel[id] * dl;
-                        v[1] += (double)vel[nodes + id] * dl;
-                        v[2] += (double)vel[2 * nodes + id] * dl;
-                    }
-                }
-            r[0] += v[0];
-            r[1] += v[1];
-            r[2] += v[2];
+            r[0] += (double)v[0];
+            r[1] += (double)v[1];
+            r[2] += (double)v[2];
             M.r[3 * i] = r[0];
             M.r[3 * i + 1] = r[1];
             M.r[3 * i + 2] = r[2];
         }
     }
-    // block min / max of the new positions
+    // block min / max of the new positions -> per-block partials; the last
+    // block reduces them (no contended atomics) and sets the next patch
     __shared__ double smn[3][4], smx[3][4];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __shared__ bool last;
+    const int wlane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int a = 0; a < 3; ++a) {
         double mn = have ? r[a] : 1e300, mx = have ? r[a] : -1e300;
         for (int o = 16; o > 0; o >>= 1) {
             mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
             mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         }
-        if (lane == 0) {
+        if (wlane == 0) {
             smn[a][warp] = mn;
             smx[a][warp] = mx;
         }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        const int nw = blockDim.x >> 5;
         for (int a = 0; a < 3; ++a) {
             double mn = smn[a][0], mx = smx[a][0];
             for (int w = 1; w < nw; ++w) {
                 mn = fmin(mn, smn[a][w]);
                 mx = fmax(mx, smx[a][w]);
             }
-            atomicMin(&L.ctl->key_min[a], dkey(mn));
-            atomicMax(&L.ctl->key_max[a], dkey(mx));
+            M.part[6 * blockIdx.x + a] = mn;
+            M.part[6 * blockIdx.x + 3 + a] = mx;
         }
         __threadfence();
         const unsigned t = atomicAdd(&L.ctl->ib_blocks_done, 1u);
-        if (t == gridDim.x - 1) {
-            __threadfence();
-            double mn[3], mx[3];
-            for (int a = 0; a < 3; ++a) {
-                mn[a] = dkey_inv(*(volatile unsigned long long *)&L.ctl->key_min[a]);
-                mx[a] = dkey_inv(*(volatile unsigned long long *)&L.ctl->key_max[a]);
-                L.ctl->key_min[a] = ~0ull;
-                L.ctl->key_max[a] = 0ull;
-            }
-            write_patch(L, mn, mx);
-            L.ctl->ib_blocks_done = 0u;
-            __threadfence();
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x)
+        for (int a = 0; a < 3; ++a) {
+            mn[a] = fmin(mn[a], __ldcg(M.part + 6 * k + a));
+            mx[a] = fmax(mx[a], __ldcg(M.part + 6 * k + 3 + a));
         }
+    __syncthreads();
+    for (int a = 0; a < 3; ++a) {
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[a] = fmin(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
+            mx[a] = fmax(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
+        }
+        if (wlane == 0) {
+            smn[a][warp] = mn[a];
+            smx[a][warp] = mx[a];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int a = 0; a < 3; ++a) {
+            for (int w = 1; w < nw; ++w) {
+                smn[a][0] = fmin(smn[a][0], smn[a][w]);
+                smx[a][0] = fmax(smx[a][0], smx[a][w]);
+            }
+            mn[a] = smn[a][0];
+            mx[a] = smx[a][0];
+        }
+        write_patch(L, mn, mx);
+        L.ctl->step += 1;  // the interpolation kernel closes the step
+        L.ctl->ib_blocks_done = 0u;
+        __threadfence();
     }
 }
 
@@ -906,32 +954,47 @@ cudaError_t launch_init(const LbView &L, cudaStream_t s)
     return cudaGetLastError();
 }
 
+static void lattice_grid(const LbView &L, dim3 &grid, dim3 &block)
+{
+    const int bx = L.n[0] >= 128 ? 128 : ((L.n[0] + 31) / 32) * 32;
+    const int by = 256 / bx;
+    block = dim3(bx, by, 1);
+    grid = dim3((L.n[0] + bx - 1) / bx, (L.n[1] + by - 1) / by, L.n[2]);
+}
+
 cudaError_t launch_lattice(const LbView &L, bool odd, bool record, cudaStream_t s)
 {
-    const unsigned g = blocks_for(L.nodes, 256);
+    dim3 g, b;
+    lattice_grid(L, g, b);
     if (L.precision == IBL_FP64) {
         if (odd) {
-            if (record) k_lattice<double, true, true><<<g, 256, 0, s>>>(L);
-            else k_lattice<double, true, false><<<g, 256, 0, s>>>(L);
+            if (record) k_lattice<double, true, true><<<g, b, 0, s>>>(L);
+            else k_lattice<double, true, false><<<g, b, 0, s>>>(L);
         } else {
-            if (record) k_lattice<double, false, true><<<g, 256, 0, s>>>(L);
-            else k_lattice<double, false, false><<<g, 256, 0, s>>>(L);
+            if (record) k_lattice<double, false, true><<<g, b, 0, s>>>(L);
+            else k_lattice<double, false, false><<<g, b, 0, s>>>(L);
         }
     } else {
         if (odd) {
-            if (record) k_lattice<float, true, true><<<g, 256, 0, s>>>(L);
-            else k_lattice<float, true, false><<<g, 256, 0, s>>>(L);
+            if (record) k_lattice<float, true, true><<<g, b, 0, s>>>(L);
+            else k_lattice<float, true, false><<<g, b, 0, s>>>(L);
         } else {
-            if (record) k_lattice<float, false, true><<<g, 256, 0, s>>>(L);
-            else k_lattice<float, false, false><<<g, 256, 0, s>>>(L);
+            if (record) k_lattice<float, false, true><<<g, b, 0, s>>>(L);
+            else k_lattice<float, false, false><<<g, b, 0, s>>>(L);
         }
     }
     return cudaGetLastError();
 }
 
+cudaError_t launch_advance(const LbView &L, cudaStream_t s)
+{
+    k_advance<<<1, 1, 0, s>>>(L.ctl);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_spread(const LbView &L, const MeshView &M, cudaStream_t s)
 {
-    const unsigned g = blocks_for(M.nv, 128);
+    const unsigned g = blocks_for((long long)M.nv * kLanesPerNode, 128);
     if (L.precision == IBL_FP64) k_spread<double><<<g, 128, 0, s>>>(L, M);
     else k_spread<float><<<g, 128, 0, s>>>(L, M);
     return cudaGetLastError();
@@ -939,7 +1002,7 @@ cudaError_t launch_spread(const LbView &L, const MeshView &M, cudaStream_t s)
 
 cudaError_t launch_interp(const LbView &L, const MeshView &M, cudaStream_t s)
 {
-    const unsigned g = blocks_for(M.nv, 128);
+    const unsigned g = blocks_for((long long)M.nv * kLanesPerNode, 128);
     if (L.precision == IBL_FP64) k_interp<double><<<g, 128, 0, s>>>(L, M);
     else k_interp<float><<<g, 128, 0, s>>>(L, M);
     return cudaGetLastError();

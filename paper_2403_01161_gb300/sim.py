@@ -151,6 +151,10 @@ class Sim:
     def step(self, n: int = 1):
         L.check(self.lib.ibl_step(self.h, int(n)))
 
+    def set_graphs(self, enable: bool):
+        """Replay whole chunks of steps as a captured CUDA graph (default on)."""
+        L.check(self.lib.ibl_set_graphs(self.h, 1 if enable else 0))
+
     def step_record(self):
         L.check(self.lib.ibl_step_record(self.h))
 
@@ -227,8 +231,10 @@ class Sim:
         return [out[k].as_dict() for k in range(fr.shape[0])]
 
     # ---- timing --------------------------------------------------------------
-    def profile(self, enable: bool):
-        L.check(self.lib.ibl_profile_enable(self.h, 1 if enable else 0))
+    def profile(self, enable, mask: int = 7):
+        """Time kernels with CUDA events (mask bit 0 lattice, 1 spread, 2 interpolation;
+        bit 3: only launches inside replayed graph chunks)."""
+        L.check(self.lib.ibl_profile_enable(self.h, mask if enable else 0))
 
     def profile_read(self):
         ms = np.zeros(3)
