@@ -235,13 +235,15 @@ int ibl_velocity_set(int32_t *c, double *w);
  * kernels bracketed by an event pair at every launch: bit 0 the lattice
  * kernel, bit 1 the force/spread kernel, bit 2 the interpolation kernel (0
  * turns timing off and clears it); bit 3 restricts timing to the launches
- * inside captured graph chunks.  ibl_profile_read synchronises and
+ * inside captured graph chunks.  Only one launch in `every` of each kernel
+ * is bracketed (1 = all), so that sparse sampling keeps the event overhead
+ * out of the step time.  ibl_profile_read synchronises and
  * returns the summed durations (ms) and launch counts [lattice, spread,
  * interpolate] since enabling.  At most 65536 launches are recorded.  With
  * graph replay the event pairs are nodes of the captured chunk, so each
  * replay re-records them: the read covers the eager launches and the last
  * replay of the chunk. */
-int ibl_profile_enable(ibl_lb *lb, int mask);
+int ibl_profile_enable(ibl_lb *lb, int mask, int every);
 int ibl_profile_read(ibl_lb *lb, double ms[3], long long launches[3]);
 
 const char *ibl_last_error(void);

@@ -81,7 +81,7 @@ SIGNATURES = [
     ("ibl_regularize_now", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     ("ibl_run_frames", ctypes.c_int, [_P, _P, _D, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Observables)]),
     ("ibl_velocity_set", ctypes.c_int, [_I32, _D]),
-    ("ibl_profile_enable", ctypes.c_int, [_P, ctypes.c_int]),
+    ("ibl_profile_enable", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
     ("ibl_profile_read", ctypes.c_int, [_P, _D, ctypes.POINTER(ctypes.c_longlong)]),
     ("ibl_last_error", ctypes.c_char_p, []),
 ]

@@ -36,7 +36,7 @@ int cuda_fail(cudaError_t e, const char *what)
 inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
 struct Layout {
-    size_t ctl = 0, frames = 0, f = 0, force = 0, vel = 0, rec = 0, total = 0;
+    size_t ctl = 0, frames = 0, frames_t = 0, f = 0, force = 0, vel = 0, rec = 0, total = 0;
 };
 
 long long pop_stride(long long nodes) { return (nodes + 63) / 64 * 64; }
@@ -59,6 +59,7 @@ bool lb_layout(const ibl_lb_params *p, int n_frames, Layout &L)
     };
     L.ctl = take(sizeof(Ctl));
     L.frames = take(sizeof(double) * 9 * (size_t)n_frames);
+    L.frames_t = take(es * 9 * (size_t)n_frames);
     L.f = take(es * 19 * (size_t)pop_stride(nodes));
     L.force = take(es * 3 * (size_t)nodes);
     L.vel = take(es * 3 * (size_t)nodes);
@@ -69,7 +70,7 @@ bool lb_layout(const ibl_lb_params *p, int n_frames, Layout &L)
 
 struct MeshLayout {
     size_t r = 0, fn = 0, tris = 0, n2t_ptr = 0, n2t = 0, nb_ptr = 0, nb_idx = 0, s0 = 0, s1 = 0, s2 = 0,
-           part = 0, ring = 0, total = 0;
+           part = 0, obs_part = 0, ring = 0, total = 0;
 };
 
 bool mesh_layout(int nv, int nt, MeshLayout &L)
@@ -92,6 +93,7 @@ bool mesh_layout(int nv, int nt, MeshLayout &L)
     L.s1 = take(sizeof(double) * 3 * nv);
     L.s2 = take(sizeof(double) * 3 * nv);
     L.part = take(sizeof(double) * 6 * (((size_t)nv + 7) / 8 + 1));  // one row per interpolation block
+    L.obs_part = take(sizeof(double) * 11 * iblb::kObsBlocksMax);
     L.ring = take(sizeof(ibl_observables) * iblb::kRingCap);
     L.total = off;
     return true;
@@ -101,6 +103,8 @@ enum { PROF_LB = 0, PROF_SPREAD = 1, PROF_INTERP = 2 };
 
 struct Profiler {
     int mask = 0;
+    int every = 1;        // bracket one launch in `every`
+    long long seen[3] = {0, 0, 0};
     std::vector<cudaEvent_t> pool;
     std::vector<std::pair<int, int>> marks;  // (kind, first event index)
     size_t used = 0;
@@ -119,6 +123,7 @@ struct Profiler {
     {
         used = 0;
         marks.clear();
+        seen[0] = seen[1] = seen[2] = 0;
     }
     ~Profiler()
     {
@@ -184,18 +189,23 @@ int prof_begin(ibl_lb *lb, int kind)
 {
     if (!((lb->prof.mask >> kind) & 1) || lb->prof.marks.size() >= Profiler::kMax) return -1;
     if ((lb->prof.mask & 8) && !lb->capturing) return -1;  // graph replays only
+    if (lb->prof.seen[kind]++ % lb->prof.every != 0) return -1;
     cudaEvent_t a = lb->prof.take();
     cudaEvent_t b = lb->prof.take();
     if (!a || !b) return -1;
     const int idx = (int)lb->prof.used - 2;
     lb->prof.marks.push_back({kind, idx});
-    cudaEventRecord(a, lb->stream);
+    // inside a capture the record must become a graph node of its own
+    if (lb->capturing) cudaEventRecordWithFlags(a, lb->stream, cudaEventRecordExternal);
+    else cudaEventRecord(a, lb->stream);
     return idx + 1;
 }
 
 void prof_end(ibl_lb *lb, int end_idx)
 {
-    if (end_idx >= 0) cudaEventRecord(lb->prof.pool[end_idx], lb->stream);
+    if (end_idx < 0) return;
+    if (lb->capturing) cudaEventRecordWithFlags(lb->prof.pool[end_idx], lb->stream, cudaEventRecordExternal);
+    else cudaEventRecord(lb->prof.pool[end_idx], lb->stream);
 }
 
 int one_step(ibl_lb *lb, bool record)
@@ -403,6 +413,7 @@ int mesh_attach(ibl_lb *lb, int nv, const double *r, int nt, const int *tri_in, 
     m->v.s1 = reinterpret_cast<double *>(w + L.s1);
     m->v.s2 = reinterpret_cast<double *>(w + L.s2);
     m->v.part = reinterpret_cast<double *>(w + L.part);
+    m->v.obs_part = reinterpret_cast<double *>(w + L.obs_part);
     m->v.ring = reinterpret_cast<ibl_observables *>(w + L.ring);
     m->v.ring_cap = iblb::kRingCap;
     m->tris = tri;
@@ -552,11 +563,13 @@ int ibl_lb_create(const ibl_lb_params *p, const double *A_frames, int n_frames, 
     v.precision = p->precision;
     v.rule = p->edge_rule;
     v.omega = 1.0 / p->tau;
+    v.omega_f = (float)(1.0 / p->tau);
     v.f = lb->ws + L.f;
     v.force = lb->ws + L.force;
     v.vel = lb->ws + L.vel;
     v.rec = p->record_fields ? lb->ws + L.rec : nullptr;
     v.frames = reinterpret_cast<const double *>(lb->ws + L.frames);
+    v.frames_t = lb->ws + L.frames_t;
     v.n_frames = n_frames;
     v.n_hold = steps_per_frame;
     v.ctl = reinterpret_cast<Ctl *>(lb->ws + L.ctl);
@@ -571,6 +584,7 @@ int ibl_lb_create(const ibl_lb_params *p, const double *A_frames, int n_frames, 
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(lb->ws + L.frames, A_frames, sizeof(double) * 9 * n_frames, cudaMemcpyHostToDevice,
                             lb->stream);
+    if (e == cudaSuccess) e = iblb::launch_convert_frames(v, 0, n_frames, lb->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(v.force, 0, es * 3 * nodes, lb->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(v.vel, 0, es * 3 * nodes, lb->stream);
     if (e == cudaSuccess && v.rec) e = cudaMemsetAsync(v.rec, 0, es * 7 * nodes, lb->stream);
@@ -601,6 +615,7 @@ int ibl_set_frame(ibl_lb *lb, int k, const double *A)
         if (!std::isfinite(A[i])) return fail(IBL_EINVAL, "non-finite velocity gradient");
     cudaError_t e = cudaMemcpyAsync(lb->ws + lb->lay.frames + sizeof(double) * 9 * (size_t)k, A, sizeof(double) * 9,
                                     cudaMemcpyHostToDevice, lb->stream);
+    if (e == cudaSuccess) e = iblb::launch_convert_frames(lb->v, k, k + 1, lb->stream);
     if (e != cudaSuccess) return cuda_fail(e, "frame upload");
     return IBL_OK;
 }
@@ -928,13 +943,14 @@ int ibl_run_frames(ibl_lb *lb, ibl_mesh *m, const double *A_frames, int n_frames
     return IBL_OK;
 }
 
-int ibl_profile_enable(ibl_lb *lb, int mask)
+int ibl_profile_enable(ibl_lb *lb, int mask, int every)
 {
-    if (!lb || mask < 0 || mask > 15) return fail(IBL_EINVAL, "bad profiling mask");
+    if (!lb || mask < 0 || mask > 15 || every < 1) return fail(IBL_EINVAL, "bad profiling mask or stride");
     cudaStreamSynchronize(lb->stream);
     drop_graph(lb);  // a captured chunk may hold event nodes of the pool
     lb->prof.clear();
     lb->prof.mask = mask;
+    lb->prof.every = every;
     return IBL_OK;
 }
 

@@ -14,12 +14,12 @@ namespace iblb {
 // Device control block of one lattice (lives in the lattice workspace).
 struct alignas(128) Ctl {
     long long step;              // steps completed (advanced by the lattice kernel)
-    unsigned int lb_blocks_done; // unused
+    unsigned int obs_blocks_done; // last-block ticket of the shape-record kernel
     unsigned int ib_blocks_done; // last-block ticket of the interpolation kernel
     int err;                     // IBL_ERRBIT_* (sticky)
     int reg_iters;               // iterations of the latest regularisation
     int n_records;               // shape records written
-    int pad0;
+    int frame;                   // frame index applied by the next step
     int patch_lo[4];             // droplet patch: lower corner (normalised into the box)
     int patch_ext[4];            // extent (hi - lo), -1 = empty
     unsigned long long pad1[8];
@@ -34,11 +34,13 @@ struct LbView {
     int precision;      // IBL_FP32_DEV / IBL_FP64
     int rule;           // IBL_EDGE_*
     double omega;       // 1 / tau
+    float omega_f;
     void *f;            // [19][qs]
     void *force;        // [3][nodes]
     void *vel;          // [3][nodes]
     void *rec;          // [7][nodes] or null: drho, u, F
     const double *frames;
+    const void *frames_t;  // the frames in the storage precision
     int n_frames;
     int n_hold;
     Ctl *ctl;
@@ -56,6 +58,7 @@ struct MeshView {
     const int *nb_idx;  // [3 nt]
     double *s0, *s1, *s2;  // regularisation scratch, [nv][3] each
     double *part;          // per-block bounding-box partials of the interpolation kernel, [blocks][6]
+    double *obs_part;      // per-block partial sums of the shape-record kernel, [kObsBlocksMax][11]
     ibl_observables *ring;
     int ring_cap;
 };
@@ -67,10 +70,12 @@ struct RegParams {
 };
 
 constexpr int kRingCap = 4096;
+constexpr int kObsBlocksMax = 304;
 
 cudaError_t launch_init(const LbView &L, cudaStream_t s);
 cudaError_t launch_lattice(const LbView &L, bool odd, bool record, cudaStream_t s);
 cudaError_t launch_advance(const LbView &L, cudaStream_t s);
+cudaError_t launch_convert_frames(const LbView &L, int k0, int k1, cudaStream_t s);
 cudaError_t launch_spread(const LbView &L, const MeshView &M, cudaStream_t s);
 cudaError_t launch_interp(const LbView &L, const MeshView &M, cudaStream_t s);
 cudaError_t launch_regularize(const LbView &L, const MeshView &M, const RegParams &p, cudaStream_t s);

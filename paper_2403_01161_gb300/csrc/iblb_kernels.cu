@@ -181,7 +181,7 @@ __device__ __forceinline__ void bc_apply(T (&f)[19], const T (&uw)[3], int rule)
 }
 
 template <typename T>
-__device__ __noinline__ void bc_dispatch(T (&f)[19], const T (&uw)[3], int rule, int code)
+__device__ __forceinline__ void bc_dispatch(T (&f)[19], const T (&uw)[3], int rule, int code)
 {
 #define IBL_BC_CASE(a, b, c)                              \
     case (a + 1) + 3 * (b + 1) + 9 * (c + 1):             \
@@ -198,26 +198,6 @@ __device__ __noinline__ void bc_dispatch(T (&f)[19], const T (&uw)[3], int rule,
         default: break;
     }
 #undef IBL_BC_CASE
-}
-
-__device__ __forceinline__ const double *frame_ptr(const LbView &L, long long step)
-{
-    long long k = step / L.n_hold;
-    if (k > L.n_frames - 1) k = L.n_frames - 1;
-    return L.frames + 9 * k;
-}
-
-// Neighbour coordinate along one axis: x + d (d in {-1,0,1}); periodic axes
-// wrap, Zou-He axes return -1 outside the box.
-__device__ __forceinline__ int step_coord(int x, int d, int n, bool periodic)
-{
-    int y = x + d;
-    if (periodic) {
-        if (y < 0) y += n;
-        else if (y >= n) y -= n;
-        return y;
-    }
-    return (y < 0 || y >= n) ? -1 : y;
 }
 
 // ---------------------------------------------------------------------------
@@ -280,10 +260,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_lattice(LbView 
 
         if (sx | sy | sz) {
             // Eq. (velo_facce_cubo_da_gradiente) in the storage precision
-            const double *A = frame_ptr(L, L.ctl->step);
+            const T *A = static_cast<const T *>(L.frames_t) + 9 * L.ctl->frame;
             const T lx = T(x) - T(0.5) * T(nx - 1), ly = T(y) - T(0.5) * T(ny - 1), lz = T(z) - T(0.5) * T(nz - 1);
-            const T uw[3] = {T(A[0]) * lx + T(A[1]) * ly + T(A[2]) * lz, T(A[3]) * lx + T(A[4]) * ly + T(A[5]) * lz,
-                             T(A[6]) * lx + T(A[7]) * ly + T(A[8]) * lz};
+            const T uw[3] = {A[0] * lx + A[1] * ly + A[2] * lz, A[3] * lx + A[4] * ly + A[5] * lz,
+                             A[6] * lx + A[7] * ly + A[8] * lz};
             bc_dispatch<T>(g, uw, L.rule, (sx + 1) + 3 * (sy + 1) + 9 * (sz + 1));
         }
 
@@ -295,8 +275,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_lattice(LbView 
             if (px && dx < 0) dx += nx;
             if (py && dy < 0) dy += ny;
             if (pz && dz < 0) dz += nz;
-            in_patch = (unsigned)dx <= (unsigned)c->patch_ext[0] && (unsigned)dy <= (unsigned)c->patch_ext[1] &&
-                       (unsigned)dz <= (unsigned)c->patch_ext[2];
+            // an empty patch has extent -1: no node is inside
+            in_patch = c->patch_ext[0] >= 0 && (unsigned)dx <= (unsigned)c->patch_ext[0] &&
+                       (unsigned)dy <= (unsigned)c->patch_ext[1] && (unsigned)dz <= (unsigned)c->patch_ext[2];
         }
         T Fx = T(0), Fy = T(0), Fz = T(0);
         T *__restrict__ force = static_cast<T *>(L.force);
@@ -323,7 +304,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_lattice(LbView 
         const T ux = (jx + T(0.5) * Fx) * ir, uy = (jy + T(0.5) * Fy) * ir, uz = (jz + T(0.5) * Fz) * ir;
         const T uu = ux * ux + uy * uy + uz * uz;
         bad = !(uu <= T(0.09)) || !(drho == drho);
-        const T om = T(L.omega);
+        const T om = sizeof(T) == 4 ? T(L.omega_f) : T(L.omega);
         const T fpre = T(1) - T(0.5) * om;
         const T uF = ux * Fx + uy * Fy + uz * Fz;
         const T base = T(1.5) * uu;
@@ -389,7 +370,15 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_lattice(LbView 
 }
 
 // Advances the step counter when no droplet kernel follows the lattice kernel.
-__global__ void k_advance(Ctl *ctl) { ctl->step += 1; }
+__device__ __forceinline__ void close_step(const LbView &L)
+{
+    const long long s = L.ctl->step + 1;
+    L.ctl->step = s;
+    const long long k = s / L.n_hold;
+    L.ctl->frame = (int)(k < L.n_frames - 1 ? k : L.n_frames - 1);
+}
+
+__global__ void k_advance(LbView L) { close_step(L); }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_init(LbView L)
@@ -458,6 +447,45 @@ __device__ __forceinline__ int wrap_index(int g, int n, bool periodic)
 
 constexpr int kLanesPerNode = 16;  // lane = (b, c) row of the 4x4x4 stencil
 
+// Per-node stencil of the 16-lane group: lanes 0..2 compute, in FP64, the
+// origin base_a = floor(r_a) - 1 and the exact fraction r_a - floor(r_a) of
+// axis a, and every lane receives all three by shuffles.  The offset of
+// stencil point k is then frac + (1 - k), the correctly rounded r - (base+k).
+struct NodeStencil {
+    int base[3];
+    double frac[3];
+    bool ok;
+};
+__device__ __forceinline__ NodeStencil node_stencil(const LbView &L, const double *r, int lane)
+{
+    double ra = 0.0, fr = 0.0;
+    int base = 0;
+    bool ok = true;
+    if (lane < 3) {
+        ra = r[lane];
+        // select by value: indexing the parameter arrays with a runtime lane
+        // would copy the kernel parameters to local memory
+        const int na = lane == 0 ? L.n[0] : (lane == 1 ? L.n[1] : L.n[2]);
+        const int bca = lane == 0 ? L.bc[0] : (lane == 1 ? L.bc[1] : L.bc[2]);
+        const AxisStencil A = axis_stencil(ra, na, bca == IBL_BC_PERIODIC);
+        ok = A.ok;
+        base = A.base;
+        fr = ok ? ra - floor(ra) : 0.0;
+    }
+    const int w0 = (threadIdx.x & 31) & ~(kLanesPerNode - 1);
+    NodeStencil S;
+    S.ok = true;
+    // every lane executes every full-mask shuffle (no short-circuit around
+    // them: a lane that skipped one would leave the others waiting)
+    for (int a = 0; a < 3; ++a) {
+        S.base[a] = __shfl_sync(0xffffffffu, base, w0 + a);
+        S.frac[a] = __shfl_sync(0xffffffffu, fr, w0 + a);
+        const int ok_a = __shfl_sync(0xffffffffu, ok ? 1 : 0, w0 + a);
+        S.ok = S.ok && (ok_a != 0);
+    }
+    return S;
+}
+
 // Nodal force F_i = -sigma dA/dx_i (Eq. (pi_drop)) gathered over the
 // triangles around node i, then spread with the 4-point delta
 // (Eq. (ibm_force_d)(a)) by atomic adds into the Eulerian force.  Sixteen
@@ -497,29 +525,28 @@ __global__ void __launch_bounds__(128) k_spread(LbView L, MeshView M)
         M.fn[3 * i + 1] = F[1];
         M.fn[3 * i + 2] = F[2];
     }
-    const double r0 = M.r[3 * i], r1 = M.r[3 * i + 1], r2 = M.r[3 * i + 2];
-    const bool perx = L.bc[0] == IBL_BC_PERIODIC, pery = L.bc[1] == IBL_BC_PERIODIC,
-               perz = L.bc[2] == IBL_BC_PERIODIC;
-    const AxisStencil ax = axis_stencil(r0, L.n[0], perx), ay = axis_stencil(r1, L.n[1], pery),
-                      az = axis_stencil(r2, L.n[2], perz);
+    const NodeStencil S = node_stencil(L, M.r + 3 * i, lane);
     if (!valid) return;
-    if (!(ax.ok && ay.ok && az.ok)) {
+    if (!S.ok) {
         if (lane == 0) atomicOr(&L.ctl->err, IBL_ERRBIT_WALL);
         return;
     }
-    // weights in the storage precision (the offsets r - x are formed in FP64)
+    const bool perx = L.bc[0] == IBL_BC_PERIODIC, pery = L.bc[1] == IBL_BC_PERIODIC,
+               perz = L.bc[2] == IBL_BC_PERIODIC;
+    // weights in the storage precision
     const int b = lane & 3, c = lane >> 2;
-    const T wy = peskin_phi<T>(T(r1 - (double)(ay.base + b)));
-    const T wz = peskin_phi<T>(T(r2 - (double)(az.base + c)));
+    const T wy = peskin_phi<T>(T(S.frac[1] + (double)(1 - b)));
+    const T wz = peskin_phi<T>(T(S.frac[2] + (double)(1 - c)));
     const int nx = L.n[0], nxy = L.n[0] * L.n[1], nodes = L.nodes;
-    const int row = wrap_index(ay.base + b, L.n[1], pery) * nx + wrap_index(az.base + c, L.n[2], perz) * nxy;
+    const int row = wrap_index(S.base[1] + b, L.n[1], pery) * nx + wrap_index(S.base[2] + c, L.n[2], perz) * nxy;
     T *force = static_cast<T *>(L.force);
     const T Fx = T(F[0]), Fy = T(F[1]), Fz = T(F[2]);
+    const T fx = T(S.frac[0]);
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-        const T wx = peskin_phi<T>(T(r0 - (double)(ax.base + a)));
+        const T wx = sizeof(T) == 8 ? peskin_phi<T>(T(S.frac[0] + (double)(1 - a))) : peskin_phi<T>(fx + T(1 - a));
         const T dl = wx * wy * wz;
-        const int id = row + wrap_index(ax.base + a, nx, perx);
+        const int id = row + wrap_index(S.base[0] + a, nx, perx);
         atomicAdd(force + id, Fx * dl);
         atomicAdd(force + nodes + id, Fy * dl);
         atomicAdd(force + 2 * nodes + id, Fz * dl);
@@ -570,25 +597,25 @@ __global__ void __launch_bounds__(128) k_interp(LbView L, MeshView M)
     const int lane = threadIdx.x % kLanesPerNode;
     const bool valid = gid < M.nv;
     const int i = valid ? gid : M.nv - 1;
-    double r[3] = {M.r[3 * i], M.r[3 * i + 1], M.r[3 * i + 2]};
-    const bool perx = L.bc[0] == IBL_BC_PERIODIC, pery = L.bc[1] == IBL_BC_PERIODIC,
-               perz = L.bc[2] == IBL_BC_PERIODIC;
-    const AxisStencil ax = axis_stencil(r[0], L.n[0], perx), ay = axis_stencil(r[1], L.n[1], pery),
-                      az = axis_stencil(r[2], L.n[2], perz);
-    const bool ok = ax.ok && ay.ok && az.ok;
+    const NodeStencil S = node_stencil(L, M.r + 3 * i, lane);
     T v[3] = {T(0), T(0), T(0)};
-    if (ok) {
+    if (S.ok) {
+        const bool perx = L.bc[0] == IBL_BC_PERIODIC, pery = L.bc[1] == IBL_BC_PERIODIC,
+                   perz = L.bc[2] == IBL_BC_PERIODIC;
         const int b = lane & 3, c = lane >> 2;
-        const T wy = peskin_phi<T>(T(r[1] - (double)(ay.base + b)));
-        const T wz = peskin_phi<T>(T(r[2] - (double)(az.base + c)));
+        const T wy = peskin_phi<T>(T(S.frac[1] + (double)(1 - b)));
+        const T wz = peskin_phi<T>(T(S.frac[2] + (double)(1 - c)));
         const int nx = L.n[0], nxy = L.n[0] * L.n[1], nodes = L.nodes;
-        const int row = wrap_index(ay.base + b, L.n[1], pery) * nx + wrap_index(az.base + c, L.n[2], perz) * nxy;
+        const int row =
+            wrap_index(S.base[1] + b, L.n[1], pery) * nx + wrap_index(S.base[2] + c, L.n[2], perz) * nxy;
         const T *vel = static_cast<const T *>(L.vel);
+        const T fx = T(S.frac[0]);
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
-            const T wx = peskin_phi<T>(T(r[0] - (double)(ax.base + a)));
+            const T wx =
+                sizeof(T) == 8 ? peskin_phi<T>(T(S.frac[0] + (double)(1 - a))) : peskin_phi<T>(fx + T(1 - a));
             const T dl = wx * wy * wz;
-            const int id = row + wrap_index(ax.base + a, nx, perx);
+            const int id = row + wrap_index(S.base[0] + a, nx, perx);
             v[0] += vel[id] * dl;
             v[1] += vel[nodes + id] * dl;
             v[2] += vel[2 * nodes + id] * dl;
@@ -597,8 +624,12 @@ __global__ void __launch_bounds__(128) k_interp(LbView L, MeshView M)
     for (int o = kLanesPerNode / 2; o > 0; o >>= 1)
         for (int a = 0; a < 3; ++a) v[a] += __shfl_xor_sync(0xffffffffu, v[a], o, kLanesPerNode);
     const bool have = valid && lane == 0;
+    double r[3] = {0.0, 0.0, 0.0};
     if (have) {
-        if (!ok) {
+        r[0] = M.r[3 * i];
+        r[1] = M.r[3 * i + 1];
+        r[2] = M.r[3 * i + 2];
+        if (!S.ok) {
             atomicOr(&L.ctl->err, IBL_ERRBIT_WALL);
         } else {
             r[0] += (double)v[0];
@@ -615,11 +646,10 @@ __global__ void __launch_bounds__(128) k_interp(LbView L, MeshView M)
     __shared__ bool last;
     const int wlane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int a = 0; a < 3; ++a) {
+        // lanes 0 and 16 hold the warp's two nodes
         double mn = have ? r[a] : 1e300, mx = have ? r[a] : -1e300;
-        for (int o = 16; o > 0; o >>= 1) {
-            mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-            mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        }
+        mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, 16));
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
         if (wlane == 0) {
             smn[a][warp] = mn;
             smx[a][warp] = mx;
@@ -671,7 +701,7 @@ __global__ void __launch_bounds__(128) k_interp(LbView L, MeshView M)
             mx[a] = smx[a][0];
         }
         write_patch(L, mn, mx);
-        L.ctl->step += 1;  // the interpolation kernel closes the step
+        close_step(L);  // the interpolation kernel closes the step
         L.ctl->ib_blocks_done = 0u;
         __threadfence();
     }
@@ -839,18 +869,16 @@ __device__ void jacobi3(double a[3][3], double lam[3], double v[3][3])
 // Shape record (Sec. 2): enclosed volume, centroid and second moment by
 // signed tetrahedra (ref, a, b, c), S = (5/V) M, eigen-decomposition, Taylor
 // D and beta of Eq. (beta).  One block.
-__global__ void __launch_bounds__(512) k_observables(LbView L, MeshView M)
+__global__ void __launch_bounds__(256) k_observables(LbView L, MeshView M)
 {
-    __shared__ double sh3[16][3];
-    __shared__ double sh11[16][11];
-    double ref[3] = {0.0, 0.0, 0.0};
-    for (int i = threadIdx.x; i < M.nv; i += blockDim.x)
-        for (int a = 0; a < 3; ++a) ref[a] += M.r[3 * i + a];
-    block_sum<3>(ref, sh3);
-    for (int a = 0; a < 3; ++a) ref[a] /= M.nv;
+    __shared__ double sh11[8][11];
+    __shared__ bool last;
+    // volume integrals relative to node 0 (any point near the droplet will
+    // do; this one needs no prior reduction)
+    const double ref[3] = {M.r[0], M.r[1], M.r[2]};
     double acc[11];
     for (int k = 0; k < 11; ++k) acc[k] = 0.0;
-    for (int t = threadIdx.x; t < M.nt; t += blockDim.x) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < M.nt; t += gridDim.x * blockDim.x) {
         double p[3][3];
         for (int v = 0; v < 3; ++v) {
             const int id = M.tris[3 * t + v];
@@ -880,8 +908,21 @@ __global__ void __launch_bounds__(512) k_observables(LbView L, MeshView M)
         cross3(e1, e2, nn);
         acc[10] += 0.5 * sqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
     }
+    // per-block partial sums; the last block adds them in block order
     block_sum<11>(acc, sh11);
-    if (threadIdx.x != 0) return;
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 11; ++k) M.obs_part[11 * blockIdx.x + k] = acc[k];
+        __threadfence();
+        const unsigned t = atomicAdd(&L.ctl->obs_blocks_done, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    for (int k = 0; k < 11; ++k) acc[k] = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b)
+        for (int k = 0; k < 11; ++k) acc[k] += __ldcg(M.obs_part + 11 * b + k);
+    L.ctl->obs_blocks_done = 0u;
     const double V = acc[0];
     double xc[3];
     for (int a = 0; a < 3; ++a) xc[a] = acc[1 + a] / 4.0 / V;
@@ -986,9 +1027,24 @@ cudaError_t launch_lattice(const LbView &L, bool odd, bool record, cudaStream_t 
     return cudaGetLastError();
 }
 
+template <typename T>
+__global__ void k_convert_frames(LbView L, int k0, int k1)
+{
+    const int i = 9 * k0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < 9 * k1) static_cast<T *>(const_cast<void *>(L.frames_t))[i] = T(L.frames[i]);
+}
+
+cudaError_t launch_convert_frames(const LbView &L, int k0, int k1, cudaStream_t s)
+{
+    const unsigned g = blocks_for(9LL * (k1 - k0), 256);
+    if (L.precision == IBL_FP64) k_convert_frames<double><<<g, 256, 0, s>>>(L, k0, k1);
+    else k_convert_frames<float><<<g, 256, 0, s>>>(L, k0, k1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_advance(const LbView &L, cudaStream_t s)
 {
-    k_advance<<<1, 1, 0, s>>>(L.ctl);
+    k_advance<<<1, 1, 0, s>>>(L);
     return cudaGetLastError();
 }
 
@@ -1016,7 +1072,9 @@ cudaError_t launch_regularize(const LbView &L, const MeshView &M, const RegParam
 
 cudaError_t launch_observables(const LbView &L, const MeshView &M, cudaStream_t s)
 {
-    k_observables<<<1, 512, 0, s>>>(L, M);
+    int g = (M.nt + 255) / 256;
+    if (g > kObsBlocksMax) g = kObsBlocksMax;
+    k_observables<<<g, 256, 0, s>>>(L, M);
     return cudaGetLastError();
 }
 

@@ -231,10 +231,10 @@ class Sim:
         return [out[k].as_dict() for k in range(fr.shape[0])]
 
     # ---- timing --------------------------------------------------------------
-    def profile(self, enable, mask: int = 7):
+    def profile(self, enable, mask: int = 7, every: int = 1):
         """Time kernels with CUDA events (mask bit 0 lattice, 1 spread, 2 interpolation;
-        bit 3: only launches inside replayed graph chunks)."""
-        L.check(self.lib.ibl_profile_enable(self.h, mask if enable else 0))
+        bit 3: only launches inside replayed graph chunks), one launch in `every`."""
+        L.check(self.lib.ibl_profile_enable(self.h, mask if enable else 0, int(every)))
 
     def profile_read(self):
         ms = np.zeros(3)
