@@ -69,7 +69,7 @@ bool lb_layout(const ibl_lb_params *p, int n_frames, Layout &L)
 }
 
 struct MeshLayout {
-    size_t r = 0, fn = 0, tris = 0, n2t_ptr = 0, n2t = 0, nb_ptr = 0, nb_idx = 0, s0 = 0, s1 = 0, s2 = 0,
+    size_t r = 0, fn = 0, tn = 0, tris = 0, n2t_ptr = 0, n2t = 0, nb_ptr = 0, nb_idx = 0, s0 = 0, s1 = 0, s2 = 0,
            part = 0, obs_part = 0, ring = 0, total = 0;
 };
 
@@ -84,6 +84,7 @@ bool mesh_layout(int nv, int nt, MeshLayout &L)
     };
     L.r = take(sizeof(double) * 3 * nv);
     L.fn = take(sizeof(double) * 3 * nv);
+    L.tn = take(sizeof(double) * 3 * nt);
     L.tris = take(sizeof(int) * 3 * nt);
     L.n2t_ptr = take(sizeof(int) * (nv + 1));
     L.n2t = take(sizeof(int) * 3 * nt);
@@ -404,6 +405,7 @@ int mesh_attach(ibl_lb *lb, int nv, const double *r, int nt, const int *tri_in, 
     m->v.sigma = sigma;
     m->v.r = reinterpret_cast<double *>(w + L.r);
     m->v.fn = reinterpret_cast<double *>(w + L.fn);
+    m->v.tn = reinterpret_cast<double *>(w + L.tn);
     m->v.tris = reinterpret_cast<const int *>(w + L.tris);
     m->v.n2t_ptr = reinterpret_cast<const int *>(w + L.n2t_ptr);
     m->v.n2t = reinterpret_cast<const int *>(w + L.n2t);

@@ -15,7 +15,7 @@ namespace iblb {
 struct alignas(128) Ctl {
     long long step;              // steps completed (advanced by the lattice kernel)
     unsigned int obs_blocks_done; // last-block ticket of the shape-record kernel
-    unsigned int ib_blocks_done; // last-block ticket of the interpolation kernel
+    int n_part;                  // bounding-box rows left for the next force/spread kernel
     int err;                     // IBL_ERRBIT_* (sticky)
     int reg_iters;               // iterations of the latest regularisation
     int n_records;               // shape records written
@@ -51,6 +51,7 @@ struct MeshView {
     double sigma;
     double *r;          // [nv][3]
     double *fn;         // [nv][3] nodal forces of the last step
+    double *tn;         // [nt][3] scaled triangle normals of the last step
     const int *tris;    // [nt][3]
     const int *n2t_ptr; // [nv+1]
     const int *n2t;     // [3 nt] entries 3*t + slot

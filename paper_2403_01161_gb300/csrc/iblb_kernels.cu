@@ -486,75 +486,28 @@ __device__ __forceinline__ NodeStencil node_stencil(const LbView &L, const doubl
     return S;
 }
 
-// Nodal force F_i = -sigma dA/dx_i (Eq. (pi_drop)) gathered over the
-// triangles around node i, then spread with the 4-point delta
-// (Eq. (ibm_force_d)(a)) by atomic adds into the Eulerian force.  Sixteen
-// lanes per node: the lanes split the incident triangles (reduced with
-// shuffles), then each lane adds one x-row of four stencil points.
+// Weights of the lane's x-row (w[0..3]) and of its y and z rows, in the
+// storage precision: offsets frac + (1 - k); in FP32 the fraction is
+// rounded to float first, in FP64 the offsets are the correctly rounded
+// r - (base + k).
 template <typename T>
-__global__ void __launch_bounds__(128) k_spread(LbView L, MeshView M)
+__device__ __forceinline__ void stencil_weights(const NodeStencil &S, int b, int c, T w[4], T &wy, T &wz)
 {
-    const int gid = blockIdx.x * (blockDim.x / kLanesPerNode) + threadIdx.x / kLanesPerNode;
-    const int lane = threadIdx.x % kLanesPerNode;
-    const bool valid = gid < M.nv;
-    const int i = valid ? gid : M.nv - 1;
-    double F[3] = {0.0, 0.0, 0.0};
-    for (int k = M.n2t_ptr[i] + lane; k < M.n2t_ptr[i + 1]; k += kLanesPerNode) {
-        const int e = M.n2t[k];
-        const int t = e / 3, slot = e - 3 * t;
-        const int v0 = M.tris[3 * t], v1 = M.tris[3 * t + 1], v2 = M.tris[3 * t + 2];
-        const double x0[3] = {M.r[3 * v0], M.r[3 * v0 + 1], M.r[3 * v0 + 2]};
-        const double x1[3] = {M.r[3 * v1], M.r[3 * v1 + 1], M.r[3 * v1 + 2]};
-        const double x2[3] = {M.r[3 * v2], M.r[3 * v2 + 1], M.r[3 * v2 + 2]};
-        double e1[3], e2[3], N[3];
-        for (int a = 0; a < 3; ++a) { e1[a] = x1[a] - x0[a]; e2[a] = x2[a] - x0[a]; }
-        cross3(e1, e2, N);
-        const double len = sqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
-        const double n[3] = {N[0] / len, N[1] / len, N[2] / len};
-        const double *xp = slot == 0 ? x1 : (slot == 1 ? x2 : x0);
-        const double *xm = slot == 0 ? x2 : (slot == 1 ? x0 : x1);
-        const double d[3] = {xm[0] - xp[0], xm[1] - xp[1], xm[2] - xp[2]};
-        double g[3];
-        cross3(n, d, g);
-        for (int a = 0; a < 3; ++a) F[a] += -M.sigma * 0.5 * g[a];
-    }
-    for (int o = kLanesPerNode / 2; o > 0; o >>= 1)
-        for (int a = 0; a < 3; ++a) F[a] += __shfl_xor_sync(0xffffffffu, F[a], o, kLanesPerNode);
-    if (valid && lane == 0) {
-        M.fn[3 * i] = F[0];
-        M.fn[3 * i + 1] = F[1];
-        M.fn[3 * i + 2] = F[2];
-    }
-    const NodeStencil S = node_stencil(L, M.r + 3 * i, lane);
-    if (!valid) return;
-    if (!S.ok) {
-        if (lane == 0) atomicOr(&L.ctl->err, IBL_ERRBIT_WALL);
-        return;
-    }
-    const bool perx = L.bc[0] == IBL_BC_PERIODIC, pery = L.bc[1] == IBL_BC_PERIODIC,
-               perz = L.bc[2] == IBL_BC_PERIODIC;
-    // weights in the storage precision
-    const int b = lane & 3, c = lane >> 2;
-    const T wy = peskin_phi<T>(T(S.frac[1] + (double)(1 - b)));
-    const T wz = peskin_phi<T>(T(S.frac[2] + (double)(1 - c)));
-    const int nx = L.n[0], nxy = L.n[0] * L.n[1], nodes = L.nodes;
-    const int row = wrap_index(S.base[1] + b, L.n[1], pery) * nx + wrap_index(S.base[2] + c, L.n[2], perz) * nxy;
-    T *force = static_cast<T *>(L.force);
-    const T Fx = T(F[0]), Fy = T(F[1]), Fz = T(F[2]);
-    const T fx = T(S.frac[0]);
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        const T wx = sizeof(T) == 8 ? peskin_phi<T>(T(S.frac[0] + (double)(1 - a))) : peskin_phi<T>(fx + T(1 - a));
-        const T dl = wx * wy * wz;
-        const int id = row + wrap_index(S.base[0] + a, nx, perx);
-        atomicAdd(force + id, Fx * dl);
-        atomicAdd(force + nodes + id, Fy * dl);
-        atomicAdd(force + 2 * nodes + id, Fz * dl);
+    if constexpr (sizeof(T) == 8) {
+        for (int a = 0; a < 4; ++a) w[a] = peskin_phi<T>(S.frac[0] + (double)(1 - a));
+        wy = peskin_phi<T>(S.frac[1] + (double)(1 - b));
+        wz = peskin_phi<T>(S.frac[2] + (double)(1 - c));
+    } else {
+        const T fx = T(S.frac[0]), fy = T(S.frac[1]), fz = T(S.frac[2]);
+        for (int a = 0; a < 4; ++a) w[a] = peskin_phi<T>(fx + T(1 - a));
+        wy = peskin_phi<T>(fy + T(1 - b));
+        wz = peskin_phi<T>(fz + T(1 - c));
     }
 }
 
 // Patch of lattice nodes the droplet's stencils can touch, from the node
-// bounding box [mn, mx]: floor(mn)-1 .. floor(mx)+2 per axis.
+// bounding box [mn, mx]: floor(mn)-1 .. floor(mx)+2 per axis (periodic axes
+// keep the lower corner inside the box and may wrap; Zou-He axes clamp).
 __device__ void write_patch(const LbView &L, const double mn[3], const double mx[3])
 {
     for (int a = 0; a < 3; ++a) {
@@ -586,10 +539,104 @@ __device__ void write_patch(const LbView &L, const double mn[3], const double mx
     }
 }
 
-// u at r_i by the 4-point delta (Eq. (ibm_force_d)(b)) and forward Euler
-// (Eq. (fwd_euler)), sixteen lanes per node (one x-row of four stencil
-// points each, reduced with shuffles); then the bounding box of the advected
-// nodes sets the patch of the next step and the last block closes the step.
+// Warp 0 of block 0 of the force/spread kernel: reduce the bounding-box rows
+// left by the previous interpolation (or regularisation) into the patch.
+__device__ void patch_from_rows(const LbView &L, const MeshView &M)
+{
+    const int lane = threadIdx.x & 31;
+    const int rows = L.ctl->n_part;
+    double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
+    for (int k = lane; k < rows; k += 32)
+        for (int a = 0; a < 3; ++a) {
+            mn[a] = fmin(mn[a], M.part[6 * k + a]);
+            mx[a] = fmax(mx[a], M.part[6 * k + 3 + a]);
+        }
+    for (int a = 0; a < 3; ++a)
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[a] = fmin(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
+            mx[a] = fmax(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
+        }
+    if (lane == 0) write_patch(L, mn, mx);
+}
+
+// Scaled unit normal of every triangle, m_t = -sigma/2 N/|N| with
+// N = (x1 - x0) x (x2 - x0), so that the force of Eq. (pi_drop) on vertex k
+// of the triangle is m_t x (x_{k+2} - x_{k+1}).  FP64.
+__global__ void __launch_bounds__(256) k_tri(MeshView M)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= M.nt) return;
+    const int v0 = M.tris[3 * t], v1 = M.tris[3 * t + 1], v2 = M.tris[3 * t + 2];
+    double e1[3], e2[3], N[3];
+    for (int a = 0; a < 3; ++a) {
+        e1[a] = M.r[3 * v1 + a] - M.r[3 * v0 + a];
+        e2[a] = M.r[3 * v2 + a] - M.r[3 * v0 + a];
+    }
+    cross3(e1, e2, N);
+    const double s = -0.5 * M.sigma / sqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
+    M.tn[3 * t] = s * N[0];
+    M.tn[3 * t + 1] = s * N[1];
+    M.tn[3 * t + 2] = s * N[2];
+}
+
+// Nodal force F_i = -sigma dA/dx_i (Eq. (pi_drop)) gathered over the
+// triangles around node i, then spread with the 4-point delta
+// (Eq. (ibm_force_d)(a)) by atomic adds into the Eulerian force.  Sixteen
+// lanes per node: the lanes split the incident triangles (reduced with
+// shuffles), then each lane adds one x-row of four stencil points.
+template <typename T>
+__global__ void __launch_bounds__(128) k_spread(LbView L, MeshView M)
+{
+    if (blockIdx.x == 0 && threadIdx.x < 32) patch_from_rows(L, M);
+    const int gid = blockIdx.x * (blockDim.x / kLanesPerNode) + threadIdx.x / kLanesPerNode;
+    const int lane = threadIdx.x % kLanesPerNode;
+    const bool valid = gid < M.nv;
+    const int i = valid ? gid : M.nv - 1;
+    double F[3] = {0.0, 0.0, 0.0};
+    for (int k = M.n2t_ptr[i] + lane; k < M.n2t_ptr[i + 1]; k += kLanesPerNode) {
+        const int e = M.n2t[k];
+        const int t = e / 3, slot = e - 3 * t;
+        const int vp = M.tris[3 * t + (slot == 2 ? 0 : slot + 1)];
+        const int vm = M.tris[3 * t + (slot == 0 ? 2 : slot - 1)];
+        const double d[3] = {M.r[3 * vm] - M.r[3 * vp], M.r[3 * vm + 1] - M.r[3 * vp + 1],
+                             M.r[3 * vm + 2] - M.r[3 * vp + 2]};
+        const double m[3] = {M.tn[3 * t], M.tn[3 * t + 1], M.tn[3 * t + 2]};
+        double g[3];
+        cross3(m, d, g);
+        for (int a = 0; a < 3; ++a) F[a] += g[a];
+    }
+    for (int o = kLanesPerNode / 2; o > 0; o >>= 1)
+        for (int a = 0; a < 3; ++a) F[a] += __shfl_xor_sync(0xffffffffu, F[a], o, kLanesPerNode);
+    if (valid && lane == 0) {
+        M.fn[3 * i] = F[0];
+        M.fn[3 * i + 1] = F[1];
+        M.fn[3 * i + 2] = F[2];
+    }
+    const NodeStencil S = node_stencil(L, M.r + 3 * i, lane);
+    if (!valid) return;
+    if (!S.ok) {
+        if (lane == 0) atomicOr(&L.ctl->err, IBL_ERRBIT_WALL);
+        return;
+    }
+    const bool perx = L.bc[0] == IBL_BC_PERIODIC, pery = L.bc[1] == IBL_BC_PERIODIC,
+               perz = L.bc[2] == IBL_BC_PERIODIC;
+    const int b = lane & 3, c = lane >> 2;
+    T w[4], wy, wz;
+    stencil_weights<T>(S, b, c, w, wy, wz);
+    const int nx = L.n[0], nxy = L.n[0] * L.n[1], nodes = L.nodes;
+    const int row = wrap_index(S.base[1] + b, L.n[1], pery) * nx + wrap_index(S.base[2] + c, L.n[2], perz) * nxy;
+    T *force = static_cast<T *>(L.force);
+    const T Fx = T(F[0]), Fy = T(F[1]), Fz = T(F[2]);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const T dl = w[a] * wy * wz;
+        const int id = row + wrap_index(S.base[0] + a, nx, perx);
+        atomicAdd(force + id, Fx * dl);
+        atomicAdd(force + nodes + id, Fy * dl);
+        atomicAdd(force + 2 * nodes + id, Fz * dl);
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(128) k_interp(LbView L, MeshView M)
 {
@@ -603,18 +650,15 @@ __global__ void __launch_bounds__(128) k_interp(LbView L, MeshView M)
         const bool perx = L.bc[0] == IBL_BC_PERIODIC, pery = L.bc[1] == IBL_BC_PERIODIC,
                    perz = L.bc[2] == IBL_BC_PERIODIC;
         const int b = lane & 3, c = lane >> 2;
-        const T wy = peskin_phi<T>(T(S.frac[1] + (double)(1 - b)));
-        const T wz = peskin_phi<T>(T(S.frac[2] + (double)(1 - c)));
+        T w[4], wy, wz;
+        stencil_weights<T>(S, b, c, w, wy, wz);
         const int nx = L.n[0], nxy = L.n[0] * L.n[1], nodes = L.nodes;
         const int row =
             wrap_index(S.base[1] + b, L.n[1], pery) * nx + wrap_index(S.base[2] + c, L.n[2], perz) * nxy;
         const T *vel = static_cast<const T *>(L.vel);
-        const T fx = T(S.frac[0]);
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
-            const T wx =
-                sizeof(T) == 8 ? peskin_phi<T>(T(S.frac[0] + (double)(1 - a))) : peskin_phi<T>(fx + T(1 - a));
-            const T dl = wx * wy * wz;
+            const T dl = w[a] * wy * wz;
             const int id = row + wrap_index(S.base[0] + a, nx, perx);
             v[0] += vel[id] * dl;
             v[1] += vel[nodes + id] * dl;
@@ -640,10 +684,9 @@ __global__ void __launch_bounds__(128) k_interp(LbView L, MeshView M)
             M.r[3 * i + 2] = r[2];
         }
     }
-    // block min / max of the new positions -> per-block partials; the last
-    // block reduces them (no contended atomics) and sets the next patch
+    // block min / max of the new positions -> one partial row per block; the
+    // next force/spread kernel reduces the rows into the patch (no tail here)
     __shared__ double smn[3][4], smx[3][4];
-    __shared__ bool last;
     const int wlane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int a = 0; a < 3; ++a) {
         // lanes 0 and 16 hold the warp's two nodes
@@ -666,44 +709,10 @@ __global__ void __launch_bounds__(128) k_interp(LbView L, MeshView M)
             M.part[6 * blockIdx.x + a] = mn;
             M.part[6 * blockIdx.x + 3 + a] = mx;
         }
-        __threadfence();
-        const unsigned t = atomicAdd(&L.ctl->ib_blocks_done, 1u);
-        last = (t == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
-    for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x)
-        for (int a = 0; a < 3; ++a) {
-            mn[a] = fmin(mn[a], __ldcg(M.part + 6 * k + a));
-            mx[a] = fmax(mx[a], __ldcg(M.part + 6 * k + 3 + a));
+        if (blockIdx.x == 0) {
+            L.ctl->n_part = gridDim.x;
+            close_step(L);  // nothing reads the step counter during this kernel
         }
-    __syncthreads();
-    for (int a = 0; a < 3; ++a) {
-        for (int o = 16; o > 0; o >>= 1) {
-            mn[a] = fmin(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
-            mx[a] = fmax(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
-        }
-        if (wlane == 0) {
-            smn[a][warp] = mn[a];
-            smx[a][warp] = mx[a];
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int a = 0; a < 3; ++a) {
-            for (int w = 1; w < nw; ++w) {
-                smn[a][0] = fmin(smn[a][0], smn[a][w]);
-                smx[a][0] = fmax(smx[a][0], smx[a][w]);
-            }
-            mn[a] = smn[a][0];
-            mx[a] = smx[a][0];
-        }
-        write_patch(L, mn, mx);
-        close_step(L);  // the interpolation kernel closes the step
-        L.ctl->ib_blocks_done = 0u;
-        __threadfence();
     }
 }
 
@@ -747,7 +756,7 @@ __device__ double block_max(double v, double *sh)
     return out;
 }
 
-__device__ void block_bbox_patch(const LbView &L, const double *r, int nv)
+__device__ void block_bbox_patch(const LbView &L, const MeshView &M, const double *r, int nv)
 {
     __shared__ double sh[32];
     double mn[3], mx[3];
@@ -760,7 +769,14 @@ __device__ void block_bbox_patch(const LbView &L, const double *r, int nv)
         mn[a] = -block_max(-lo, sh);
         mx[a] = block_max(hi, sh);
     }
-    if (threadIdx.x == 0) write_patch(L, mn, mx);
+    if (threadIdx.x == 0) {
+        write_patch(L, mn, mx);
+        for (int a = 0; a < 3; ++a) {
+            M.part[a] = mn[a];
+            M.part[3 + a] = mx[a];
+        }
+        L.ctl->n_part = 1;
+    }
 }
 
 // Mesh regularisation, Sec. 3.3, one block: x_o fixed, x_q the previous
@@ -818,7 +834,7 @@ __global__ void __launch_bounds__(1024) k_regularize(LbView L, MeshView M, RegPa
         for (int i = threadIdx.x; i < 3 * nv; i += blockDim.x) M.r[i] = M.s1[i];
     }
     __syncthreads();
-    block_bbox_patch(L, M.r, nv);
+    block_bbox_patch(L, M, M.r, nv);
     if (threadIdx.x == 0) {
         L.ctl->reg_iters = it;
         if (!conv) atomicOr(&L.ctl->err, IBL_ERRBIT_NOCONV);
@@ -827,7 +843,7 @@ __global__ void __launch_bounds__(1024) k_regularize(LbView L, MeshView M, RegPa
 
 __global__ void __launch_bounds__(256) k_patch(LbView L, MeshView M)
 {
-    block_bbox_patch(L, M.r, M.nv);
+    block_bbox_patch(L, M, M.r, M.nv);
 }
 
 // Symmetric 3x3 eigen-decomposition by cyclic Jacobi rotations: each
@@ -1050,6 +1066,7 @@ cudaError_t launch_advance(const LbView &L, cudaStream_t s)
 
 cudaError_t launch_spread(const LbView &L, const MeshView &M, cudaStream_t s)
 {
+    k_tri<<<blocks_for(M.nt, 256), 256, 0, s>>>(M);
     const unsigned g = blocks_for((long long)M.nv * kLanesPerNode, 128);
     if (L.precision == IBL_FP64) k_spread<double><<<g, 128, 0, s>>>(L, M);
     else k_spread<float><<<g, 128, 0, s>>>(L, M);
