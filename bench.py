@@ -62,7 +62,8 @@ def config_dict(w, extra=None):
 
 def traffic_from_profiles():
     """Per-launch DRAM bytes of the lattice kernel from the committed ncu
-    summary, if it was taken on the current kernel source."""
+    record, if it was taken on the current lattice source (the part of the
+    kernel file up to the end of the lattice kernel)."""
     p = os.path.join(ROOT, "profiles", "lattice_traffic.json")
     if not os.path.exists(p):
         return None
@@ -70,9 +71,12 @@ def traffic_from_profiles():
         d = json.load(fh)
     import hashlib
 
-    src = os.path.join(ROOT, "paper_2403_01161_gb300", "csrc", "iblb_kernels.cu")
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    if d.get("kernel_source_sha256") != h:
+    src = open(os.path.join(ROOT, "paper_2403_01161_gb300", "csrc", "iblb_kernels.cu")).read()
+    marker = "// Advances the step counter when no droplet kernel follows the lattice kernel."
+    if marker not in src:
+        return None
+    h = hashlib.sha256(src[: src.index(marker)].encode()).hexdigest()
+    if d.get("lattice_source_sha256") != h:
         return None
     return float(d["bytes_per_launch_full_size"])
 
