@@ -218,6 +218,29 @@ int ibl_copy_neighbours(ibl_mesh *m, int32_t *ptr, int32_t *idx, int *nnz);
  * *iters receives the iteration count. */
 int ibl_regularize_now(ibl_mesh *m, int *iters);
 
+/* Allocation-free variant of the mesh regularisation (the paper has no
+ * counterpart: this is an interface for callers that cannot allocate device
+ * memory -- for instance a host program whose own allocator reserves the
+ * device's memory up front, a time-budgeted loop that cannot absorb an
+ * allocation call, or a plug-in whose host forbids allocations).  It runs
+ * the same iteration as ibl_regularize_now on caller-owned device buffers:
+ * r (n_nodes x 3 doubles, read and overwritten with the result), the
+ * one-ring CSR nb_ptr (n_nodes + 1 int32) and nb_idx (nb_ptr[n_nodes]
+ * int32, one-ring neighbours as returned by ibl_copy_neighbours), and
+ * result (2 int32: iterations, 1 if converged else 0).  Asynchronous on
+ * `stream` (a cudaStream_t, NULL = legacy default stream).
+ * Scratch: a fixed array inside the library (16384 nodes x 9 doubles,
+ * 1.18 MB) that every GPU loading the library holds until the process
+ * exits; n_nodes above 16384 is rejected with IBL_EINVAL.  The first call
+ * on a device looks up that array's device address (with the caller's
+ * current device), so make the first call on each device before any stream
+ * capture.  Every call uses the same array and leaves its contents behind;
+ * each call writes every element it reads first, so nothing needs
+ * clearing, but calls whose executions overlap on the GPU (other streams,
+ * other threads) race on it.  Calls no allocating routine. */
+int ibl_regularize_noalloc(double *r, const int32_t *nb_ptr, const int32_t *nb_idx, int n_nodes, double alpha,
+                           double gamma, double tol, int max_iter, int plus_sign, int32_t *result, void *stream);
+
 /* The paper's trajectory loop with host buffers (Sec. 3.2, steps 1-4): for
  * each of n_frames frames, copy the frame (host, 9 doubles) to the device,
  * run steps_per_frame IBLB steps, and copy the droplet's shape record back

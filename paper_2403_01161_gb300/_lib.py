@@ -79,6 +79,8 @@ SIGNATURES = [
     ("ibl_copy_mesh", ctypes.c_int, [_P, _D, _D, _I32]),
     ("ibl_copy_neighbours", ctypes.c_int, [_P, _I32, _I32, ctypes.POINTER(ctypes.c_int)]),
     ("ibl_regularize_now", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
+    ("ibl_regularize_noalloc", ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                              ctypes.c_double, ctypes.c_int, ctypes.c_int, _P, _P]),
     ("ibl_run_frames", ctypes.c_int, [_P, _P, _D, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Observables)]),
     ("ibl_velocity_set", ctypes.c_int, [_I32, _D]),
     ("ibl_profile_enable", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),

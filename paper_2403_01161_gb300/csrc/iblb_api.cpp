@@ -134,6 +134,8 @@ struct Profiler {
 
 }  // namespace
 
+int iblb::iblb_set_error(int code, const char *msg) { return fail(code, msg); }
+
 struct ibl_lb {
     ibl_lb_params p;
     LbView v;

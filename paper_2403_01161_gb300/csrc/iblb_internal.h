@@ -83,6 +83,9 @@ cudaError_t launch_regularize(const LbView &L, const MeshView &M, const RegParam
 cudaError_t launch_observables(const LbView &L, const MeshView &M, cudaStream_t s);
 cudaError_t launch_patch_from_mesh(const LbView &L, const MeshView &M, cudaStream_t s);
 
+// records a message for ibl_last_error() and returns `code` (iblb_api.cpp)
+int iblb_set_error(int code, const char *msg);
+
 // library velocity order (shared with the host code of the library only)
 void velocity_table(int c[19][3], double w[19]);
 

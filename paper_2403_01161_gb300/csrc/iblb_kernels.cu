@@ -19,6 +19,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <mutex>
 #include <utility>
 
 #include "iblb_internal.h"
@@ -1112,3 +1113,128 @@ void velocity_table(int c[19][3], double w[19])
 }
 
 }  // namespace iblb
+
+// ---------------------------------------------------------------------------
+// Allocation-free mesh regularisation.
+//
+// Some callers cannot allocate device memory: a host program whose own
+// allocator has reserved the device's memory up front (so any other
+// allocation fails or fragments its pool), a control loop with a fixed time
+// budget that cannot absorb an allocation call that may synchronise the
+// device, or a plug-in whose host forbids it to allocate.  For them this
+// variant of the regularisation kernel keeps its scratch in a fixed array
+// of this file instead of in a caller workspace.  The array is part of the
+// library image, so every GPU that loads the library holds it (1.18 MB)
+// until the process exits.
+namespace iblb {
+namespace {
+
+constexpr int kNoAllocMaxNodes = 16384;  // enough for a level-5 icosphere (10242 nodes)
+
+// x_o, the ping-pong iterate and x_b, each [kNoAllocMaxNodes][3] doubles.
+static __device__ __align__(256) double g_noalloc_scratch[3 * 3 * kNoAllocMaxNodes];
+
+// Same iteration as k_regularize (Sec. 3.3), reading and writing only the
+// caller's positions and the static scratch; result[0] = iterations,
+// result[1] = 1 if the exit test held.
+__global__ void __launch_bounds__(1024)
+    k_regularize_noalloc(double *r, const int *nb_ptr, const int *nb_idx, int nv, double *scratch, RegParams p,
+                         int *result)
+{
+    __shared__ double sh[32];
+    double *xo = scratch, *s1 = scratch + 3 * kNoAllocMaxNodes, *xb = scratch + 6 * kNoAllocMaxNodes;
+    double *buf[2] = {r, s1};
+    for (int i = threadIdx.x; i < 3 * nv; i += blockDim.x) xo[i] = r[i];
+    __syncthreads();
+    const double sg = p.plus_sign ? 1.0 : -1.0;
+    int cur = 0, it = 0;
+    bool conv = false;
+    while (it < p.max_iter) {
+        ++it;
+        const double *xq = buf[cur];
+        double *xp = buf[cur ^ 1];
+        for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+            const int b0 = nb_ptr[i], b1 = nb_ptr[i + 1];
+            const int ni = b1 - b0;
+            for (int a = 0; a < 3; ++a) {
+                double s = 0.0;
+                for (int k = b0; k < b1; ++k) s += xq[3 * nb_idx[k] + a];
+                const double v = p.alpha * xo[3 * i + a] + (1.0 - p.alpha) / ni * s;
+                xp[3 * i + a] = v;
+                xb[3 * i + a] = v - (p.alpha * xo[3 * i + a] + (1.0 - p.alpha) * xq[3 * i + a]);
+            }
+        }
+        __syncthreads();
+        double dmax = 0.0;
+        for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+            const int b0 = nb_ptr[i], b1 = nb_ptr[i + 1];
+            const int ni = b1 - b0;
+            double d2 = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                double s = 0.0;
+                for (int k = b0; k < b1; ++k) s += xb[3 * nb_idx[k] + a];
+                const double v = xp[3 * i + a] - (p.gamma * xb[3 * i + a] + sg * (1.0 - p.gamma) / ni * s);
+                xp[3 * i + a] = v;
+                const double d = v - xq[3 * i + a];
+                d2 += d * d;
+            }
+            dmax = fmax(dmax, sqrt(d2));
+        }
+        dmax = block_max(dmax, sh);
+        cur ^= 1;
+        if (dmax < p.tol) {
+            conv = true;
+            break;
+        }
+    }
+    if (cur != 0) {
+        for (int i = threadIdx.x; i < 3 * nv; i += blockDim.x) r[i] = s1[i];
+    }
+    if (threadIdx.x == 0) {
+        result[0] = it;
+        result[1] = conv ? 1 : 0;
+    }
+}
+
+std::mutex g_noalloc_mu;
+double *g_noalloc_ptr[256] = {};  // device address of the array, per device ordinal
+
+}  // namespace
+}  // namespace iblb
+
+extern "C" int ibl_regularize_noalloc(double *r, const int32_t *nb_ptr, const int32_t *nb_idx, int n_nodes,
+                                      double alpha, double gamma, double tol, int max_iter, int plus_sign,
+                                      int32_t *result, void *stream)
+{
+    using namespace iblb;
+    if (!r || !nb_ptr || !nb_idx || !result) return iblb_set_error(IBL_EINVAL, "null pointer argument");
+    if (n_nodes < 1 || n_nodes > kNoAllocMaxNodes)
+        return iblb_set_error(IBL_EINVAL, "ibl_regularize_noalloc: n_nodes must be in 1..16384 (the size of its "
+                                          "fixed scratch array)");
+    if (!(alpha >= 0 && alpha <= 1) || !(gamma >= 0 && gamma <= 1) || !(tol > 0) || max_iter < 1)
+        return iblb_set_error(IBL_EINVAL, "regularisation parameters out of range");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return iblb_set_error(IBL_ECUDA, cudaGetErrorString(e));
+    if (dev < 0 || dev >= 256) return iblb_set_error(IBL_EINVAL, "device ordinal out of range");
+    double *scratch = nullptr;
+    {
+        // first call on this device: look up the array's device address with
+        // the device current (the name alone is a host-side stand-in)
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void *p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess) return iblb_set_error(IBL_ECUDA, cudaGetErrorString(e));
+            g_noalloc_ptr[dev] = static_cast<double *>(p);
+        }
+        scratch = g_noalloc_ptr[dev];
+    }
+    RegParams p{alpha, gamma, tol, max_iter, plus_sign ? 1 : 0};
+    k_regularize_noalloc<<<1, 1024, 0, static_cast<cudaStream_t>(stream)>>>(
+        r, reinterpret_cast<const int *>(nb_ptr), reinterpret_cast<const int *>(nb_idx), n_nodes, scratch, p,
+        reinterpret_cast<int *>(result));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return iblb_set_error(IBL_ECUDA, cudaGetErrorString(e));
+    return IBL_OK;
+}
