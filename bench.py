@@ -140,6 +140,23 @@ def dist_info():
     return rank, world, local
 
 
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The largest of each rank's value (times are taken as the slowest rank's)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(nodes_per_rank: int, steps: int, world: int, seconds: float) -> float:
+    """Whole-job MLUPS: every rank advances its own replica by `steps` steps."""
+    return world * nodes_per_rank * steps / seconds / 1e6
+
+
 def cpu_baseline(w, budget_s=15.0, max_steps=400):
     """The FP64 oracle, as it stands, on this host's cores: a bounded number
     of steps of the same workload (same box, mesh and gradients)."""
@@ -228,11 +245,8 @@ def run_ours(args):
     st = sim.status()
     if st != 0:
         raise RuntimeError("device error status %d during the timed region" % st)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * w.nodes * args.steps / (ms * 1e-3) / 1e6
+    ms = max_over_ranks(ms, world, dev)
+    value = job_throughput(w.nodes, args.steps, world, ms * 1e-3)
     lb_ms, lb_n = prof["lattice"]
     t_launch = lb_ms / lb_n * 1e-3 if lb_n else None
     achieved = BYTES_PER_NODE * w.nodes / t_launch / 1e9 if t_launch else None
@@ -255,17 +269,14 @@ def run_ours(args):
     e2e_s = time.perf_counter() - t0
     sim2.close()
     assert len(recs) == n_fr
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, world, dev)
     e2e_steps = n_fr * w.n_hold
     import ctypes
 
     from paper_2403_01161_gb300 import _lib
 
     rec_bytes = ctypes.sizeof(_lib.Observables)
-    e2e = {"value": world * w.nodes * e2e_steps / e2e_s / 1e6, "unit": UNIT,
+    e2e = {"value": job_throughput(w.nodes, e2e_steps, world, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": 72.0 / w.n_hold, "d2h_bytes_per_step": rec_bytes / w.n_hold,
            "steps": e2e_steps, "api": "ibl_run_frames (host gradients in, host shape records out)"}
 
