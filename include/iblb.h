@@ -249,6 +249,28 @@ int ibl_regularize_noalloc(double *r, const int32_t *nb_ptr, const int32_t *nb_i
 int ibl_run_frames(ibl_lb *lb, ibl_mesh *m, const double *A_frames, int n_frames,
                    int steps_per_frame, ibl_observables *out);
 
+/* ---- ensemble of droplets ---------------------------------------------- */
+
+/* Many independent droplets advanced together (Sec. 4 runs one droplet per
+ * turbulent trajectory; an ensemble batches such trajectories on one GPU).
+ * Members are existing lattices, each with its droplet mesh, of any box and
+ * mesh size, sharing precision, stream and step count.  Each ensemble step
+ * launches every phase of the IBLB step once for all members (triangle
+ * normals, force + spread, lattice update, interpolation + advection), plus
+ * each member's own scheduled regularisation and shape record; whole chunks
+ * of steps replay as one CUDA graph.  Members keep working with the
+ * per-member readout calls; stepping a member on its own desynchronises it
+ * (IBL_EINVAL at the next ensemble step).  The workspace (device, caller
+ * owned) holds the member tables. */
+typedef struct ibl_ensemble ibl_ensemble;
+int ibl_ensemble_workspace_size(int n_members, ibl_lb *const *members, size_t *bytes);
+int ibl_ensemble_create(int n_members, ibl_lb *const *members, void *workspace, size_t bytes, ibl_ensemble **out);
+/* Enqueues n steps of every member (asynchronous). */
+int ibl_ensemble_step(ibl_ensemble *e, long long n);
+/* Waits and returns the first member's error status, if any. */
+int ibl_ensemble_sync(ibl_ensemble *e);
+void ibl_ensemble_destroy(ibl_ensemble *e);
+
 /* ---- introspection --------------------------------------------------- */
 
 /* The library's D3Q19 velocities (19 x 3 int32) and weights (19 doubles). */

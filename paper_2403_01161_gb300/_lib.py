@@ -82,6 +82,12 @@ SIGNATURES = [
     ("ibl_regularize_noalloc", ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                               ctypes.c_double, ctypes.c_int, ctypes.c_int, _P, _P]),
     ("ibl_run_frames", ctypes.c_int, [_P, _P, _D, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Observables)]),
+    ("ibl_ensemble_workspace_size", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_P), _SZ]),
+    ("ibl_ensemble_create", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_P), _P, ctypes.c_size_t,
+                                           ctypes.POINTER(_P)]),
+    ("ibl_ensemble_step", ctypes.c_int, [_P, ctypes.c_longlong]),
+    ("ibl_ensemble_sync", ctypes.c_int, [_P]),
+    ("ibl_ensemble_destroy", None, [_P]),
     ("ibl_velocity_set", ctypes.c_int, [_I32, _D]),
     ("ibl_profile_enable", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
     ("ibl_profile_read", ctypes.c_int, [_P, _D, ctypes.POINTER(ctypes.c_longlong)]),

@@ -511,6 +511,135 @@ int capture_chunk(ibl_lb *lb, int chunk)
 
 }  // namespace
 
+struct ibl_ensemble {
+    std::vector<ibl_lb *> m;
+    iblb::EnsembleView v{};
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int chunk = 0;
+    ~ibl_ensemble()
+    {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+    }
+};
+
+namespace {
+
+struct EnsembleLayout {
+    size_t lv = 0, mv = 0, lat_member = 0, lat_start = 0, node_member = 0, node_start = 0, tri_member = 0,
+           tri_start = 0, total = 0;
+    int lat_blocks = 0, node_blocks = 0, tri_blocks = 0;
+};
+
+int ensemble_layout(int n, ibl_lb *const *members, EnsembleLayout &L, std::string &why)
+{
+    if (n < 1 || !members) {
+        why = "need at least one member";
+        return IBL_EINVAL;
+    }
+    long long lat = 0, node = 0, tri = 0;
+    for (int k = 0; k < n; ++k) {
+        const ibl_lb *lb = members[k];
+        if (!lb || !lb->mesh) {
+            why = "every member needs a lattice with a droplet mesh";
+            return IBL_EINVAL;
+        }
+        lat += (lb->v.nodes + 255) / 256;
+        node += ((long long)lb->mesh->v.nv * 16 + 127) / 128;
+        tri += (lb->mesh->v.nt + 255) / 256;
+    }
+    if (lat > 0x7fffffffLL) {
+        why = "ensemble too large";
+        return IBL_EINVAL;
+    }
+    size_t off = 0;
+    auto take = [&](size_t b) {
+        const size_t o = off;
+        off = align256(off + b);
+        return o;
+    };
+    L.lv = take(sizeof(LbView) * n);
+    L.mv = take(sizeof(MeshView) * n);
+    L.lat_member = take(sizeof(int) * lat);
+    L.lat_start = take(sizeof(int) * (n + 1));
+    L.node_member = take(sizeof(int) * node);
+    L.node_start = take(sizeof(int) * (n + 1));
+    L.tri_member = take(sizeof(int) * tri);
+    L.tri_start = take(sizeof(int) * (n + 1));
+    L.total = off;
+    L.lat_blocks = (int)lat;
+    L.node_blocks = (int)node;
+    L.tri_blocks = (int)tri;
+    return IBL_OK;
+}
+
+int ensemble_chunk(const ibl_ensemble *e)
+{
+    long long c = 2;
+    auto lcm = [&](long long a, long long b) { return a / gcd_ll(a, b) * b; };
+    for (ibl_lb *lb : e->m) {
+        if (lb->mesh->reg_every > 0) c = lcm(c, lb->mesh->reg_every);
+        if (lb->mesh->readout_every > 0) c = lcm(c, lb->mesh->readout_every);
+        if (c > 2048) return 0;
+    }
+    while (c < 32) c *= 2;
+    return (int)c;
+}
+
+// One ensemble step on `s`: the four batched kernels, then each member's
+// scheduled regularisation and shape record; advances every member's count.
+int ensemble_one_step(ibl_ensemble *e, cudaStream_t s)
+{
+    const long long step = e->m[0]->host_step;
+    cudaError_t err = iblb::launch_ensemble_step(e->v, (step & 1) != 0, s);
+    if (err != cudaSuccess) return cuda_fail(err, "ensemble step launch");
+    const long long next = step + 1;
+    for (ibl_lb *lb : e->m) {
+        ibl_mesh *mm = lb->mesh;
+        if (mm->reg_every > 0 && next % mm->reg_every == 0) {
+            err = iblb::launch_regularize(lb->v, mm->v, mm->reg, s);
+            if (err != cudaSuccess) return cuda_fail(err, "ensemble regularisation launch");
+        }
+        if (mm->readout_every > 0 && next % mm->readout_every == 0) {
+            err = iblb::launch_observables(lb->v, mm->v, s);
+            if (err != cudaSuccess) return cuda_fail(err, "ensemble observables launch");
+        }
+        lb->host_step = next;
+    }
+    return IBL_OK;
+}
+
+int ensemble_capture(ibl_ensemble *e, int chunk)
+{
+    cudaError_t err = cudaSuccess;
+    if (!e->cap_stream) err = cudaStreamCreateWithFlags(&e->cap_stream, cudaStreamNonBlocking);
+    if (err != cudaSuccess) return cuda_fail(err, "ensemble capture stream");
+    std::vector<long long> saved;
+    for (ibl_lb *lb : e->m) saved.push_back(lb->host_step);
+    err = cudaStreamBeginCapture(e->cap_stream, cudaStreamCaptureModeThreadLocal);
+    int st = IBL_OK;
+    if (err == cudaSuccess) {
+        for (int k = 0; k < chunk && st == IBL_OK; ++k) st = ensemble_one_step(e, e->cap_stream);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(e->cap_stream, &g);
+        if (e2 != cudaSuccess && st == IBL_OK) st = cuda_fail(e2, "end capture");
+        if (st == IBL_OK) {
+            const cudaError_t e3 = cudaGraphInstantiate(&e->gexec, g, 0);
+            if (e3 != cudaSuccess) st = cuda_fail(e3, "graph instantiate");
+        }
+        if (g) cudaGraphDestroy(g);
+    } else {
+        st = cuda_fail(err, "begin capture");
+    }
+    for (size_t k = 0; k < e->m.size(); ++k) e->m[k]->host_step = saved[k];
+    if (st == IBL_OK) e->chunk = chunk;
+    return st;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char *ibl_last_error(void) { return g_err.c_str(); }
@@ -945,6 +1074,140 @@ int ibl_run_frames(ibl_lb *lb, ibl_mesh *m, const double *A_frames, int n_frames
         if (c.err) return lb_status_from_device(lb);
     }
     return IBL_OK;
+}
+
+int ibl_ensemble_workspace_size(int n, ibl_lb *const *members, size_t *bytes)
+{
+    if (!bytes) return fail(IBL_EINVAL, "null argument");
+    EnsembleLayout L;
+    std::string why;
+    const int st = ensemble_layout(n, members, L, why);
+    if (st != IBL_OK) return fail(st, why);
+    *bytes = L.total;
+    return IBL_OK;
+}
+
+int ibl_ensemble_create(int n, ibl_lb *const *members, void *workspace, size_t bytes, ibl_ensemble **out)
+{
+    if (!out) return fail(IBL_EINVAL, "null argument");
+    EnsembleLayout L;
+    std::string why;
+    const int st = ensemble_layout(n, members, L, why);
+    if (st != IBL_OK) return fail(st, why);
+    if (!workspace || bytes < L.total) return fail(IBL_ENOMEM, "ensemble workspace too small");
+    if (((uintptr_t)workspace & 255) != 0) return fail(IBL_EINVAL, "workspace must be 256-byte aligned");
+    const ibl_lb *m0 = members[0];
+    std::vector<LbView> lv;
+    std::vector<MeshView> mv;
+    std::vector<int> lat_member, lat_start, node_member, node_start, tri_member, tri_start;
+    for (int k = 0; k < n; ++k) {
+        const ibl_lb *lb = members[k];
+        if (lb->p.precision != m0->p.precision) return fail(IBL_EINVAL, "members differ in precision");
+        if (lb->stream != m0->stream) return fail(IBL_EINVAL, "members are bound to different streams");
+        if (lb->host_step != m0->host_step) return fail(IBL_EINVAL, "members are at different step counts");
+        for (int j = 0; j < k; ++j)
+            if (members[j] == lb) return fail(IBL_EINVAL, "a lattice appears twice");
+        lv.push_back(lb->v);
+        mv.push_back(lb->mesh->v);
+        lat_start.push_back((int)lat_member.size());
+        for (int b = 0; b < (lb->v.nodes + 255) / 256; ++b) lat_member.push_back(k);
+        node_start.push_back((int)node_member.size());
+        for (int b = 0; b < (lb->mesh->v.nv * 16 + 127) / 128; ++b) node_member.push_back(k);
+        tri_start.push_back((int)tri_member.size());
+        for (int b = 0; b < (lb->mesh->v.nt + 255) / 256; ++b) tri_member.push_back(k);
+    }
+    lat_start.push_back((int)lat_member.size());
+    node_start.push_back((int)node_member.size());
+    tri_start.push_back((int)tri_member.size());
+    char *w = static_cast<char *>(workspace);
+    cudaStream_t s = m0->stream;
+    cudaError_t e = cudaSuccess;
+    auto up = [&](size_t off, const void *src, size_t nbytes) {
+        if (e == cudaSuccess) e = cudaMemcpyAsync(w + off, src, nbytes, cudaMemcpyHostToDevice, s);
+    };
+    up(L.lv, lv.data(), sizeof(LbView) * n);
+    up(L.mv, mv.data(), sizeof(MeshView) * n);
+    up(L.lat_member, lat_member.data(), sizeof(int) * lat_member.size());
+    up(L.lat_start, lat_start.data(), sizeof(int) * lat_start.size());
+    up(L.node_member, node_member.data(), sizeof(int) * node_member.size());
+    up(L.node_start, node_start.data(), sizeof(int) * node_start.size());
+    up(L.tri_member, tri_member.data(), sizeof(int) * tri_member.size());
+    up(L.tri_start, tri_start.data(), sizeof(int) * tri_start.size());
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host tables are temporaries
+    if (e != cudaSuccess) return cuda_fail(e, "ensemble upload");
+    ibl_ensemble *en = new ibl_ensemble();
+    en->m.assign(members, members + n);
+    en->stream = s;
+    iblb::EnsembleView &v = en->v;
+    v.lv = reinterpret_cast<const LbView *>(w + L.lv);
+    v.mv = reinterpret_cast<const MeshView *>(w + L.mv);
+    v.lat_member = reinterpret_cast<const int *>(w + L.lat_member);
+    v.lat_start = reinterpret_cast<const int *>(w + L.lat_start);
+    v.node_member = reinterpret_cast<const int *>(w + L.node_member);
+    v.node_start = reinterpret_cast<const int *>(w + L.node_start);
+    v.tri_member = reinterpret_cast<const int *>(w + L.tri_member);
+    v.tri_start = reinterpret_cast<const int *>(w + L.tri_start);
+    v.lat_blocks = L.lat_blocks;
+    v.node_blocks = L.node_blocks;
+    v.tri_blocks = L.tri_blocks;
+    v.precision = m0->p.precision;
+    *out = en;
+    return IBL_OK;
+}
+
+int ibl_ensemble_step(ibl_ensemble *en, long long n)
+{
+    if (!en || n < 0) return fail(IBL_EINVAL, "bad ensemble step request");
+    const long long h0 = en->m[0]->host_step;
+    for (ibl_lb *lb : en->m)
+        if (lb->host_step != h0 || !lb->mesh) return fail(IBL_EINVAL, "members were stepped apart from the ensemble");
+    const int chunk = ensemble_chunk(en);
+    long long done = 0;
+    if (chunk > 0) {
+        while (done < n && en->m[0]->host_step % chunk != 0) {
+            const int st = ensemble_one_step(en, en->stream);
+            if (st != IBL_OK) return st;
+            ++done;
+        }
+        if (n - done >= chunk) {
+            if (en->chunk != chunk) {
+                if (en->gexec) {
+                    cudaGraphExecDestroy(en->gexec);
+                    en->gexec = nullptr;
+                }
+                const int st = ensemble_capture(en, chunk);
+                if (st != IBL_OK) return st;
+            }
+            while (n - done >= chunk) {
+                const cudaError_t e = cudaGraphLaunch(en->gexec, en->stream);
+                if (e != cudaSuccess) return cuda_fail(e, "ensemble graph launch");
+                for (ibl_lb *lb : en->m) lb->host_step += chunk;
+                done += chunk;
+            }
+        }
+    }
+    for (; done < n; ++done) {
+        const int st = ensemble_one_step(en, en->stream);
+        if (st != IBL_OK) return st;
+    }
+    return IBL_OK;
+}
+
+int ibl_ensemble_sync(ibl_ensemble *en)
+{
+    if (!en) return fail(IBL_EINVAL, "null ensemble");
+    for (ibl_lb *lb : en->m) {
+        const int st = lb_status_from_device(lb);
+        if (st != IBL_OK) return st;
+    }
+    return IBL_OK;
+}
+
+void ibl_ensemble_destroy(ibl_ensemble *en)
+{
+    if (!en) return;
+    cudaStreamSynchronize(en->stream);
+    delete en;
 }
 
 int ibl_profile_enable(ibl_lb *lb, int mask, int every)

@@ -70,6 +70,20 @@ struct RegParams {
     int plus_sign;
 };
 
+// Device tables of an ensemble step (all members advance together).
+struct EnsembleView {
+    const LbView *lv;        // [n] member lattices (device copy)
+    const MeshView *mv;      // [n] member meshes (device copy)
+    const int *lat_member;   // [lat_blocks] member of each lattice block
+    const int *lat_start;    // [n+1] first lattice block of each member
+    const int *node_member;  // [node_blocks]
+    const int *node_start;   // [n+1]
+    const int *tri_member;   // [tri_blocks]
+    const int *tri_start;    // [n+1]
+    int lat_blocks, node_blocks, tri_blocks;
+    int precision;
+};
+
 constexpr int kRingCap = 4096;
 constexpr int kObsBlocksMax = 304;
 
@@ -82,6 +96,7 @@ cudaError_t launch_interp(const LbView &L, const MeshView &M, cudaStream_t s);
 cudaError_t launch_regularize(const LbView &L, const MeshView &M, const RegParams &p, cudaStream_t s);
 cudaError_t launch_observables(const LbView &L, const MeshView &M, cudaStream_t s);
 cudaError_t launch_patch_from_mesh(const LbView &L, const MeshView &M, cudaStream_t s);
+cudaError_t launch_ensemble_step(const EnsembleView &E, bool odd, cudaStream_t s);
 
 // records a message for ibl_last_error() and returns `code` (iblb_api.cpp)
 int iblb_set_error(int code, const char *msg);

@@ -209,14 +209,11 @@ __device__ __forceinline__ void bc_dispatch(T (&f)[19], const T (&uw)[3], int ru
 // the host).  The collision works on opposite pairs (c_i, -c_i), whose
 // equilibrium and source terms share their even parts.
 template <typename T, bool ODD, bool REC>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_lattice(LbView L)
+__device__ __forceinline__ bool lattice_node(const LbView &L, const int x, const int y, const int z)
 {
     const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
     bool bad = false;
-    if (x < nx && y < ny) {
+    {
         const int nxy = nx * ny;
         const int node = x + nx * y + nxy * z;
         T *__restrict__ f = static_cast<T *>(L.f);
@@ -365,7 +362,49 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_lattice(LbView 
             rec[6 * nodes + node] = Fz;
         }
     }
+    return bad;
+}
+
+template <typename T, bool ODD, bool REC>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_lattice(LbView L)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    bool bad = false;
+    if (x < L.n[0] && y < L.n[1]) bad = lattice_node<T, ODD, REC>(L, x, y, z);
     // sticky instability flag, one atomic per warp at most
+    const unsigned m = __ballot_sync(0xffffffffu, bad);
+    if (m != 0u && (threadIdx.x & 31) == 0) atomicOr(&L.ctl->err, IBL_ERRBIT_UNSTABLE);
+}
+
+// Ensemble: one launch over the lattices of all members.  Block b belongs to
+// member blk_member[b] and covers its 256 consecutive nodes starting at
+// 256 * (b - blk_start[member]) in x-fastest order.
+template <typename T, bool ODD>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
+    k_lattice_batched(const LbView *__restrict__ views, const int *__restrict__ blk_member,
+                      const int *__restrict__ blk_start)
+{
+    const int mi = blk_member[blockIdx.x];
+    const LbView &L = views[mi];
+    const int nx = L.n[0], ny = L.n[1];
+    const int lin0 = (blockIdx.x - blk_start[mi]) * 256;
+    const int nxy = nx * ny;
+    const int z0 = lin0 / nxy;
+    const int rem = lin0 - z0 * nxy;
+    const int y0 = rem / nx;
+    int x = rem - y0 * nx + (int)threadIdx.x, y = y0, z = z0;
+    while (x >= nx) {  // at most 256 / nx carries
+        x -= nx;
+        ++y;
+    }
+    while (y >= ny) {
+        y -= ny;
+        ++z;
+    }
+    bool bad = false;
+    if (lin0 + (int)threadIdx.x < L.nodes) bad = lattice_node<T, ODD, false>(L, x, y, z);
     const unsigned m = __ballot_sync(0xffffffffu, bad);
     if (m != 0u && (threadIdx.x & 31) == 0) atomicOr(&L.ctl->err, IBL_ERRBIT_UNSTABLE);
 }
@@ -447,6 +486,7 @@ __device__ __forceinline__ int wrap_index(int g, int n, bool periodic)
 }
 
 constexpr int kLanesPerNode = 16;  // lane = (b, c) row of the 4x4x4 stencil
+constexpr int kIbThreads = 128;    // threads per block of the node-group kernels
 
 // Per-node stencil of the 16-lane group: lanes 0..2 compute, in FP64, the
 // origin base_a = floor(r_a) - 1 and the exact fraction r_a - floor(r_a) of
@@ -563,9 +603,8 @@ __device__ void patch_from_rows(const LbView &L, const MeshView &M)
 // Scaled unit normal of every triangle, m_t = -sigma/2 N/|N| with
 // N = (x1 - x0) x (x2 - x0), so that the force of Eq. (pi_drop) on vertex k
 // of the triangle is m_t x (x_{k+2} - x_{k+1}).  FP64.
-__global__ void __launch_bounds__(256) k_tri(MeshView M)
+__device__ __forceinline__ void tri_body(const MeshView &M, const int t)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= M.nt) return;
     const int v0 = M.tris[3 * t], v1 = M.tris[3 * t + 1], v2 = M.tris[3 * t + 2];
     double e1[3], e2[3], N[3];
@@ -580,16 +619,18 @@ __global__ void __launch_bounds__(256) k_tri(MeshView M)
     M.tn[3 * t + 2] = s * N[2];
 }
 
+__global__ void __launch_bounds__(256) k_tri(MeshView M) { tri_body(M, blockIdx.x * blockDim.x + threadIdx.x); }
+
 // Nodal force F_i = -sigma dA/dx_i (Eq. (pi_drop)) gathered over the
 // triangles around node i, then spread with the 4-point delta
 // (Eq. (ibm_force_d)(a)) by atomic adds into the Eulerian force.  Sixteen
 // lanes per node: the lanes split the incident triangles (reduced with
 // shuffles), then each lane adds one x-row of four stencil points.
 template <typename T>
-__global__ void __launch_bounds__(128) k_spread(LbView L, MeshView M)
+__device__ __forceinline__ void spread_body(const LbView &L, const MeshView &M, const int blk)
 {
-    if (blockIdx.x == 0 && threadIdx.x < 32) patch_from_rows(L, M);
-    const int gid = blockIdx.x * (blockDim.x / kLanesPerNode) + threadIdx.x / kLanesPerNode;
+    if (blk == 0 && threadIdx.x < 32) patch_from_rows(L, M);
+    const int gid = blk * (kIbThreads / kLanesPerNode) + threadIdx.x / kLanesPerNode;
     const int lane = threadIdx.x % kLanesPerNode;
     const bool valid = gid < M.nv;
     const int i = valid ? gid : M.nv - 1;
@@ -639,9 +680,15 @@ __global__ void __launch_bounds__(128) k_spread(LbView L, MeshView M)
 }
 
 template <typename T>
-__global__ void __launch_bounds__(128) k_interp(LbView L, MeshView M)
+__global__ void __launch_bounds__(128) k_spread(LbView L, MeshView M)
 {
-    const int gid = blockIdx.x * (blockDim.x / kLanesPerNode) + threadIdx.x / kLanesPerNode;
+    spread_body<T>(L, M, blockIdx.x);
+}
+
+template <typename T>
+__device__ __forceinline__ void interp_body(const LbView &L, const MeshView &M, const int blk, const int nblk)
+{
+    const int gid = blk * (kIbThreads / kLanesPerNode) + threadIdx.x / kLanesPerNode;
     const int lane = threadIdx.x % kLanesPerNode;
     const bool valid = gid < M.nv;
     const int i = valid ? gid : M.nv - 1;
@@ -707,14 +754,48 @@ __global__ void __launch_bounds__(128) k_interp(LbView L, MeshView M)
                 mn = fmin(mn, smn[a][w]);
                 mx = fmax(mx, smx[a][w]);
             }
-            M.part[6 * blockIdx.x + a] = mn;
-            M.part[6 * blockIdx.x + 3 + a] = mx;
+            M.part[6 * blk + a] = mn;
+            M.part[6 * blk + 3 + a] = mx;
         }
-        if (blockIdx.x == 0) {
-            L.ctl->n_part = gridDim.x;
+        if (blk == 0) {
+            L.ctl->n_part = nblk;
             close_step(L);  // nothing reads the step counter during this kernel
         }
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_interp(LbView L, MeshView M)
+{
+    interp_body<T>(L, M, blockIdx.x, gridDim.x);
+}
+
+// Ensemble versions: block b works for member blk_member[b] as its local
+// block b - blk_start[member]; node-group kernels use ceil(nv/8) blocks per
+// member, the triangle kernel ceil(nt/256).
+__global__ void __launch_bounds__(256)
+    k_tri_batched(const MeshView *__restrict__ mv, const int *__restrict__ blk_member, const int *__restrict__ blk_start)
+{
+    const int mi = blk_member[blockIdx.x];
+    tri_body(mv[mi], (blockIdx.x - blk_start[mi]) * blockDim.x + threadIdx.x);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128)
+    k_spread_batched(const LbView *__restrict__ lv, const MeshView *__restrict__ mv, const int *__restrict__ blk_member,
+                     const int *__restrict__ blk_start)
+{
+    const int mi = blk_member[blockIdx.x];
+    spread_body<T>(lv[mi], mv[mi], blockIdx.x - blk_start[mi]);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128)
+    k_interp_batched(const LbView *__restrict__ lv, const MeshView *__restrict__ mv, const int *__restrict__ blk_member,
+                     const int *__restrict__ blk_start)
+{
+    const int mi = blk_member[blockIdx.x];
+    interp_body<T>(lv[mi], mv[mi], blockIdx.x - blk_start[mi], blk_start[mi + 1] - blk_start[mi]);
 }
 
 // ---------------------------------------------------------------------------
@@ -1068,17 +1149,17 @@ cudaError_t launch_advance(const LbView &L, cudaStream_t s)
 cudaError_t launch_spread(const LbView &L, const MeshView &M, cudaStream_t s)
 {
     k_tri<<<blocks_for(M.nt, 256), 256, 0, s>>>(M);
-    const unsigned g = blocks_for((long long)M.nv * kLanesPerNode, 128);
-    if (L.precision == IBL_FP64) k_spread<double><<<g, 128, 0, s>>>(L, M);
-    else k_spread<float><<<g, 128, 0, s>>>(L, M);
+    const unsigned g = blocks_for((long long)M.nv * kLanesPerNode, kIbThreads);
+    if (L.precision == IBL_FP64) k_spread<double><<<g, kIbThreads, 0, s>>>(L, M);
+    else k_spread<float><<<g, kIbThreads, 0, s>>>(L, M);
     return cudaGetLastError();
 }
 
 cudaError_t launch_interp(const LbView &L, const MeshView &M, cudaStream_t s)
 {
-    const unsigned g = blocks_for((long long)M.nv * kLanesPerNode, 128);
-    if (L.precision == IBL_FP64) k_interp<double><<<g, 128, 0, s>>>(L, M);
-    else k_interp<float><<<g, 128, 0, s>>>(L, M);
+    const unsigned g = blocks_for((long long)M.nv * kLanesPerNode, kIbThreads);
+    if (L.precision == IBL_FP64) k_interp<double><<<g, kIbThreads, 0, s>>>(L, M);
+    else k_interp<float><<<g, kIbThreads, 0, s>>>(L, M);
     return cudaGetLastError();
 }
 
@@ -1099,6 +1180,23 @@ cudaError_t launch_observables(const LbView &L, const MeshView &M, cudaStream_t 
 cudaError_t launch_patch_from_mesh(const LbView &L, const MeshView &M, cudaStream_t s)
 {
     k_patch<<<1, 256, 0, s>>>(L, M);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ensemble_step(const EnsembleView &E, bool odd, cudaStream_t s)
+{
+    k_tri_batched<<<E.tri_blocks, 256, 0, s>>>(E.mv, E.tri_member, E.tri_start);
+    if (E.precision == IBL_FP64) {
+        k_spread_batched<double><<<E.node_blocks, kIbThreads, 0, s>>>(E.lv, E.mv, E.node_member, E.node_start);
+        if (odd) k_lattice_batched<double, true><<<E.lat_blocks, 256, 0, s>>>(E.lv, E.lat_member, E.lat_start);
+        else k_lattice_batched<double, false><<<E.lat_blocks, 256, 0, s>>>(E.lv, E.lat_member, E.lat_start);
+        k_interp_batched<double><<<E.node_blocks, kIbThreads, 0, s>>>(E.lv, E.mv, E.node_member, E.node_start);
+    } else {
+        k_spread_batched<float><<<E.node_blocks, kIbThreads, 0, s>>>(E.lv, E.mv, E.node_member, E.node_start);
+        if (odd) k_lattice_batched<float, true><<<E.lat_blocks, 256, 0, s>>>(E.lv, E.lat_member, E.lat_start);
+        else k_lattice_batched<float, false><<<E.lat_blocks, 256, 0, s>>>(E.lv, E.lat_member, E.lat_start);
+        k_interp_batched<float><<<E.node_blocks, kIbThreads, 0, s>>>(E.lv, E.mv, E.node_member, E.node_start);
+    }
     return cudaGetLastError();
 }
 

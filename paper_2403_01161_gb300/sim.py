@@ -242,3 +242,40 @@ class Sim:
         L.check(self.lib.ibl_profile_read(self.h, _dp(ms), cnt))
         return {"lattice": (float(ms[0]), int(cnt[0])), "spread": (float(ms[1]), int(cnt[1])),
                 "interp": (float(ms[2]), int(cnt[2]))}
+
+
+class Ensemble:
+    """Droplets advanced together by batched kernels (one launch per phase
+    for all members).  members: Sim objects, each with a droplet, same
+    precision and stream, same step count.  The members stay alive with the
+    ensemble and keep their per-member readouts."""
+
+    def __init__(self, members):
+        self.lib = L.load()
+        self.members = list(members)
+        arr = (ctypes.c_void_p * len(self.members))(*[m.h.value for m in self.members])
+        self._arr = arr
+        nbytes = ctypes.c_size_t()
+        L.check(self.lib.ibl_ensemble_workspace_size(len(self.members), arr, ctypes.byref(nbytes)))
+        self.ws = _workspace(nbytes.value, self.members[0].device)
+        h = ctypes.c_void_p()
+        L.check(self.lib.ibl_ensemble_create(len(self.members), arr, ctypes.c_void_p(self.ws.data_ptr()),
+                                             nbytes.value, ctypes.byref(h)))
+        self.h = h
+
+    def step(self, n: int = 1):
+        L.check(self.lib.ibl_ensemble_step(self.h, int(n)))
+
+    def sync(self):
+        L.check(self.lib.ibl_ensemble_sync(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.ibl_ensemble_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
