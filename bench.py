@@ -180,6 +180,72 @@ def cpu_baseline(w, budget_s=15.0, max_steps=400):
             "sample": "%d FP64 oracle steps of %s (steps 1..%d of the trajectory), %.1f s" % (n, w.name, n, dt)}
 
 
+def ensemble_partition(sizes, world):
+    """Longest-processing-time assignment of members (by node count) to ranks."""
+    load = [0] * world
+    owner = [0] * len(sizes)
+    for k in sorted(range(len(sizes)), key=lambda k: -sizes[k]):
+        r = min(range(world), key=lambda j: load[j])
+        owner[k] = r
+        load[r] += sizes[k]
+    return owner
+
+
+def measure_ensemble(dev, steps, warmup, rank, world):
+    """Batched ensemble of the 64 uneven droplets (boxes 48^3..96^3, R 6..10,
+    own OU trajectories) against the same droplets stepped one at a time.
+    Returns droplet-steps/s of both (whole job), or None on ranks without work."""
+    import torch
+
+    from paper_2403_01161_gb300 import config
+    from paper_2403_01161_gb300.sim import Ensemble, Sim
+
+    ws = config.ensemble_workloads(64, steps=warmup + 2 * steps + 8)
+    owner = ensemble_partition([w.nodes for w in ws], world)
+    mine = [w for k, w in enumerate(ws) if owner[k] == rank]
+    sims = []
+    for w in mine:
+        g = Sim(w.n, w.tau, w.frames, w.n_hold, precision=w.precision, device=dev)
+        g.add_icosphere(w.level, w.R, w.sigma)
+        g.set_readout(100)
+        sims.append(g)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn):
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return max_over_ranks(e0.elapsed_time(e1) * 1e-3, world, dev)
+
+    E = Ensemble(sims) if sims else None
+    if E:
+        E.step(warmup)
+    t_ens = timed(lambda: E.step(steps) if E else None)
+    if E:
+        E.sync()
+        E.close()
+    for g in sims:
+        g.step(warmup)
+    t_seq = timed(lambda: [g.step(steps) for g in sims])
+    for g in sims:
+        g.sync()
+        g.close()
+    return {"metric": "droplet-steps/s", "value": len(ws) * steps / t_ens,
+            "one_at_a_time": len(ws) * steps / t_seq, "speedup": t_seq / t_ens, "members": len(ws),
+            "total_nodes": sum(w.nodes for w in ws), "steps": steps, "warmup": warmup,
+            "ms_per_step": t_ens / steps * 1e3,
+            "mlups": sum(w.nodes for w in ws) * steps / t_ens / 1e6,
+            "config": "64 droplets, boxes 48^3-96^3 (seeds 1000-1063), R 6-10, icosphere level 3 or 4, "
+                      "own OU gradients, FP32; baseline: the same droplets stepped one after another with "
+                      "the single-droplet kernels (graph replay each)"}
+
+
 def run_reference(args):
     rank, world, _ = dist_info()
     if rank != 0:
@@ -280,6 +346,8 @@ def run_ours(args):
            "h2d_bytes_per_step": 72.0 / w.n_hold, "d2h_bytes_per_step": rec_bytes / w.n_hold,
            "steps": e2e_steps, "api": "ibl_run_frames (host gradients in, host shape records out)"}
 
+    ens = measure_ensemble(dev, args.ensemble_steps, 20, rank, world)
+
     if rank == 0:
         cb = cpu_baseline(w) if world == 1 else None
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -292,6 +360,7 @@ def run_ours(args):
                              "kernel_us": t_launch * 1e6 if t_launch else None, "launches_timed": lb_n,
                              "bytes_per_launch": BYTES_PER_NODE * w.nodes},
                 "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches * world, "clocks": clk,
+                "ensemble": ens,
                 "droplet_steps_per_s": world * args.steps / (ms * 1e-3),
                 "lagrangian_updates_per_s": world * (10 * 4 ** w.level + 2) * args.steps / (ms * 1e-3)}
         print(json.dumps(line))
@@ -306,9 +375,13 @@ def main():
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ensemble-steps", type=int, default=200,
+                    help="timed steps of the 64-droplet ensemble measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.ensemble_steps < 1:
+        ap.error("--ensemble-steps must be >= 1")
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

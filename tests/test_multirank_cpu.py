@@ -59,3 +59,14 @@ def test_reference_arm_other_ranks_exit_without_work(monkeypatch, capsys):
 
     assert bench.run_reference(A()) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_ensemble_partition_balances_nodes():
+    import bench
+
+    sizes = [96 ** 3, 48 ** 3, 88 ** 3, 56 ** 3, 64 ** 3, 80 ** 3, 72 ** 3, 48 ** 3]
+    owner = bench.ensemble_partition(sizes, 2)
+    load = [sum(s for s, o in zip(sizes, owner) if o == r) for r in range(2)]
+    assert set(owner) == {0, 1}
+    assert max(load) - min(load) <= max(sizes)
+    assert bench.ensemble_partition(sizes, 1) == [0] * len(sizes)
