@@ -273,6 +273,13 @@ void ibl_ensemble_destroy(ibl_ensemble *e);
 
 /* ---- introspection --------------------------------------------------- */
 
+/* Synchronises and returns the droplet patch of the next step: lower
+ * corner lo[3] and extents ext[3] (nodes - 1 per axis; -1 = empty).  With a
+ * droplet, each step updates the patch nodes on a high-priority helper
+ * stream next to the droplet kernels, and all other nodes on the bound
+ * stream concurrently. */
+int ibl_patch(ibl_lb *lb, int32_t lo[3], int32_t ext[3]);
+
 /* The library's D3Q19 velocities (19 x 3 int32) and weights (19 doubles). */
 int ibl_velocity_set(int32_t *c, double *w);
 

@@ -88,6 +88,7 @@ SIGNATURES = [
     ("ibl_ensemble_step", ctypes.c_int, [_P, ctypes.c_longlong]),
     ("ibl_ensemble_sync", ctypes.c_int, [_P]),
     ("ibl_ensemble_destroy", None, [_P]),
+    ("ibl_patch", ctypes.c_int, [_P, _I32, _I32]),
     ("ibl_velocity_set", ctypes.c_int, [_I32, _D]),
     ("ibl_profile_enable", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
     ("ibl_profile_read", ctypes.c_int, [_P, _D, ctypes.POINTER(ctypes.c_longlong)]),

@@ -150,12 +150,38 @@ struct ibl_lb {
     bool graphs = true;
     int chunk = 0;                       // steps per captured chunk (0 = none captured)
     cudaGraphExec_t gexec = nullptr;
-    cudaStream_t cap_stream = nullptr;   // private stream used only for capture
+    cudaStream_t cap_stream = nullptr;   // private streams used only for capture
+    cudaStream_t cap_helper = nullptr;
     bool capturing = false;
+    // With a droplet, a step runs on two streams: the bound stream carries the
+    // lattice update of the nodes outside the droplet patch, the high-priority
+    // helper stream the droplet kernels and the patch nodes.  evNear[p] marks
+    // the end of the patch-node update (or of a regularisation) of the last
+    // step of parity p, evFar[p] the end of the outside update and step count.
+    cudaStream_t helper = nullptr;
+    int hi_prio = 0;  // priority of the helper-stream kernels
+    cudaEvent_t evNear[2] = {nullptr, nullptr}, evFar[2] = {nullptr, nullptr};
+    cudaEvent_t evFork = nullptr, evJoin = nullptr;
+    // a separate set for graph capture (events recorded inside a capture
+    // cannot be waited on by eager launches)
+    cudaEvent_t cNear[2] = {nullptr, nullptr}, cFar[2] = {nullptr, nullptr};
+    cudaEvent_t cFork = nullptr, cJoin = nullptr;
     ~ibl_lb()
     {
         if (gexec) cudaGraphExecDestroy(gexec);
         if (cap_stream) cudaStreamDestroy(cap_stream);
+        if (cap_helper) cudaStreamDestroy(cap_helper);
+        if (helper) cudaStreamDestroy(helper);
+        for (int k = 0; k < 2; ++k) {
+            if (evNear[k]) cudaEventDestroy(evNear[k]);
+            if (evFar[k]) cudaEventDestroy(evFar[k]);
+            if (cNear[k]) cudaEventDestroy(cNear[k]);
+            if (cFar[k]) cudaEventDestroy(cFar[k]);
+        }
+        if (evFork) cudaEventDestroy(evFork);
+        if (evJoin) cudaEventDestroy(evJoin);
+        if (cFork) cudaEventDestroy(cFork);
+        if (cJoin) cudaEventDestroy(cJoin);
     }
 };
 
@@ -188,7 +214,7 @@ int lb_status_from_device(ibl_lb *lb)
 }
 
 // Returns the index of the end event to record after the launch, or -1.
-int prof_begin(ibl_lb *lb, int kind)
+int prof_begin(ibl_lb *lb, int kind, cudaStream_t s)
 {
     if (!((lb->prof.mask >> kind) & 1) || lb->prof.marks.size() >= Profiler::kMax) return -1;
     if ((lb->prof.mask & 8) && !lb->capturing) return -1;  // graph replays only
@@ -199,54 +225,87 @@ int prof_begin(ibl_lb *lb, int kind)
     const int idx = (int)lb->prof.used - 2;
     lb->prof.marks.push_back({kind, idx});
     // inside a capture the record must become a graph node of its own
-    if (lb->capturing) cudaEventRecordWithFlags(a, lb->stream, cudaEventRecordExternal);
-    else cudaEventRecord(a, lb->stream);
+    if (lb->capturing) cudaEventRecordWithFlags(a, s, cudaEventRecordExternal);
+    else cudaEventRecord(a, s);
     return idx + 1;
 }
 
-void prof_end(ibl_lb *lb, int end_idx)
+void prof_end(ibl_lb *lb, int end_idx, cudaStream_t s)
 {
     if (end_idx < 0) return;
-    if (lb->capturing) cudaEventRecordWithFlags(lb->prof.pool[end_idx], lb->stream, cudaEventRecordExternal);
-    else cudaEventRecord(lb->prof.pool[end_idx], lb->stream);
+    if (lb->capturing) cudaEventRecordWithFlags(lb->prof.pool[end_idx], s, cudaEventRecordExternal);
+    else cudaEventRecord(lb->prof.pool[end_idx], s);
 }
 
-int one_step(ibl_lb *lb, bool record)
+// One step.  sL: the bound stream (or the capture stream), sH: the helper
+// stream (or its capture twin).  Without a droplet everything runs on sL.
+int one_step(ibl_lb *lb, bool record, cudaStream_t sL, cudaStream_t sH)
 {
     cudaError_t e;
     ibl_mesh *m = lb->mesh;
-    const bool odd = (lb->host_step & 1) != 0;
-    if (m) {
-        const int pe = prof_begin(lb, PROF_SPREAD);
-        e = iblb::launch_spread(lb->v, m->v, lb->stream);
-        prof_end(lb, pe);
-        if (e != cudaSuccess) return cuda_fail(e, "spread launch");
-    }
-    const int pl = prof_begin(lb, PROF_LB);
-    e = iblb::launch_lattice(lb->v, odd, record, lb->stream);
-    prof_end(lb, pl);
-    if (e != cudaSuccess) return cuda_fail(e, "lattice launch");
+    const int par = (int)(lb->host_step & 1);
+    const bool odd = par != 0;
     const long long next = lb->host_step + 1;
+    const int pbuf = (int)(lb->host_step % 3), pnext = (int)(next % 3);
+    cudaEvent_t *evNear = lb->capturing ? lb->cNear : lb->evNear;
+    cudaEvent_t *evFar = lb->capturing ? lb->cFar : lb->evFar;
     if (!m) {
-        e = iblb::launch_advance(lb->v, lb->stream);
-        if (e != cudaSuccess) return cuda_fail(e, "step counter launch");
+        const int pl = prof_begin(lb, PROF_LB, sL);
+        e = iblb::launch_lattice(lb->v, odd, record, iblb::LAUNCH_FULL, pbuf, sL);
+        prof_end(lb, pl, sL);
+        if (e == cudaSuccess) e = iblb::launch_advance(lb->v, sL);
+        if (e != cudaSuccess) return cuda_fail(e, "lattice launch");
+        lb->host_step = next;
+        return IBL_OK;
     }
-    if (m) {
-        const int pi = prof_begin(lb, PROF_INTERP);
-        e = iblb::launch_interp(lb->v, m->v, lb->stream);
-        prof_end(lb, pi);
-        if (e != cudaSuccess) return cuda_fail(e, "interpolation launch");
-        if (m->reg_every > 0 && next % m->reg_every == 0) {
-            e = iblb::launch_regularize(lb->v, m->v, m->reg, lb->stream);
-            if (e != cudaSuccess) return cuda_fail(e, "regularisation launch");
-        }
-        if (m->readout_every > 0 && next % m->readout_every == 0) {
-            e = iblb::launch_observables(lb->v, m->v, lb->stream);
-            if (e != cudaSuccess) return cuda_fail(e, "observables launch");
-        }
+    // helper stream: forces + spread (and the next step's patch), then the
+    // patch nodes once the previous outside update has finished
+    const int ps = prof_begin(lb, PROF_SPREAD, sH);
+    e = iblb::launch_spread(lb->v, m->v, pnext, sH, lb->hi_prio);
+    prof_end(lb, ps, sH);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sH, evFar[par ^ 1], 0);
+    if (e == cudaSuccess) e = iblb::launch_near(lb->v, odd, record, pbuf, sH, lb->hi_prio);
+    if (e == cudaSuccess) e = cudaEventRecord(evNear[par], sH);
+    if (e != cudaSuccess) return cuda_fail(e, "droplet-side launch");
+    // bound stream: the outside nodes once the previous patch update (and
+    // regularisation) has finished; then the step counter
+    e = cudaStreamWaitEvent(sL, evNear[par ^ 1], 0);
+    const int pl = prof_begin(lb, PROF_LB, sL);
+    if (e == cudaSuccess) e = iblb::launch_lattice(lb->v, odd, record, iblb::LAUNCH_FAR, pbuf, sL);
+    prof_end(lb, pl, sL);
+    if (e == cudaSuccess) e = iblb::launch_advance(lb->v, sL);
+    if (e == cudaSuccess) e = cudaEventRecord(evFar[par], sL);
+    if (e != cudaSuccess) return cuda_fail(e, "lattice launch");
+    // helper stream: interpolation + advection, scheduled regularisation
+    // (which rewrites the next step's patch, so the next outside update
+    // waits for it) and shape record (which reads the step counter)
+    const int pi = prof_begin(lb, PROF_INTERP, sH);
+    e = iblb::launch_interp(lb->v, m->v, sH, lb->hi_prio);
+    prof_end(lb, pi, sH);
+    if (e != cudaSuccess) return cuda_fail(e, "interpolation launch");
+    if (m->reg_every > 0 && next % m->reg_every == 0) {
+        e = iblb::launch_regularize(lb->v, m->v, m->reg, pnext, sH, lb->hi_prio);
+        if (e == cudaSuccess) e = cudaEventRecord(evNear[par], sH);
+        if (e != cudaSuccess) return cuda_fail(e, "regularisation launch");
+    }
+    if (m->readout_every > 0 && next % m->readout_every == 0) {
+        // the record reads the step counter: after this step's count, and
+        // before the next step's (the next outside update waits for it)
+        e = cudaStreamWaitEvent(sH, evFar[par], 0);
+        if (e == cudaSuccess) e = iblb::launch_observables(lb->v, m->v, sH, lb->hi_prio);
+        if (e == cudaSuccess) e = cudaEventRecord(evNear[par], sH);
+        if (e != cudaSuccess) return cuda_fail(e, "observables launch");
     }
     lb->host_step = next;
     return IBL_OK;
+}
+
+// Orders `to` after everything enqueued so far on `from`.
+cudaError_t join(cudaStream_t from, cudaStream_t to, cudaEvent_t ev)
+{
+    cudaError_t e = cudaEventRecord(ev, from);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(to, ev, 0);
+    return e;
 }
 
 // ---- mesh construction (library's own implementation) ---------------------
@@ -435,7 +494,7 @@ int mesh_attach(ibl_lb *lb, int nv, const double *r, int nt, const int *tri_in, 
     up(L.nb_ptr, nb_ptr.data(), sizeof(int) * (nv + 1));
     up(L.nb_idx, nb_idx.data(), sizeof(int) * nb_idx.size());
     if (e == cudaSuccess) e = cudaMemsetAsync(w + L.fn, 0, sizeof(double) * 3 * nv, s);
-    if (e == cudaSuccess) e = iblb::launch_patch_from_mesh(lb->v, m->v, s);
+    if (e == cudaSuccess) e = iblb::launch_patch_from_mesh(lb->v, m->v, (int)(lb->host_step % 3), s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host vectors above are pageable temporaries
     if (e != cudaSuccess) {
         delete m;
@@ -462,11 +521,12 @@ void drop_graph(ibl_lb *lb)
 
 long long gcd_ll(long long a, long long b) { return b == 0 ? a : gcd_ll(b, a % b); }
 
-// Steps per chunk: a multiple of 2 (AA parity) and of the regularisation and
-// readout periods, at least 32; 0 when that would exceed 2048.
+// Steps per chunk: a multiple of 6 (AA parity and the three patch buffers)
+// and of the regularisation and readout periods, at least 32; 0 when that
+// would exceed 2048.
 int chunk_length(const ibl_lb *lb)
 {
-    long long c = 2;
+    long long c = 6;
     const ibl_mesh *m = lb->mesh;
     auto lcm = [&](long long a, long long b) { return a / gcd_ll(a, b) * b; };
     if (m && m->reg_every > 0) c = lcm(c, m->reg_every);
@@ -476,33 +536,62 @@ int chunk_length(const ibl_lb *lb)
     return (int)c;
 }
 
-// Captures one chunk starting at an aligned step (host_step % chunk == 0).
+// Creates the helper stream (highest priority) and the step events.
+int ensure_streams(ibl_lb *lb)
+{
+    if (lb->helper) return IBL_OK;
+    int lo = 0, hi = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    lb->hi_prio = hi;
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&lb->helper, cudaStreamNonBlocking, hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&lb->cap_stream, cudaStreamNonBlocking, lo);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&lb->cap_helper, cudaStreamNonBlocking, hi);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaEventCreateWithFlags(&lb->evNear[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&lb->evFar[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&lb->cNear[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&lb->cFar[k], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&lb->evFork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&lb->evJoin, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&lb->cFork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&lb->cJoin, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(e, "stream/event creation");
+    return IBL_OK;
+}
+
+// Captures one chunk starting at an aligned step (host_step % chunk == 0):
+// fork the helper capture stream off the main one, re-record the step
+// events inside the capture, run the steps, join back.
 int capture_chunk(ibl_lb *lb, int chunk)
 {
-    cudaError_t e = cudaSuccess;
-    if (!lb->cap_stream) e = cudaStreamCreateWithFlags(&lb->cap_stream, cudaStreamNonBlocking);
-    if (e != cudaSuccess) return cuda_fail(e, "capture stream");
+    int st = ensure_streams(lb);
+    if (st != IBL_OK) return st;
     const long long saved = lb->host_step;
-    cudaStream_t bound = lb->stream;
-    lb->stream = lb->cap_stream;
-    e = cudaStreamBeginCapture(lb->cap_stream, cudaStreamCaptureModeThreadLocal);
-    int st = IBL_OK;
-    if (e == cudaSuccess) {
-        lb->capturing = true;
-        for (int k = 0; k < chunk && st == IBL_OK; ++k) st = one_step(lb, false);
-        lb->capturing = false;
-        cudaGraph_t g = nullptr;
-        const cudaError_t e2 = cudaStreamEndCapture(lb->cap_stream, &g);
-        if (e2 != cudaSuccess && st == IBL_OK) st = cuda_fail(e2, "end capture");
-        if (st == IBL_OK) {
-            const cudaError_t e3 = cudaGraphInstantiate(&lb->gexec, g, 0);
-            if (e3 != cudaSuccess) st = cuda_fail(e3, "graph instantiate");
-        }
-        if (g) cudaGraphDestroy(g);
-    } else {
-        st = cuda_fail(e, "begin capture");
+    cudaStream_t cL = lb->cap_stream, cH = lb->cap_helper;
+    cudaError_t e = cudaStreamBeginCapture(cL, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "begin capture");
+    lb->capturing = true;
+    e = join(cL, cH, lb->cFork);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaEventRecord(lb->cNear[k], cH);
+        if (e == cudaSuccess) e = cudaEventRecord(lb->cFar[k], cL);
     }
-    lb->stream = bound;
+    if (e != cudaSuccess) st = cuda_fail(e, "capture fork");
+    for (int k = 0; k < chunk && st == IBL_OK; ++k) st = one_step(lb, false, cL, cH);
+    if (st == IBL_OK) {
+        e = join(cH, cL, lb->cJoin);
+        if (e != cudaSuccess) st = cuda_fail(e, "capture join");
+    }
+    lb->capturing = false;
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(cL, &g);
+    if (e2 != cudaSuccess && st == IBL_OK) st = cuda_fail(e2, "end capture");
+    if (st == IBL_OK) {
+        const cudaError_t e3 = cudaGraphInstantiateWithFlags(&lb->gexec, g, cudaGraphInstantiateFlagUseNodePriority);
+        if (e3 != cudaSuccess) st = cuda_fail(e3, "graph instantiate");
+    }
+    if (g) cudaGraphDestroy(g);
     lb->host_step = saved;
     if (st == IBL_OK) lb->chunk = chunk;
     else drop_graph(lb);
@@ -560,8 +649,6 @@ int ensemble_layout(int n, ibl_lb *const *members, EnsembleLayout &L, std::strin
         off = align256(off + b);
         return o;
     };
-    L.lv = take(sizeof(LbView) * n);
-    L.mv = take(sizeof(MeshView) * n);
     L.lat_member = take(sizeof(int) * lat);
     L.lat_start = take(sizeof(int) * (n + 1));
     L.node_member = take(sizeof(int) * node);
@@ -577,7 +664,7 @@ int ensemble_layout(int n, ibl_lb *const *members, EnsembleLayout &L, std::strin
 
 int ensemble_chunk(const ibl_ensemble *e)
 {
-    long long c = 2;
+    long long c = 6;
     auto lcm = [&](long long a, long long b) { return a / gcd_ll(a, b) * b; };
     for (ibl_lb *lb : e->m) {
         if (lb->mesh->reg_every > 0) c = lcm(c, lb->mesh->reg_every);
@@ -593,13 +680,13 @@ int ensemble_chunk(const ibl_ensemble *e)
 int ensemble_one_step(ibl_ensemble *e, cudaStream_t s)
 {
     const long long step = e->m[0]->host_step;
-    cudaError_t err = iblb::launch_ensemble_step(e->v, (step & 1) != 0, s);
+    cudaError_t err = iblb::launch_ensemble_step(e->v, step, s);
     if (err != cudaSuccess) return cuda_fail(err, "ensemble step launch");
     const long long next = step + 1;
     for (ibl_lb *lb : e->m) {
         ibl_mesh *mm = lb->mesh;
         if (mm->reg_every > 0 && next % mm->reg_every == 0) {
-            err = iblb::launch_regularize(lb->v, mm->v, mm->reg, s);
+            err = iblb::launch_regularize(lb->v, mm->v, mm->reg, (int)(next % 3), s);
             if (err != cudaSuccess) return cuda_fail(err, "ensemble regularisation launch");
         }
         if (mm->readout_every > 0 && next % mm->readout_every == 0) {
@@ -626,7 +713,7 @@ int ensemble_capture(ibl_ensemble *e, int chunk)
         const cudaError_t e2 = cudaStreamEndCapture(e->cap_stream, &g);
         if (e2 != cudaSuccess && st == IBL_OK) st = cuda_fail(e2, "end capture");
         if (st == IBL_OK) {
-            const cudaError_t e3 = cudaGraphInstantiate(&e->gexec, g, 0);
+            const cudaError_t e3 = cudaGraphInstantiateWithFlags(&e->gexec, g, cudaGraphInstantiateFlagUseNodePriority);
             if (e3 != cudaSuccess) st = cuda_fail(e3, "graph instantiate");
         }
         if (g) cudaGraphDestroy(g);
@@ -643,6 +730,21 @@ int ensemble_capture(ibl_ensemble *e, int chunk)
 extern "C" {
 
 const char *ibl_last_error(void) { return g_err.c_str(); }
+
+int ibl_patch(ibl_lb *lb, int32_t lo[3], int32_t ext[3])
+{
+    if (!lb || !lo || !ext) return fail(IBL_EINVAL, "null argument");
+    Ctl c;
+    cudaError_t e = cudaMemcpyAsync(&c, lb->v.ctl, sizeof c, cudaMemcpyDeviceToHost, lb->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(lb->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "patch readout");
+    const int b = (int)(lb->host_step % 3);
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = c.patch_lo[b][a];
+        ext[a] = c.patch_ext[b][a];
+    }
+    return IBL_OK;
+}
 
 int ibl_velocity_set(int32_t *c, double *w)
 {
@@ -708,10 +810,11 @@ int ibl_lb_create(const ibl_lb_params *p, const double *A_frames, int n_frames, 
     v.ctl = reinterpret_cast<Ctl *>(lb->ws + L.ctl);
     Ctl c;
     std::memset(&c, 0, sizeof c);
-    for (int a = 0; a < 4; ++a) {
-        c.patch_lo[a] = 0;
-        c.patch_ext[a] = -1;
-    }
+    for (int b = 0; b < 3; ++b)
+        for (int a = 0; a < 4; ++a) {
+            c.patch_lo[b][a] = 0;
+            c.patch_ext[b][a] = -1;
+        }
     const size_t es = p->precision == IBL_FP64 ? 8 : 4;
     cudaError_t e = cudaMemcpyAsync(v.ctl, &c, sizeof c, cudaMemcpyHostToDevice, lb->stream);
     if (e == cudaSuccess)
@@ -846,33 +949,47 @@ int ibl_set_readout(ibl_mesh *m, int every)
 int ibl_step(ibl_lb *lb, long long n)
 {
     if (!lb || n < 0) return fail(IBL_EINVAL, "bad step request");
+    if (n == 0) return IBL_OK;
+    int st = ensure_streams(lb);
+    if (st != IBL_OK) return st;
+    cudaStream_t sL = lb->stream, sH = lb->helper;
+    // the helper stream starts after everything already on the bound stream
+    cudaError_t e = join(sL, sH, lb->evFork);
+    if (e != cudaSuccess) return cuda_fail(e, "stream fork");
     const int chunk = lb->graphs ? chunk_length(lb) : 0;
     long long done = 0;
     if (chunk > 0) {
         // eager steps up to the next chunk boundary, then whole chunks by replay
         while (done < n && lb->host_step % chunk != 0) {
-            const int st = one_step(lb, false);
+            st = one_step(lb, false, sL, sH);
             if (st != IBL_OK) return st;
             ++done;
         }
         if (n - done >= chunk) {
             if (lb->chunk != chunk) {
                 drop_graph(lb);
-                const int st = capture_chunk(lb, chunk);
+                st = capture_chunk(lb, chunk);
                 if (st != IBL_OK) return st;
             }
+            e = join(sH, sL, lb->evJoin);  // the graph starts after all eager work
+            if (e != cudaSuccess) return cuda_fail(e, "stream join");
             while (n - done >= chunk) {
-                const cudaError_t e = cudaGraphLaunch(lb->gexec, lb->stream);
+                e = cudaGraphLaunch(lb->gexec, sL);
                 if (e != cudaSuccess) return cuda_fail(e, "graph launch");
                 lb->host_step += chunk;
                 done += chunk;
             }
+            e = join(sL, sH, lb->evFork);
+            if (e != cudaSuccess) return cuda_fail(e, "stream fork");
         }
     }
     for (; done < n; ++done) {
-        const int st = one_step(lb, false);
+        st = one_step(lb, false, sL, sH);
         if (st != IBL_OK) return st;
     }
+    // the bound stream resumes after all helper-stream work
+    e = join(sH, sL, lb->evJoin);
+    if (e != cudaSuccess) return cuda_fail(e, "stream join");
     return IBL_OK;
 }
 
@@ -889,9 +1006,16 @@ int ibl_step_record(ibl_lb *lb)
 {
     if (!lb) return fail(IBL_EINVAL, "null lattice");
     if (!lb->v.rec) return fail(IBL_EINVAL, "lattice created without record_fields");
-    const int st = one_step(lb, true);
-    if (st == IBL_OK) lb->recorded = true;
-    return st;
+    int st = ensure_streams(lb);
+    if (st != IBL_OK) return st;
+    cudaError_t e = join(lb->stream, lb->helper, lb->evFork);
+    if (e != cudaSuccess) return cuda_fail(e, "stream fork");
+    st = one_step(lb, true, lb->stream, lb->helper);
+    if (st != IBL_OK) return st;
+    e = join(lb->helper, lb->stream, lb->evJoin);
+    if (e != cudaSuccess) return cuda_fail(e, "stream join");
+    lb->recorded = true;
+    return IBL_OK;
 }
 
 int ibl_sync(ibl_lb *lb)
@@ -1038,7 +1162,7 @@ int ibl_regularize_now(ibl_mesh *m, int *iters)
 {
     if (!m || !m->lb) return fail(IBL_EINVAL, "null mesh");
     ibl_lb *lb = m->lb;
-    cudaError_t e = iblb::launch_regularize(lb->v, m->v, m->reg, lb->stream);
+    cudaError_t e = iblb::launch_regularize(lb->v, m->v, m->reg, (int)(lb->host_step % 3), lb->stream);
     if (e != cudaSuccess) return cuda_fail(e, "regularisation launch");
     Ctl c;
     e = cudaMemcpyAsync(&c, lb->v.ctl, sizeof c, cudaMemcpyDeviceToHost, lb->stream);
@@ -1125,8 +1249,6 @@ int ibl_ensemble_create(int n, ibl_lb *const *members, void *workspace, size_t b
     auto up = [&](size_t off, const void *src, size_t nbytes) {
         if (e == cudaSuccess) e = cudaMemcpyAsync(w + off, src, nbytes, cudaMemcpyHostToDevice, s);
     };
-    up(L.lv, lv.data(), sizeof(LbView) * n);
-    up(L.mv, mv.data(), sizeof(MeshView) * n);
     up(L.lat_member, lat_member.data(), sizeof(int) * lat_member.size());
     up(L.lat_start, lat_start.data(), sizeof(int) * lat_start.size());
     up(L.node_member, node_member.data(), sizeof(int) * node_member.size());
@@ -1139,17 +1261,17 @@ int ibl_ensemble_create(int n, ibl_lb *const *members, void *workspace, size_t b
     en->m.assign(members, members + n);
     en->stream = s;
     iblb::EnsembleView &v = en->v;
-    v.lv = reinterpret_cast<const LbView *>(w + L.lv);
-    v.mv = reinterpret_cast<const MeshView *>(w + L.mv);
+    v.lv = lv;
+    v.mv = mv;
     v.lat_member = reinterpret_cast<const int *>(w + L.lat_member);
-    v.lat_start = reinterpret_cast<const int *>(w + L.lat_start);
+    v.lat_start_d = reinterpret_cast<const int *>(w + L.lat_start);
     v.node_member = reinterpret_cast<const int *>(w + L.node_member);
-    v.node_start = reinterpret_cast<const int *>(w + L.node_start);
+    v.node_start_d = reinterpret_cast<const int *>(w + L.node_start);
     v.tri_member = reinterpret_cast<const int *>(w + L.tri_member);
-    v.tri_start = reinterpret_cast<const int *>(w + L.tri_start);
-    v.lat_blocks = L.lat_blocks;
-    v.node_blocks = L.node_blocks;
-    v.tri_blocks = L.tri_blocks;
+    v.tri_start_d = reinterpret_cast<const int *>(w + L.tri_start);
+    v.lat_start = lat_start;
+    v.node_start = node_start;
+    v.tri_start = tri_start;
     v.precision = m0->p.precision;
     *out = en;
     return IBL_OK;

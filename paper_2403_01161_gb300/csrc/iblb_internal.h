@@ -6,12 +6,16 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 
 #include "../../include/iblb.h"
 
 namespace iblb {
 
 // Device control block of one lattice (lives in the lattice workspace).
+// Patch buffers: step t uses buffer t % 3.  The force/spread kernel of step
+// t writes buffer (t + 1) % 3 while the outside update of step t - 1 may
+// still read buffer (t - 1) % 3, so three buffers are needed.
 struct alignas(128) Ctl {
     long long step;              // steps completed (advanced by the lattice kernel)
     unsigned int obs_blocks_done; // last-block ticket of the shape-record kernel
@@ -20,9 +24,8 @@ struct alignas(128) Ctl {
     int reg_iters;               // iterations of the latest regularisation
     int n_records;               // shape records written
     int frame;                   // frame index applied by the next step
-    int patch_lo[4];             // droplet patch: lower corner (normalised into the box)
-    int patch_ext[4];            // extent (hi - lo), -1 = empty
-    unsigned long long pad1[8];
+    int patch_lo[3][4];          // droplet patch of step t in buffer t % 3: lower corner (inside the box)
+    int patch_ext[3][4];         // extent (hi - lo), -1 = empty
 };
 
 // Views handed to kernels by value.
@@ -70,17 +73,27 @@ struct RegParams {
     int plus_sign;
 };
 
-// Device tables of an ensemble step (all members advance together).
+// An ensemble step launches each phase once per group of up to kGroup
+// members; the group's views travel by value in the kernel parameters (read
+// in constant space), the block -> member tables live in device memory.
+constexpr int kGroup = 64;
+struct LbGroup {
+    LbView v[kGroup];
+};
+struct MeshGroup {
+    MeshView v[kGroup];
+};
+
 struct EnsembleView {
-    const LbView *lv;        // [n] member lattices (device copy)
-    const MeshView *mv;      // [n] member meshes (device copy)
-    const int *lat_member;   // [lat_blocks] member of each lattice block
-    const int *lat_start;    // [n+1] first lattice block of each member
-    const int *node_member;  // [node_blocks]
-    const int *node_start;   // [n+1]
-    const int *tri_member;   // [tri_blocks]
-    const int *tri_start;    // [n+1]
-    int lat_blocks, node_blocks, tri_blocks;
+    std::vector<LbView> lv;      // host copies of the member views
+    std::vector<MeshView> mv;
+    const int *lat_member;       // [lat blocks] member of each lattice block (device)
+    const int *node_member;      // [node blocks]
+    const int *tri_member;       // [tri blocks]
+    const int *lat_start_d;      // [n+1] first block of each member (device)
+    const int *node_start_d;
+    const int *tri_start_d;
+    std::vector<int> lat_start, node_start, tri_start;  // host copies
     int precision;
 };
 
@@ -88,15 +101,18 @@ constexpr int kRingCap = 4096;
 constexpr int kObsBlocksMax = 304;
 
 cudaError_t launch_init(const LbView &L, cudaStream_t s);
-cudaError_t launch_lattice(const LbView &L, bool odd, bool record, cudaStream_t s);
+cudaError_t launch_lattice(const LbView &L, bool odd, bool record, int mode, int pbuf, cudaStream_t s);
+cudaError_t launch_near(const LbView &L, bool odd, bool record, int pbuf, cudaStream_t s, int prio = 0);
+enum { LAUNCH_FULL = 0, LAUNCH_FAR = 1 };
 cudaError_t launch_advance(const LbView &L, cudaStream_t s);
 cudaError_t launch_convert_frames(const LbView &L, int k0, int k1, cudaStream_t s);
-cudaError_t launch_spread(const LbView &L, const MeshView &M, cudaStream_t s);
-cudaError_t launch_interp(const LbView &L, const MeshView &M, cudaStream_t s);
-cudaError_t launch_regularize(const LbView &L, const MeshView &M, const RegParams &p, cudaStream_t s);
-cudaError_t launch_observables(const LbView &L, const MeshView &M, cudaStream_t s);
-cudaError_t launch_patch_from_mesh(const LbView &L, const MeshView &M, cudaStream_t s);
-cudaError_t launch_ensemble_step(const EnsembleView &E, bool odd, cudaStream_t s);
+cudaError_t launch_spread(const LbView &L, const MeshView &M, int next_buf, cudaStream_t s, int prio = 0);
+cudaError_t launch_interp(const LbView &L, const MeshView &M, cudaStream_t s, int prio = 0);
+cudaError_t launch_regularize(const LbView &L, const MeshView &M, const RegParams &p, int buf, cudaStream_t s,
+                              int prio = 0);
+cudaError_t launch_observables(const LbView &L, const MeshView &M, cudaStream_t s, int prio = 0);
+cudaError_t launch_patch_from_mesh(const LbView &L, const MeshView &M, int buf, cudaStream_t s);
+cudaError_t launch_ensemble_step(const EnsembleView &E, long long step, cudaStream_t s);
 
 // records a message for ibl_last_error() and returns `code` (iblb_api.cpp)
 int iblb_set_error(int code, const char *msg);

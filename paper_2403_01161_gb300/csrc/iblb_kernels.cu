@@ -208,11 +208,33 @@ __device__ __forceinline__ void bc_dispatch(T (&f)[19], const T (&uw)[3], int ru
 // division is needed.  Indices are 32-bit (19 * stride < 2^31 is checked on
 // the host).  The collision works on opposite pairs (c_i, -c_i), whose
 // equilibrium and source terms share their even parts.
-template <typename T, bool ODD, bool REC>
-__device__ __forceinline__ bool lattice_node(const LbView &L, const int x, const int y, const int z)
+// Node sets of one lattice launch: every node, reading the droplet patch's
+// force where the node lies in the patch (FULL); only the nodes outside the
+// patch (FAR); only patch nodes (NEAR).  FAR and NEAR launches of the same
+// step may run concurrently: in the AA pattern every population slot is read
+// and written by one node only within a step.
+enum { LAT_FULL = 0, LAT_FAR = 1, LAT_NEAR = 2 };
+
+__device__ __forceinline__ bool node_in_patch(const LbView &L, const Ctl *c, int buf, int x, int y, int z)
+{
+    int dx = x - c->patch_lo[buf][0], dy = y - c->patch_lo[buf][1], dz = z - c->patch_lo[buf][2];
+    if (L.bc[0] == IBL_BC_PERIODIC && dx < 0) dx += L.n[0];
+    if (L.bc[1] == IBL_BC_PERIODIC && dy < 0) dy += L.n[1];
+    if (L.bc[2] == IBL_BC_PERIODIC && dz < 0) dz += L.n[2];
+    // an empty patch has extent -1: no node is inside
+    return c->patch_ext[buf][0] >= 0 && (unsigned)dx <= (unsigned)c->patch_ext[buf][0] &&
+           (unsigned)dy <= (unsigned)c->patch_ext[buf][1] && (unsigned)dz <= (unsigned)c->patch_ext[buf][2];
+}
+
+template <typename T, bool ODD, bool REC, int MODE>
+__device__ __forceinline__ bool lattice_node(const LbView &L, const int x, const int y, const int z, const int pbuf)
 {
     const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
     bool bad = false;
+    // the patch of this step lives in buffer pbuf (step % 3)
+    bool in_patch = (MODE == LAT_NEAR);
+    if constexpr (MODE != LAT_NEAR) in_patch = node_in_patch(L, L.ctl, pbuf, x, y, z);
+    if (MODE == LAT_FAR && in_patch) return false;
     {
         const int nxy = nx * ny;
         const int node = x + nx * y + nxy * z;
@@ -266,17 +288,6 @@ __device__ __forceinline__ bool lattice_node(const LbView &L, const int x, const
         }
 
         // droplet patch: read the spread force (and clear it), store u below
-        bool in_patch;
-        {
-            const Ctl *c = L.ctl;
-            int dx = x - c->patch_lo[0], dy = y - c->patch_lo[1], dz = z - c->patch_lo[2];
-            if (px && dx < 0) dx += nx;
-            if (py && dy < 0) dy += ny;
-            if (pz && dz < 0) dz += nz;
-            // an empty patch has extent -1: no node is inside
-            in_patch = c->patch_ext[0] >= 0 && (unsigned)dx <= (unsigned)c->patch_ext[0] &&
-                       (unsigned)dy <= (unsigned)c->patch_ext[1] && (unsigned)dz <= (unsigned)c->patch_ext[2];
-        }
         T Fx = T(0), Fy = T(0), Fz = T(0);
         T *__restrict__ force = static_cast<T *>(L.force);
         const int nodes = L.nodes;
@@ -365,31 +376,59 @@ __device__ __forceinline__ bool lattice_node(const LbView &L, const int x, const
     return bad;
 }
 
-template <typename T, bool ODD, bool REC>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_lattice(LbView L)
+template <typename T, bool ODD, bool REC, int MODE>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? (ODD ? 3 : 4) : 2) k_lattice(LbView L, int pbuf)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     bool bad = false;
-    if (x < L.n[0] && y < L.n[1]) bad = lattice_node<T, ODD, REC>(L, x, y, z);
+    if (x < L.n[0] && y < L.n[1]) bad = lattice_node<T, ODD, REC, MODE>(L, x, y, z, pbuf);
     // sticky instability flag, one atomic per warp at most
     const unsigned m = __ballot_sync(0xffffffffu, bad);
     if (m != 0u && (threadIdx.x & 31) == 0) atomicOr(&L.ctl->err, IBL_ERRBIT_UNSTABLE);
 }
 
-// Ensemble: one launch over the lattices of all members.  Block b belongs to
-// member blk_member[b] and covers its 256 consecutive nodes starting at
-// 256 * (b - blk_start[member]) in x-fastest order.
-template <typename T, bool ODD>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
-    k_lattice_batched(const LbView *__restrict__ views, const int *__restrict__ blk_member,
-                      const int *__restrict__ blk_start)
+// The patch nodes of the step (grid-stride over the patch box, x fastest).
+template <typename T, bool ODD, bool REC>
+__global__ void __launch_bounds__(256) k_lattice_near(LbView L, int buf)
 {
-    const int mi = blk_member[blockIdx.x];
-    const LbView &L = views[mi];
+    const Ctl *c = L.ctl;
+    const int ex = c->patch_ext[buf][0] + 1, ey = c->patch_ext[buf][1] + 1, ez = c->patch_ext[buf][2] + 1;
+    const int lx = c->patch_lo[buf][0], ly = c->patch_lo[buf][1], lz = c->patch_lo[buf][2];
+    const int count = (ex > 0 && ey > 0 && ez > 0) ? ex * ey * ez : 0;
+    for (int base = blockIdx.x * blockDim.x; base < count; base += gridDim.x * blockDim.x) {
+        const int idx = base + threadIdx.x;
+        bool bad = false;
+        if (idx < count) {
+            const int pz = idx / (ex * ey);
+            const int rem = idx - pz * ex * ey;
+            const int py = rem / ex;
+            const int px = rem - py * ex;
+            int x = lx + px, y = ly + py, z = lz + pz;
+            if (x >= L.n[0]) x -= L.n[0];  // a periodic patch may wrap once
+            if (y >= L.n[1]) y -= L.n[1];
+            if (z >= L.n[2]) z -= L.n[2];
+            bad = lattice_node<T, ODD, REC, LAT_NEAR>(L, x, y, z, buf);
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, bad);
+        if (m != 0u && (threadIdx.x & 31) == 0) atomicOr(&L.ctl->err, IBL_ERRBIT_UNSTABLE);
+    }
+}
+
+// Ensemble: one launch over the lattices of a group of members.  Block b
+// works for member blk_member[b0 + b] (view G.v[member - m0], read from the
+// kernel parameters) and covers its 256 consecutive nodes starting at
+// 256 * (b0 + b - blk_start[member]) in x-fastest order.
+template <typename T, bool ODD>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? (ODD ? 3 : 4) : 2)
+    k_lattice_batched(const __grid_constant__ LbGroup G, const int m0, const int b0,
+                      const int *__restrict__ blk_member, const int *__restrict__ blk_start, const int pbuf)
+{
+    const int mi = blk_member[b0 + blockIdx.x];
+    const LbView &L = G.v[mi - m0];
     const int nx = L.n[0], ny = L.n[1];
-    const int lin0 = (blockIdx.x - blk_start[mi]) * 256;
+    const int lin0 = (b0 + (int)blockIdx.x - blk_start[mi]) * 256;
     const int nxy = nx * ny;
     const int z0 = lin0 / nxy;
     const int rem = lin0 - z0 * nxy;
@@ -404,7 +443,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
         ++z;
     }
     bool bad = false;
-    if (lin0 + (int)threadIdx.x < L.nodes) bad = lattice_node<T, ODD, false>(L, x, y, z);
+    if (lin0 + (int)threadIdx.x < L.nodes) bad = lattice_node<T, ODD, false, LAT_FULL>(L, x, y, z, pbuf);
     const unsigned m = __ballot_sync(0xffffffffu, bad);
     if (m != 0u && (threadIdx.x & 31) == 0) atomicOr(&L.ctl->err, IBL_ERRBIT_UNSTABLE);
 }
@@ -549,17 +588,19 @@ __device__ __forceinline__ void stencil_weights(const NodeStencil &S, int b, int
 // Patch of lattice nodes the droplet's stencils can touch, from the node
 // bounding box [mn, mx]: floor(mn)-1 .. floor(mx)+2 per axis (periodic axes
 // keep the lower corner inside the box and may wrap; Zou-He axes clamp).
-__device__ void write_patch(const LbView &L, const double mn[3], const double mx[3])
+// `grow` extra nodes on each side (1 covers the nodes' motion over one more
+// step: |u| <= 0.3 keeps floor(r) within one node).
+__device__ void write_patch(const LbView &L, const double mn[3], const double mx[3], int buf, int grow)
 {
     for (int a = 0; a < 3; ++a) {
         const int n = L.n[a];
         double lo_d = mn[a], hi_d = mx[a];
         if (!(lo_d > -1e8 && lo_d < 1e8) || !(hi_d > -1e8 && hi_d < 1e8) || hi_d < lo_d) {
-            L.ctl->patch_lo[a] = 0;
-            L.ctl->patch_ext[a] = n - 1;
+            L.ctl->patch_lo[buf][a] = 0;
+            L.ctl->patch_ext[buf][a] = n - 1;
             continue;
         }
-        long long lo = (long long)floor(lo_d) - 1, hi = (long long)floor(hi_d) + 2;
+        long long lo = (long long)floor(lo_d) - 1 - grow, hi = (long long)floor(hi_d) + 2 + grow;
         if (L.bc[a] == IBL_BC_PERIODIC) {
             if (hi - lo + 1 >= n) {
                 lo = 0;
@@ -575,14 +616,16 @@ __device__ void write_patch(const LbView &L, const double mn[3], const double mx
             if (hi > n - 1) hi = n - 1;
             if (hi < lo) hi = lo;
         }
-        L.ctl->patch_lo[a] = (int)lo;
-        L.ctl->patch_ext[a] = (int)(hi - lo);
+        L.ctl->patch_lo[buf][a] = (int)lo;
+        L.ctl->patch_ext[buf][a] = (int)(hi - lo);
     }
 }
 
-// Warp 0 of block 0 of the force/spread kernel: reduce the bounding-box rows
-// left by the previous interpolation (or regularisation) into the patch.
-__device__ void patch_from_rows(const LbView &L, const MeshView &M)
+// Warp 0 of block 0 of the force/spread kernel of step t: reduce the
+// bounding-box rows of r_t left by the previous interpolation (or
+// regularisation) into the patch of step t + 1, grown by one node, in
+// buffer `buf` (the parity of step t + 1).
+__device__ void patch_from_rows(const LbView &L, const MeshView &M, int buf)
 {
     const int lane = threadIdx.x & 31;
     const int rows = L.ctl->n_part;
@@ -597,7 +640,7 @@ __device__ void patch_from_rows(const LbView &L, const MeshView &M)
             mn[a] = fmin(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
             mx[a] = fmax(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
         }
-    if (lane == 0) write_patch(L, mn, mx);
+    if (lane == 0) write_patch(L, mn, mx, buf, 1);
 }
 
 // Scaled unit normal of every triangle, m_t = -sigma/2 N/|N| with
@@ -627,9 +670,9 @@ __global__ void __launch_bounds__(256) k_tri(MeshView M) { tri_body(M, blockIdx.
 // lanes per node: the lanes split the incident triangles (reduced with
 // shuffles), then each lane adds one x-row of four stencil points.
 template <typename T>
-__device__ __forceinline__ void spread_body(const LbView &L, const MeshView &M, const int blk)
+__device__ __forceinline__ void spread_body(const LbView &L, const MeshView &M, const int blk, const int next_buf)
 {
-    if (blk == 0 && threadIdx.x < 32) patch_from_rows(L, M);
+    if (blk == 0 && threadIdx.x < 32) patch_from_rows(L, M, next_buf);
     const int gid = blk * (kIbThreads / kLanesPerNode) + threadIdx.x / kLanesPerNode;
     const int lane = threadIdx.x % kLanesPerNode;
     const bool valid = gid < M.nv;
@@ -680,9 +723,9 @@ __device__ __forceinline__ void spread_body(const LbView &L, const MeshView &M, 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(128) k_spread(LbView L, MeshView M)
+__global__ void __launch_bounds__(128) k_spread(LbView L, MeshView M, int next_buf)
 {
-    spread_body<T>(L, M, blockIdx.x);
+    spread_body<T>(L, M, blockIdx.x, next_buf);
 }
 
 template <typename T>
@@ -757,10 +800,7 @@ __device__ __forceinline__ void interp_body(const LbView &L, const MeshView &M, 
             M.part[6 * blk + a] = mn;
             M.part[6 * blk + 3 + a] = mx;
         }
-        if (blk == 0) {
-            L.ctl->n_part = nblk;
-            close_step(L);  // nothing reads the step counter during this kernel
-        }
+        if (blk == 0) L.ctl->n_part = nblk;
     }
 }
 
@@ -770,32 +810,41 @@ __global__ void __launch_bounds__(128) k_interp(LbView L, MeshView M)
     interp_body<T>(L, M, blockIdx.x, gridDim.x);
 }
 
-// Ensemble versions: block b works for member blk_member[b] as its local
-// block b - blk_start[member]; node-group kernels use ceil(nv/8) blocks per
-// member, the triangle kernel ceil(nt/256).
+// Closes the step of every member of a group (one thread per member).
+__global__ void k_advance_batched(const __grid_constant__ LbGroup LG, const int count)
+{
+    if ((int)threadIdx.x < count) close_step(LG.v[threadIdx.x]);
+}
+
+// Ensemble versions: block b works for member blk_member[b0 + b] as its
+// local block b0 + b - blk_start[member]; node-group kernels use ceil(nv/8)
+// blocks per member, the triangle kernel ceil(nt/256).
 __global__ void __launch_bounds__(256)
-    k_tri_batched(const MeshView *__restrict__ mv, const int *__restrict__ blk_member, const int *__restrict__ blk_start)
+    k_tri_batched(const __grid_constant__ MeshGroup MG, const int m0, const int b0, const int *__restrict__ blk_member,
+                  const int *__restrict__ blk_start)
 {
-    const int mi = blk_member[blockIdx.x];
-    tri_body(mv[mi], (blockIdx.x - blk_start[mi]) * blockDim.x + threadIdx.x);
+    const int mi = blk_member[b0 + blockIdx.x];
+    tri_body(MG.v[mi - m0], (b0 + (int)blockIdx.x - blk_start[mi]) * blockDim.x + threadIdx.x);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(128)
-    k_spread_batched(const LbView *__restrict__ lv, const MeshView *__restrict__ mv, const int *__restrict__ blk_member,
-                     const int *__restrict__ blk_start)
+    k_spread_batched(const __grid_constant__ LbGroup LG, const __grid_constant__ MeshGroup MG, const int m0,
+                     const int b0, const int *__restrict__ blk_member, const int *__restrict__ blk_start,
+                     const int next_buf)
 {
-    const int mi = blk_member[blockIdx.x];
-    spread_body<T>(lv[mi], mv[mi], blockIdx.x - blk_start[mi]);
+    const int mi = blk_member[b0 + blockIdx.x];
+    spread_body<T>(LG.v[mi - m0], MG.v[mi - m0], b0 + (int)blockIdx.x - blk_start[mi], next_buf);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(128)
-    k_interp_batched(const LbView *__restrict__ lv, const MeshView *__restrict__ mv, const int *__restrict__ blk_member,
-                     const int *__restrict__ blk_start)
+    k_interp_batched(const __grid_constant__ LbGroup LG, const __grid_constant__ MeshGroup MG, const int m0,
+                     const int b0, const int *__restrict__ blk_member, const int *__restrict__ blk_start)
 {
-    const int mi = blk_member[blockIdx.x];
-    interp_body<T>(lv[mi], mv[mi], blockIdx.x - blk_start[mi], blk_start[mi + 1] - blk_start[mi]);
+    const int mi = blk_member[b0 + blockIdx.x];
+    interp_body<T>(LG.v[mi - m0], MG.v[mi - m0], b0 + (int)blockIdx.x - blk_start[mi],
+                   blk_start[mi + 1] - blk_start[mi]);
 }
 
 // ---------------------------------------------------------------------------
@@ -838,7 +887,7 @@ __device__ double block_max(double v, double *sh)
     return out;
 }
 
-__device__ void block_bbox_patch(const LbView &L, const MeshView &M, const double *r, int nv)
+__device__ void block_bbox_patch(const LbView &L, const MeshView &M, const double *r, int nv, int buf)
 {
     __shared__ double sh[32];
     double mn[3], mx[3];
@@ -852,7 +901,7 @@ __device__ void block_bbox_patch(const LbView &L, const MeshView &M, const doubl
         mx[a] = block_max(hi, sh);
     }
     if (threadIdx.x == 0) {
-        write_patch(L, mn, mx);
+        write_patch(L, mn, mx, buf, 1);
         for (int a = 0; a < 3; ++a) {
             M.part[a] = mn[a];
             M.part[3 + a] = mx[a];
@@ -863,7 +912,9 @@ __device__ void block_bbox_patch(const LbView &L, const MeshView &M, const doubl
 
 // Mesh regularisation, Sec. 3.3, one block: x_o fixed, x_q the previous
 // iterate, x_p the new one (ping-pong between r and s1), x_b in s2.
-__global__ void __launch_bounds__(1024) k_regularize(LbView L, MeshView M, RegParams p)
+// patch_buf: patch buffer (parity) of the next step, rewritten from the
+// regularised positions.
+__global__ void __launch_bounds__(1024) k_regularize(LbView L, MeshView M, RegParams p, int patch_buf)
 {
     __shared__ double sh[32];
     const int nv = M.nv;
@@ -916,16 +967,16 @@ __global__ void __launch_bounds__(1024) k_regularize(LbView L, MeshView M, RegPa
         for (int i = threadIdx.x; i < 3 * nv; i += blockDim.x) M.r[i] = M.s1[i];
     }
     __syncthreads();
-    block_bbox_patch(L, M, M.r, nv);
+    block_bbox_patch(L, M, M.r, nv, patch_buf);
     if (threadIdx.x == 0) {
         L.ctl->reg_iters = it;
         if (!conv) atomicOr(&L.ctl->err, IBL_ERRBIT_NOCONV);
     }
 }
 
-__global__ void __launch_bounds__(256) k_patch(LbView L, MeshView M)
+__global__ void __launch_bounds__(256) k_patch(LbView L, MeshView M, int buf)
 {
-    block_bbox_patch(L, M, M.r, M.nv);
+    block_bbox_patch(L, M, M.r, M.nv, buf);
 }
 
 // Symmetric 3x3 eigen-decomposition by cyclic Jacobi rotations: each
@@ -1085,6 +1136,25 @@ __global__ void __launch_bounds__(256) k_observables(LbView L, MeshView M)
 // launchers
 static inline unsigned blocks_for(long long n, int b) { return (unsigned)((n + b - 1) / b); }
 
+// Launch with an explicit scheduling priority (0 = the stream's own).  The
+// attribute is recorded into the kernel node under stream capture, which the
+// stream priority alone is not.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_p(void (*k)(KArgs...), dim3 g, dim3 b, cudaStream_t s, int prio, Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = g;
+    cfg.blockDim = b;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributePriority;
+    attr[0].val.priority = prio;
+    cfg.attrs = attr;
+    cfg.numAttrs = prio != 0 ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
+}
+
 cudaError_t launch_init(const LbView &L, cudaStream_t s)
 {
     const unsigned g = blocks_for(L.nodes, 256);
@@ -1101,28 +1171,54 @@ static void lattice_grid(const LbView &L, dim3 &grid, dim3 &block)
     grid = dim3((L.n[0] + bx - 1) / bx, (L.n[1] + by - 1) / by, L.n[2]);
 }
 
-cudaError_t launch_lattice(const LbView &L, bool odd, bool record, cudaStream_t s)
+template <typename T, bool ODD, bool REC>
+static void lattice_launch_t(const LbView &L, int mode, int pbuf, dim3 g, dim3 b, cudaStream_t s)
+{
+    if (mode == LAT_FAR) k_lattice<T, ODD, REC, LAT_FAR><<<g, b, 0, s>>>(L, pbuf);
+    else k_lattice<T, ODD, REC, LAT_FULL><<<g, b, 0, s>>>(L, pbuf);
+}
+
+cudaError_t launch_lattice(const LbView &L, bool odd, bool record, int mode, int pbuf, cudaStream_t s)
 {
     dim3 g, b;
     lattice_grid(L, g, b);
     if (L.precision == IBL_FP64) {
         if (odd) {
-            if (record) k_lattice<double, true, true><<<g, b, 0, s>>>(L);
-            else k_lattice<double, true, false><<<g, b, 0, s>>>(L);
+            if (record) lattice_launch_t<double, true, true>(L, mode, pbuf, g, b, s);
+            else lattice_launch_t<double, true, false>(L, mode, pbuf, g, b, s);
         } else {
-            if (record) k_lattice<double, false, true><<<g, b, 0, s>>>(L);
-            else k_lattice<double, false, false><<<g, b, 0, s>>>(L);
+            if (record) lattice_launch_t<double, false, true>(L, mode, pbuf, g, b, s);
+            else lattice_launch_t<double, false, false>(L, mode, pbuf, g, b, s);
         }
     } else {
         if (odd) {
-            if (record) k_lattice<float, true, true><<<g, b, 0, s>>>(L);
-            else k_lattice<float, true, false><<<g, b, 0, s>>>(L);
+            if (record) lattice_launch_t<float, true, true>(L, mode, pbuf, g, b, s);
+            else lattice_launch_t<float, true, false>(L, mode, pbuf, g, b, s);
         } else {
-            if (record) k_lattice<float, false, true><<<g, b, 0, s>>>(L);
-            else k_lattice<float, false, false><<<g, b, 0, s>>>(L);
+            if (record) lattice_launch_t<float, false, true>(L, mode, pbuf, g, b, s);
+            else lattice_launch_t<float, false, false>(L, mode, pbuf, g, b, s);
         }
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_near(const LbView &L, bool odd, bool record, int pbuf, cudaStream_t s, int prio)
+{
+    const dim3 g(2 * 152), b(256);  // grid-stride over the patch box
+    if (L.precision == IBL_FP64) {
+        if (odd) {
+            if (record) return launch_p(k_lattice_near<double, true, true>, g, b, s, prio, L, pbuf);
+            return launch_p(k_lattice_near<double, true, false>, g, b, s, prio, L, pbuf);
+        }
+        if (record) return launch_p(k_lattice_near<double, false, true>, g, b, s, prio, L, pbuf);
+        return launch_p(k_lattice_near<double, false, false>, g, b, s, prio, L, pbuf);
+    }
+    if (odd) {
+        if (record) return launch_p(k_lattice_near<float, true, true>, g, b, s, prio, L, pbuf);
+        return launch_p(k_lattice_near<float, true, false>, g, b, s, prio, L, pbuf);
+    }
+    if (record) return launch_p(k_lattice_near<float, false, true>, g, b, s, prio, L, pbuf);
+    return launch_p(k_lattice_near<float, false, false>, g, b, s, prio, L, pbuf);
 }
 
 template <typename T>
@@ -1146,58 +1242,77 @@ cudaError_t launch_advance(const LbView &L, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_spread(const LbView &L, const MeshView &M, cudaStream_t s)
+cudaError_t launch_spread(const LbView &L, const MeshView &M, int next_buf, cudaStream_t s, int prio)
 {
-    k_tri<<<blocks_for(M.nt, 256), 256, 0, s>>>(M);
-    const unsigned g = blocks_for((long long)M.nv * kLanesPerNode, kIbThreads);
-    if (L.precision == IBL_FP64) k_spread<double><<<g, kIbThreads, 0, s>>>(L, M);
-    else k_spread<float><<<g, kIbThreads, 0, s>>>(L, M);
-    return cudaGetLastError();
+    cudaError_t e = launch_p(k_tri, dim3(blocks_for(M.nt, 256)), dim3(256), s, prio, M);
+    if (e != cudaSuccess) return e;
+    const dim3 g(blocks_for((long long)M.nv * kLanesPerNode, kIbThreads)), b(kIbThreads);
+    if (L.precision == IBL_FP64) return launch_p(k_spread<double>, g, b, s, prio, L, M, next_buf);
+    return launch_p(k_spread<float>, g, b, s, prio, L, M, next_buf);
 }
 
-cudaError_t launch_interp(const LbView &L, const MeshView &M, cudaStream_t s)
+cudaError_t launch_interp(const LbView &L, const MeshView &M, cudaStream_t s, int prio)
 {
-    const unsigned g = blocks_for((long long)M.nv * kLanesPerNode, kIbThreads);
-    if (L.precision == IBL_FP64) k_interp<double><<<g, kIbThreads, 0, s>>>(L, M);
-    else k_interp<float><<<g, kIbThreads, 0, s>>>(L, M);
-    return cudaGetLastError();
+    const dim3 g(blocks_for((long long)M.nv * kLanesPerNode, kIbThreads)), b(kIbThreads);
+    if (L.precision == IBL_FP64) return launch_p(k_interp<double>, g, b, s, prio, L, M);
+    return launch_p(k_interp<float>, g, b, s, prio, L, M);
 }
 
-cudaError_t launch_regularize(const LbView &L, const MeshView &M, const RegParams &p, cudaStream_t s)
+cudaError_t launch_regularize(const LbView &L, const MeshView &M, const RegParams &p, int buf, cudaStream_t s,
+                              int prio)
 {
-    k_regularize<<<1, 1024, 0, s>>>(L, M, p);
-    return cudaGetLastError();
+    return launch_p(k_regularize, dim3(1), dim3(1024), s, prio, L, M, p, buf);
 }
 
-cudaError_t launch_observables(const LbView &L, const MeshView &M, cudaStream_t s)
+cudaError_t launch_observables(const LbView &L, const MeshView &M, cudaStream_t s, int prio)
 {
     int g = (M.nt + 255) / 256;
     if (g > kObsBlocksMax) g = kObsBlocksMax;
-    k_observables<<<g, 256, 0, s>>>(L, M);
+    return launch_p(k_observables, dim3(g), dim3(256), s, prio, L, M);
+}
+
+cudaError_t launch_patch_from_mesh(const LbView &L, const MeshView &M, int buf, cudaStream_t s)
+{
+    k_patch<<<1, 256, 0, s>>>(L, M, buf);
     return cudaGetLastError();
 }
 
-cudaError_t launch_patch_from_mesh(const LbView &L, const MeshView &M, cudaStream_t s)
+cudaError_t launch_ensemble_step(const EnsembleView &E, long long step, cudaStream_t s)
 {
-    k_patch<<<1, 256, 0, s>>>(L, M);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_ensemble_step(const EnsembleView &E, bool odd, cudaStream_t s)
-{
-    k_tri_batched<<<E.tri_blocks, 256, 0, s>>>(E.mv, E.tri_member, E.tri_start);
-    if (E.precision == IBL_FP64) {
-        k_spread_batched<double><<<E.node_blocks, kIbThreads, 0, s>>>(E.lv, E.mv, E.node_member, E.node_start);
-        if (odd) k_lattice_batched<double, true><<<E.lat_blocks, 256, 0, s>>>(E.lv, E.lat_member, E.lat_start);
-        else k_lattice_batched<double, false><<<E.lat_blocks, 256, 0, s>>>(E.lv, E.lat_member, E.lat_start);
-        k_interp_batched<double><<<E.node_blocks, kIbThreads, 0, s>>>(E.lv, E.mv, E.node_member, E.node_start);
-    } else {
-        k_spread_batched<float><<<E.node_blocks, kIbThreads, 0, s>>>(E.lv, E.mv, E.node_member, E.node_start);
-        if (odd) k_lattice_batched<float, true><<<E.lat_blocks, 256, 0, s>>>(E.lv, E.lat_member, E.lat_start);
-        else k_lattice_batched<float, false><<<E.lat_blocks, 256, 0, s>>>(E.lv, E.lat_member, E.lat_start);
-        k_interp_batched<float><<<E.node_blocks, kIbThreads, 0, s>>>(E.lv, E.mv, E.node_member, E.node_start);
+    const bool odd = (step & 1) != 0;
+    const int pbuf = (int)(step % 3);
+    const int n = (int)E.lv.size();
+    // parameter blocks are large: keep them off the stack
+    static thread_local LbGroup lg;
+    static thread_local MeshGroup mg;
+    for (int m0 = 0; m0 < n; m0 += kGroup) {
+        const int m1 = m0 + kGroup < n ? m0 + kGroup : n;
+        for (int k = m0; k < m1; ++k) {
+            lg.v[k - m0] = E.lv[k];
+            mg.v[k - m0] = E.mv[k];
+        }
+        const int tb0 = E.tri_start[m0], tb = E.tri_start[m1] - tb0;
+        const int nb0 = E.node_start[m0], nb = E.node_start[m1] - nb0;
+        const int lb0 = E.lat_start[m0], lbn = E.lat_start[m1] - lb0;
+        const int nxt = (int)((step + 1) % 3);  // patch buffer of the next step
+        k_tri_batched<<<tb, 256, 0, s>>>(mg, m0, tb0, E.tri_member, E.tri_start_d);
+        if (E.precision == IBL_FP64) {
+            k_spread_batched<double>
+                <<<nb, kIbThreads, 0, s>>>(lg, mg, m0, nb0, E.node_member, E.node_start_d, nxt);
+            if (odd) k_lattice_batched<double, true><<<lbn, 256, 0, s>>>(lg, m0, lb0, E.lat_member, E.lat_start_d, pbuf);
+            else k_lattice_batched<double, false><<<lbn, 256, 0, s>>>(lg, m0, lb0, E.lat_member, E.lat_start_d, pbuf);
+            k_interp_batched<double><<<nb, kIbThreads, 0, s>>>(lg, mg, m0, nb0, E.node_member, E.node_start_d);
+        } else {
+            k_spread_batched<float><<<nb, kIbThreads, 0, s>>>(lg, mg, m0, nb0, E.node_member, E.node_start_d, nxt);
+            if (odd) k_lattice_batched<float, true><<<lbn, 256, 0, s>>>(lg, m0, lb0, E.lat_member, E.lat_start_d, pbuf);
+            else k_lattice_batched<float, false><<<lbn, 256, 0, s>>>(lg, m0, lb0, E.lat_member, E.lat_start_d, pbuf);
+            k_interp_batched<float><<<nb, kIbThreads, 0, s>>>(lg, mg, m0, nb0, E.node_member, E.node_start_d);
+        }
+        k_advance_batched<<<1, kGroup, 0, s>>>(lg, m1 - m0);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
     }
-    return cudaGetLastError();
+    return cudaSuccess;
 }
 
 void velocity_table(int c[19][3], double w[19])

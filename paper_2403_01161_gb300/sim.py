@@ -230,6 +230,13 @@ class Sim:
         L.check(self.lib.ibl_run_frames(self.h, self.mesh_h, _dp(fr), fr.shape[0], int(steps_per_frame), out))
         return [out[k].as_dict() for k in range(fr.shape[0])]
 
+    def patch(self):
+        """(lo (3,), ext (3,)) of the droplet patch of the next step."""
+        lo = np.zeros(3, dtype=np.int32)
+        ext = np.zeros(3, dtype=np.int32)
+        L.check(self.lib.ibl_patch(self.h, _ip(lo), _ip(ext)))
+        return lo, ext
+
     # ---- timing --------------------------------------------------------------
     def profile(self, enable, mask: int = 7, every: int = 1):
         """Time kernels with CUDA events (mask bit 0 lattice, 1 spread, 2 interpolation;
