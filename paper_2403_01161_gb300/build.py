@@ -28,7 +28,7 @@ def sources():
 
 
 def _deps():
-    return sources() + [os.path.join(CSRC, "iblb_internal.h"),
+    return sources() + [os.path.join(CSRC, "iblb_internal.h"), os.path.join(CSRC, "iblb_device.cuh"),
                         os.path.join(os.path.dirname(HERE), "include", "iblb.h")]
 
 

@@ -23,53 +23,10 @@
 #include <utility>
 
 #include "iblb_internal.h"
+#include "iblb_device.cuh"
 
 namespace iblb {
 namespace {
-
-// ---------------------------------------------------------------------------
-// D3Q19 velocity set, library order: rest, nine "positive" links, then their
-// opposites at i + 9.  Weights 1/3, 1/18, 1/36 (Sec. 3.1).
-__host__ __device__ constexpr int cxf(int i)
-{
-    const int t[19] = {0, 1, 0, 0, 1, 1, 1, 1, 0, 0, -1, 0, 0, -1, -1, -1, -1, 0, 0};
-    return t[i];
-}
-__host__ __device__ constexpr int cyf(int i)
-{
-    const int t[19] = {0, 0, 1, 0, 1, -1, 0, 0, 1, 1, 0, -1, 0, -1, 1, 0, 0, -1, -1};
-    return t[i];
-}
-__host__ __device__ constexpr int czf(int i)
-{
-    const int t[19] = {0, 0, 0, 1, 0, 0, 1, -1, 1, -1, 0, 0, -1, 0, 0, -1, 1, -1, 1};
-    return t[i];
-}
-
-__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : (i <= 9 ? i + 9 : i - 9); }
-__host__ __device__ constexpr int c2(int i) { return cxf(i) * cxf(i) + cyf(i) * cyf(i) + czf(i) * czf(i); }
-__host__ __device__ constexpr int comp(int i, int a) { return a == 0 ? cxf(i) : (a == 1 ? cyf(i) : czf(i)); }
-__host__ __device__ constexpr double wgt(int i) { return c2(i) == 0 ? 1.0 / 3.0 : (c2(i) == 1 ? 1.0 / 18.0 : 1.0 / 36.0); }
-
-template <int... Is, class F>
-__device__ __forceinline__ void sfor_impl(std::integer_sequence<int, Is...>, F &&f)
-{
-    (f(std::integral_constant<int, Is>{}), ...);
-}
-template <int N, class F>
-__device__ __forceinline__ void sfor(F &&f)
-{
-    sfor_impl(std::make_integer_sequence<int, N>{}, f);
-}
-
-// ---------------------------------------------------------------------------
-// Box boundary (Sec. 3.1).  SX, SY, SZ = -1 on the plane l = 0, +1 on l = L,
-// 0 elsewhere.  Population j is unknown when its source x - c_j is outside.
-template <int SX, int SY, int SZ>
-__host__ __device__ constexpr bool unknown_dir(int j)
-{
-    return (SX != 0 && cxf(j) * SX < 0) || (SY != 0 && cyf(j) * SY < 0) || (SZ != 0 && czf(j) * SZ < 0);
-}
 
 template <typename T, int SX, int SY, int SZ>
 __device__ __forceinline__ void bc_apply(T (&f)[19], const T (&uw)[3], int rule)
@@ -484,107 +441,6 @@ __global__ void __launch_bounds__(256) k_init(LbView L)
 
 // ---------------------------------------------------------------------------
 // Immersed boundary.
-// Peskin 4-point stencil phi (Sec. 3.1), in the storage precision T.
-template <typename T>
-__device__ __forceinline__ T peskin_phi(T x)
-{
-    const T a = fabs(x);
-    if (a < T(1)) return T(0.125) * (T(3) - T(2) * a + sqrt(T(1) + T(4) * a - T(4) * a * a));
-    if (a < T(2)) return T(0.125) * (T(5) - T(2) * a - sqrt(T(-7) + T(12) * a - T(4) * a * a));
-    return T(0);
-}
-
-__device__ __forceinline__ void cross3(const double a[3], const double b[3], double o[3])
-{
-    o[0] = a[1] * b[2] - a[2] * b[1];
-    o[1] = a[2] * b[0] - a[0] * b[2];
-    o[2] = a[0] * b[1] - a[1] * b[0];
-}
-
-// The 4-point stencil along one axis starts at base = floor(r) - 1.  On a
-// Zou-He axis all four nodes must be interior (1..n-2); periodic axes wrap.
-struct AxisStencil {
-    int base;
-    bool ok;
-};
-__device__ __forceinline__ AxisStencil axis_stencil(double ra, int n, bool periodic)
-{
-    AxisStencil A;
-    A.ok = fabs(ra) < 1e8;
-    A.base = A.ok ? (int)floor(ra) - 1 : 0;
-    if (A.ok && !periodic) A.ok = A.base >= 1 && A.base + 3 <= n - 2;
-    return A;
-}
-__device__ __forceinline__ int wrap_index(int g, int n, bool periodic)
-{
-    if (periodic) {
-        g %= n;
-        if (g < 0) g += n;
-    }
-    return g;
-}
-
-constexpr int kLanesPerNode = 16;  // lane = (b, c) row of the 4x4x4 stencil
-constexpr int kIbThreads = 128;    // threads per block of the node-group kernels
-
-// Per-node stencil of the 16-lane group: lanes 0..2 compute, in FP64, the
-// origin base_a = floor(r_a) - 1 and the exact fraction r_a - floor(r_a) of
-// axis a, and every lane receives all three by shuffles.  The offset of
-// stencil point k is then frac + (1 - k), the correctly rounded r - (base+k).
-struct NodeStencil {
-    int base[3];
-    double frac[3];
-    bool ok;
-};
-__device__ __forceinline__ NodeStencil node_stencil(const LbView &L, const double *r, int lane)
-{
-    double ra = 0.0, fr = 0.0;
-    int base = 0;
-    bool ok = true;
-    if (lane < 3) {
-        ra = r[lane];
-        // select by value: indexing the parameter arrays with a runtime lane
-        // would copy the kernel parameters to local memory
-        const int na = lane == 0 ? L.n[0] : (lane == 1 ? L.n[1] : L.n[2]);
-        const int bca = lane == 0 ? L.bc[0] : (lane == 1 ? L.bc[1] : L.bc[2]);
-        const AxisStencil A = axis_stencil(ra, na, bca == IBL_BC_PERIODIC);
-        ok = A.ok;
-        base = A.base;
-        fr = ok ? ra - floor(ra) : 0.0;
-    }
-    const int w0 = (threadIdx.x & 31) & ~(kLanesPerNode - 1);
-    NodeStencil S;
-    S.ok = true;
-    // every lane executes every full-mask shuffle (no short-circuit around
-    // them: a lane that skipped one would leave the others waiting)
-    for (int a = 0; a < 3; ++a) {
-        S.base[a] = __shfl_sync(0xffffffffu, base, w0 + a);
-        S.frac[a] = __shfl_sync(0xffffffffu, fr, w0 + a);
-        const int ok_a = __shfl_sync(0xffffffffu, ok ? 1 : 0, w0 + a);
-        S.ok = S.ok && (ok_a != 0);
-    }
-    return S;
-}
-
-// Weights of the lane's x-row (w[0..3]) and of its y and z rows, in the
-// storage precision: offsets frac + (1 - k); in FP32 the fraction is
-// rounded to float first, in FP64 the offsets are the correctly rounded
-// r - (base + k).
-template <typename T>
-__device__ __forceinline__ void stencil_weights(const NodeStencil &S, int b, int c, T w[4], T &wy, T &wz)
-{
-    if constexpr (sizeof(T) == 8) {
-        for (int a = 0; a < 4; ++a) w[a] = peskin_phi<T>(S.frac[0] + (double)(1 - a));
-        wy = peskin_phi<T>(S.frac[1] + (double)(1 - b));
-        wz = peskin_phi<T>(S.frac[2] + (double)(1 - c));
-    } else {
-        const T fx = T(S.frac[0]), fy = T(S.frac[1]), fz = T(S.frac[2]);
-        for (int a = 0; a < 4; ++a) w[a] = peskin_phi<T>(fx + T(1 - a));
-        wy = peskin_phi<T>(fy + T(1 - b));
-        wz = peskin_phi<T>(fz + T(1 - c));
-    }
-}
-
 // Patch of lattice nodes the droplet's stencils can touch, from the node
 // bounding box [mn, mx]: floor(mn)-1 .. floor(mx)+2 per axis (periodic axes
 // keep the lower corner inside the box and may wrap; Zou-He axes clamp).
@@ -847,46 +703,6 @@ __global__ void __launch_bounds__(128)
                    blk_start[mi + 1] - blk_start[mi]);
 }
 
-// ---------------------------------------------------------------------------
-// Single-block reductions.
-template <int K>
-__device__ void block_sum(double (&v)[K], double (*sh)[K])
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int k = 0; k < K; ++k)
-        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-    if (lane == 0)
-        for (int k = 0; k < K; ++k) sh[warp][k] = v[k];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int k = 0; k < K; ++k) {
-            double s = 0.0;
-            for (int w = 0; w < nw; ++w) s += sh[w][k];
-            sh[0][k] = s;
-        }
-    }
-    __syncthreads();
-    for (int k = 0; k < K; ++k) v[k] = sh[0][k];
-    __syncthreads();
-}
-
-__device__ double block_max(double v, double *sh)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if (lane == 0) sh[warp] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double m = sh[0];
-        for (int w = 1; w < nw; ++w) m = fmax(m, sh[w]);
-        sh[0] = m;
-    }
-    __syncthreads();
-    const double out = sh[0];
-    __syncthreads();
-    return out;
-}
-
 __device__ void block_bbox_patch(const LbView &L, const MeshView &M, const double *r, int nv, int buf)
 {
     __shared__ double sh[32];
@@ -977,42 +793,6 @@ __global__ void __launch_bounds__(1024) k_regularize(LbView L, MeshView M, RegPa
 __global__ void __launch_bounds__(256) k_patch(LbView L, MeshView M, int buf)
 {
     block_bbox_patch(L, M, M.r, M.nv, buf);
-}
-
-// Symmetric 3x3 eigen-decomposition by cyclic Jacobi rotations: each
-// rotation J in the (p,q) plane with t = sgn(th)/(|th| + sqrt(th^2 + 1)),
-// th = (a_qq - a_pp)/(2 a_pq), c = 1/sqrt(1 + t^2), s = t c, annihilates a_pq.
-__device__ void jacobi3(double a[3][3], double lam[3], double v[3][3])
-{
-    for (int r = 0; r < 3; ++r)
-        for (int c = 0; c < 3; ++c) v[r][c] = (r == c) ? 1.0 : 0.0;
-    const double scale = fabs(a[0][0]) + fabs(a[1][1]) + fabs(a[2][2]) + 1e-300;
-    for (int sweep = 0; sweep < 60; ++sweep) {
-        const double off = fabs(a[0][1]) + fabs(a[0][2]) + fabs(a[1][2]);
-        if (off <= 1e-17 * scale) break;
-        for (int pq = 0; pq < 3; ++pq) {
-            const int p = pq == 2 ? 1 : 0;
-            const int q = pq == 0 ? 1 : 2;
-            const double apq = a[p][q];
-            if (apq == 0.0) continue;
-            const double th = (a[q][q] - a[p][p]) / (2.0 * apq);
-            const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-            const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
-            a[p][p] -= t * apq;
-            a[q][q] += t * apq;
-            a[p][q] = a[q][p] = 0.0;
-            const int r = 3 - p - q;
-            const double arp = a[r][p], arq = a[r][q];
-            a[r][p] = a[p][r] = c * arp - s * arq;
-            a[r][q] = a[q][r] = s * arp + c * arq;
-            for (int k = 0; k < 3; ++k) {
-                const double vkp = v[k][p], vkq = v[k][q];
-                v[k][p] = c * vkp - s * vkq;
-                v[k][q] = s * vkp + c * vkq;
-            }
-        }
-    }
-    for (int k = 0; k < 3; ++k) lam[k] = a[k][k];
 }
 
 // Shape record (Sec. 2): enclosed volume, centroid and second moment by
