@@ -271,6 +271,46 @@ int ibl_ensemble_step(ibl_ensemble *e, long long n);
 int ibl_ensemble_sync(ibl_ensemble *e);
 void ibl_ensemble_destroy(ibl_ensemble *e);
 
+/* ---- gradients of the deformation ------------------------------------ */
+
+/* Discrete adjoint of the IBLB trajectory (the paper has no counterpart:
+ * it differentiates the step of items 1-4 above, without regularisation).
+ * The objective is the Taylor deformation D of the droplet after n_steps
+ * steps from step 0 (Sec. 2: D from the eigenvalues of S = (5/V) int (x -
+ * x_c)(x - x_c)^T dV of the final mesh); the parameters are the surface
+ * tension sigma (Eq. (pi_drop)) and every velocity-gradient frame A_k
+ * (Eq. (velo_facce_cubo_da_gradiente), frame k held over steps
+ * [k N, (k + 1) N), the last frame for all later steps; frame 0 also sets
+ * the initial equilibrium populations).
+ *
+ * ibl_adjoint requires a droplet on `lb`, the step count at 0 and the
+ * regularisation off (every = 0).  It re-initialises the populations to
+ * the equilibrium of the current frame 0, runs the n_steps forward steps
+ * (graph replay as ibl_step) saving a checkpoint every K steps, then
+ * sweeps backwards: each segment of K steps is recomputed from its
+ * checkpoint, keeping the node positions and the density, velocity and
+ * force of every node for each step, and the adjoint of each step is taken
+ * in reverse (interpolation + advection, lattice update with the Zou-He
+ * rebuild, spreading, nodal forces).  Adjoint state: populations and
+ * Eulerian fields in the storage precision, node quantities and all
+ * accumulated gradients in FP64.
+ *
+ * Outputs (host, caller-owned, each may be NULL): *D; *dD_dsigma;
+ * dD_dA[9 k + 3 a + b] = dD/dA_k[a][b] for every frame k of the lattice
+ * (n_frames x 9 doubles); dD_dr0 = dD/dr of the initial node positions
+ * (n_nodes x 3).  Synchronising; on return the lattice and droplet hold the
+ * state after n_steps steps (shape records of the forward pass are kept,
+ * the recomputation writes none).  The workspace (device, 256-byte
+ * aligned, caller-owned, `bytes` from ibl_adjoint_workspace_size) holds
+ * ceil(n_steps / K) + 1 checkpoints (populations, control block, positions)
+ * plus min(K, n_steps) steps of recorded moments (7 values per lattice
+ * node) and positions, and the adjoint fields.  Errors: IBL_EINVAL for a
+ * bad state or argument, IBL_ENOMEM for a short workspace, and the sticky
+ * device errors of the forward and recomputed steps. */
+int ibl_adjoint_workspace_size(const ibl_lb *lb, long long n_steps, int K, size_t *bytes);
+int ibl_adjoint(ibl_lb *lb, long long n_steps, int K, void *workspace, size_t bytes, double *D, double *dD_dsigma,
+                double *dD_dA, double *dD_dr0);
+
 /* ---- introspection --------------------------------------------------- */
 
 /* Synchronises and returns the droplet patch of the next step: lower

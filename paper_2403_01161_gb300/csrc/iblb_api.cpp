@@ -725,6 +725,84 @@ int ensemble_capture(ibl_ensemble *e, int chunk)
     return st;
 }
 
+
+// ---- discrete adjoint: workspace layout and checkpoints --------------------
+// A checkpoint holds what the next steps read of the state: the populations
+// (in their AA slot layout), the control block (step, frame, patches), the
+// node positions and the bounding-box rows the next force kernel reduces.
+// The force field is zero between steps and the velocity field is written
+// before it is read, so neither is saved.
+struct AdjLayout {
+    size_t lam[2] = {0, 0}, lam_u = 0, lam_F = 0, rec = 0, traj = 0, lam_r = 0, lam_Fn = 0, tri_w = 0, acc = 0,
+           obs = 0, ck = 0, total = 0;
+    size_t rec_step = 0, traj_step = 0;                  // bytes per recorded step
+    size_t ck_f = 0, ck_ctl = 0, ck_r = 0, ck_part = 0;  // offsets inside one checkpoint
+    size_t f_bytes = 0, r_bytes = 0, part_bytes = 0, ck_step = 0;
+    long long n_seg = 0;
+};
+
+bool adj_layout(const ibl_lb *lb, const ibl_mesh *m, long long T, int K, AdjLayout &A)
+{
+    if (!lb || !m || T < 1 || K < 1) return false;
+    const size_t es = lb->p.precision == IBL_FP64 ? 8 : 4;
+    const size_t nodes = (size_t)lb->v.nodes;
+    const int nv = m->v.nv, nt = m->v.nt;
+    A.n_seg = (T + K - 1) / K;
+    const long long kmax = std::min<long long>(K, T);
+    A.f_bytes = es * 19 * (size_t)lb->v.qs;
+    A.r_bytes = sizeof(double) * 3 * (size_t)nv;
+    A.part_bytes = m->lay.obs_part - m->lay.part;
+    A.ck_f = 0;
+    A.ck_ctl = align256(A.f_bytes);
+    A.ck_r = A.ck_ctl + align256(sizeof(Ctl));
+    A.ck_part = A.ck_r + align256(A.r_bytes);
+    A.ck_step = A.ck_part + align256(A.part_bytes);
+    A.rec_step = align256(es * 7 * nodes);
+    A.traj_step = align256(A.r_bytes);
+    size_t off = 0;
+    auto take = [&](size_t b) {
+        const size_t o = off;
+        off = align256(off + b);
+        return o;
+    };
+    A.lam[0] = take(es * 19 * nodes);
+    A.lam[1] = take(es * 19 * nodes);
+    A.lam_u = take(es * 3 * nodes);
+    A.lam_F = take(es * 3 * nodes);
+    A.lam_r = take(A.r_bytes);
+    A.lam_Fn = take(A.r_bytes);
+    A.tri_w = take(sizeof(double) * 7 * (size_t)nt);
+    A.acc = take(sizeof(double) * (1 + 9 * (size_t)lb->v.n_frames));
+    A.obs = take(sizeof(double) * 11);
+    A.rec = take(A.rec_step * (size_t)kmax);
+    A.traj = take(A.traj_step * (size_t)kmax);
+    A.ck = take(A.ck_step * (size_t)(A.n_seg + 1));
+    A.total = off;
+    return true;
+}
+
+cudaError_t adj_save(ibl_lb *lb, const AdjLayout &A, char *ws, long long k, cudaStream_t s)
+{
+    char *c = ws + A.ck + A.ck_step * (size_t)k;
+    const ibl_mesh *m = lb->mesh;
+    cudaError_t e = cudaMemcpyAsync(c + A.ck_f, lb->v.f, A.f_bytes, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c + A.ck_ctl, lb->v.ctl, sizeof(Ctl), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c + A.ck_r, m->v.r, A.r_bytes, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c + A.ck_part, m->v.part, A.part_bytes, cudaMemcpyDeviceToDevice, s);
+    return e;
+}
+
+cudaError_t adj_restore(ibl_lb *lb, const AdjLayout &A, const char *ws, long long k, cudaStream_t s)
+{
+    const char *c = ws + A.ck + A.ck_step * (size_t)k;
+    const ibl_mesh *m = lb->mesh;
+    cudaError_t e = cudaMemcpyAsync(lb->v.f, c + A.ck_f, A.f_bytes, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(lb->v.ctl, c + A.ck_ctl, sizeof(Ctl), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(m->v.r, c + A.ck_r, A.r_bytes, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(m->v.part, c + A.ck_part, A.part_bytes, cudaMemcpyDeviceToDevice, s);
+    return e;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1359,6 +1437,128 @@ int ibl_profile_read(ibl_lb *lb, double ms[3], long long launches[3])
             launches[mk.first] += 1;
         }
     }
+    return IBL_OK;
+}
+
+int ibl_adjoint_workspace_size(const ibl_lb *lb, long long n_steps, int K, size_t *bytes)
+{
+    AdjLayout A;
+    if (!bytes) return fail(IBL_EINVAL, "null argument");
+    if (!lb || !lb->mesh) return fail(IBL_EINVAL, "the lattice has no droplet");
+    if (!adj_layout(lb, lb->mesh, n_steps, K, A)) return fail(IBL_EINVAL, "n_steps and K must be >= 1");
+    *bytes = A.total;
+    return IBL_OK;
+}
+
+int ibl_adjoint(ibl_lb *lb, long long n_steps, int K, void *workspace, size_t bytes, double *D, double *dD_dsigma,
+                double *dD_dA, double *dD_dr0)
+{
+    if (!lb || !lb->mesh) return fail(IBL_EINVAL, "the lattice has no droplet");
+    ibl_mesh *m = lb->mesh;
+    AdjLayout A;
+    if (!adj_layout(lb, m, n_steps, K, A)) return fail(IBL_EINVAL, "n_steps and K must be >= 1");
+    if (lb->host_step != 0) return fail(IBL_EINVAL, "the adjoint starts from step 0");
+    if (m->reg_every != 0) return fail(IBL_EINVAL, "the adjoint needs the regularisation switched off");
+    if (!workspace || bytes < A.total) return fail(IBL_ENOMEM, "adjoint workspace too small");
+    if (((uintptr_t)workspace & 255) != 0) return fail(IBL_EINVAL, "workspace must be 256-byte aligned");
+    int st = ensure_streams(lb);
+    if (st != IBL_OK) return st;
+    char *ws = static_cast<char *>(workspace);
+    cudaStream_t s = lb->stream;
+    const size_t es = lb->p.precision == IBL_FP64 ? 8 : 4;
+    const size_t nodes = (size_t)lb->v.nodes;
+    const int nf = lb->v.n_frames;
+    iblb::AdjView J;
+    J.lam_u = ws + A.lam_u;
+    J.lam_F = ws + A.lam_F;
+    J.lam_r = reinterpret_cast<double *>(ws + A.lam_r);
+    J.lam_Fn = reinterpret_cast<double *>(ws + A.lam_Fn);
+    J.tri_w = reinterpret_cast<double *>(ws + A.tri_w);
+    J.acc = reinterpret_cast<double *>(ws + A.acc);
+    J.obs = reinterpret_cast<double *>(ws + A.obs);
+    void *lam[2] = {ws + A.lam[0], ws + A.lam[1]};
+    cudaError_t e = cudaMemsetAsync(lam[0], 0, es * 19 * nodes, s);  // D does not depend on the final populations
+    if (e == cudaSuccess) e = cudaMemsetAsync(J.lam_u, 0, es * 3 * nodes, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(J.acc, 0, sizeof(double) * (1 + 9 * (size_t)nf), s);
+    // the initial state is the equilibrium of the current frame 0
+    if (e == cudaSuccess) e = iblb::launch_init(lb->v, s);
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint set-up");
+
+    // forward pass with a checkpoint at the start of every segment and one
+    // of the final state
+    for (long long sg = 0; sg < A.n_seg; ++sg) {
+        e = adj_save(lb, A, ws, sg, s);
+        if (e != cudaSuccess) return cuda_fail(e, "checkpoint");
+        st = ibl_step(lb, std::min<long long>(K, n_steps - sg * K));
+        if (st != IBL_OK) return st;
+    }
+    e = adj_save(lb, A, ws, A.n_seg, s);
+    // seed: D of the final mesh and dD/dr_T
+    if (e == cudaSuccess) e = iblb::launch_adj_seed(m->v, J, s);
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint seed");
+
+    // reverse sweep: recompute each segment eagerly on the bound stream,
+    // keeping r_t and the moments of every step, then step back through it
+    const int readout = m->readout_every;
+    m->readout_every = 0;  // the recomputation writes no shape records
+    void *rec_saved = lb->v.rec;
+    int cur = 0;  // lam[cur] holds the adjoint of the populations of step t + 1
+    st = IBL_OK;
+    for (long long sg = A.n_seg - 1; sg >= 0 && st == IBL_OK; --sg) {
+        const long long t0 = sg * K;
+        const int len = (int)std::min<long long>(K, n_steps - t0);
+        e = adj_restore(lb, A, ws, sg, s);
+        if (e != cudaSuccess) {
+            st = cuda_fail(e, "checkpoint restore");
+            break;
+        }
+        lb->host_step = t0;
+        for (int k = 0; k < len && st == IBL_OK; ++k) {
+            e = cudaMemcpyAsync(ws + A.traj + A.traj_step * k, m->v.r, A.r_bytes, cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) {
+                st = cuda_fail(e, "trajectory copy");
+                break;
+            }
+            lb->v.rec = ws + A.rec + A.rec_step * k;
+            st = one_step(lb, true, s, s);
+        }
+        lb->v.rec = rec_saved;
+        for (int k = len - 1; k >= 0 && st == IBL_OK; --k) {
+            MeshView Mt = m->v;
+            Mt.r = reinterpret_cast<double *>(ws + A.traj + A.traj_step * k);
+            const long long t = t0 + k;
+            const int frame = (int)std::min<long long>(t / lb->v.n_hold, nf - 1);
+            e = iblb::launch_adj_step(lb->v, Mt, J, ws + A.rec + A.rec_step * k, lam[cur], lam[cur ^ 1], frame, s);
+            if (e != cudaSuccess) st = cuda_fail(e, "adjoint step launch");
+            cur ^= 1;
+        }
+    }
+    m->readout_every = readout;
+    lb->v.rec = rec_saved;
+    // the initial populations depend on frame 0
+    if (st == IBL_OK) {
+        e = iblb::launch_adj_init(lb->v, J, lam[cur], s);
+        if (e != cudaSuccess) st = cuda_fail(e, "adjoint initial state");
+    }
+    // leave the lattice and droplet at the final step, as ibl_step would
+    if (st == IBL_OK) {
+        e = adj_restore(lb, A, ws, A.n_seg, s);
+        if (e != cudaSuccess) st = cuda_fail(e, "final state restore");
+    }
+    lb->host_step = n_steps;
+    if (st != IBL_OK) return st;
+    std::vector<double> acc(1 + 9 * (size_t)nf);
+    double obs0 = 0.0;
+    e = cudaMemcpyAsync(acc.data(), J.acc, sizeof(double) * acc.size(), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&obs0, J.obs, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && dD_dr0) e = cudaMemcpyAsync(dD_dr0, J.lam_r, A.r_bytes, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint readout");
+    st = lb_status_from_device(lb);
+    if (st != IBL_OK) return st;
+    if (D) *D = obs0;
+    if (dD_dsigma) *dD_dsigma = acc[0];
+    if (dD_dA) std::memcpy(dD_dA, acc.data() + 1, sizeof(double) * 9 * (size_t)nf);
     return IBL_OK;
 }
 

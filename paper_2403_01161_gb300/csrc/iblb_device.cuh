@@ -1,7 +1,8 @@
 // iblb_device.cuh -- device helpers shared by the step kernels
 // (iblb_kernels.cu) and the adjoint kernels (iblb_adjoint.cu): the D3Q19
 // velocity set, compile-time loops, the Peskin 4-point stencil and its
-// per-node broadcast, block reductions and the 3x3 Jacobi eigen-solver.
+// per-node broadcast, the scaled triangle normals of the surface-tension
+// force, block reductions and the 3x3 Jacobi eigen-solver.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -157,6 +158,25 @@ __device__ __forceinline__ void stencil_weights(const NodeStencil &S, int b, int
         wy = peskin_phi<T>(fy + T(1 - b));
         wz = peskin_phi<T>(fz + T(1 - c));
     }
+}
+
+// Scaled unit normal of every triangle, m_t = -sigma/2 N/|N| with
+// N = (x1 - x0) x (x2 - x0), so that the force of Eq. (pi_drop) on vertex k
+// of the triangle is m_t x (x_{k+2} - x_{k+1}).  FP64.
+__device__ __forceinline__ void tri_body(const MeshView &M, const int t)
+{
+    if (t >= M.nt) return;
+    const int v0 = M.tris[3 * t], v1 = M.tris[3 * t + 1], v2 = M.tris[3 * t + 2];
+    double e1[3], e2[3], N[3];
+    for (int a = 0; a < 3; ++a) {
+        e1[a] = M.r[3 * v1 + a] - M.r[3 * v0 + a];
+        e2[a] = M.r[3 * v2 + a] - M.r[3 * v0 + a];
+    }
+    cross3(e1, e2, N);
+    const double s = -0.5 * M.sigma / sqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
+    M.tn[3 * t] = s * N[0];
+    M.tn[3 * t + 1] = s * N[1];
+    M.tn[3 * t + 2] = s * N[2];
 }
 
 // ---------------------------------------------------------------------------

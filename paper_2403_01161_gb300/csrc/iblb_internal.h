@@ -1,5 +1,5 @@
 // Internal interface between the C-ABI host code (iblb_api.cpp) and the
-// CUDA kernels (iblb_kernels.cu).  Not installed; not part of the ABI.
+// CUDA kernels (iblb_kernels.cu, iblb_adjoint.cu).  Not installed; not part of the ABI.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -97,6 +97,17 @@ struct EnsembleView {
     int precision;
 };
 
+// Discrete adjoint of one step (device pointers in the adjoint workspace).
+struct AdjView {
+    void *lam_u;     // [3][nodes] adjoint of the lattice velocity seen by the interpolation (storage type); kept zero between steps
+    void *lam_F;     // [3][nodes] adjoint of the Eulerian force (storage type)
+    double *lam_r;   // [nv][3] adjoint of the node positions
+    double *lam_Fn;  // [nv][3] adjoint of the nodal forces
+    double *tri_w;   // [nt][7] per-triangle unit normal, 1/|N| and W of the force adjoint
+    double *acc;     // [1 + 9 n_frames] dD/dsigma, then dD/dA_k row-major
+    double *obs;     // [11] D and the adjoints of the volume sums of the readout
+};
+
 constexpr int kRingCap = 4096;
 constexpr int kObsBlocksMax = 304;
 
@@ -113,6 +124,12 @@ cudaError_t launch_regularize(const LbView &L, const MeshView &M, const RegParam
 cudaError_t launch_observables(const LbView &L, const MeshView &M, cudaStream_t s, int prio = 0);
 cudaError_t launch_patch_from_mesh(const LbView &L, const MeshView &M, int buf, cudaStream_t s);
 cudaError_t launch_ensemble_step(const EnsembleView &E, long long step, cudaStream_t s);
+
+// adjoint kernels (iblb_adjoint.cu); Mt.r holds the positions r_t of the step
+cudaError_t launch_adj_seed(const MeshView &M, const AdjView &J, cudaStream_t s);
+cudaError_t launch_adj_step(const LbView &L, const MeshView &Mt, const AdjView &J, const void *rec,
+                            const void *lam_next, void *lam_cur, int frame, cudaStream_t s);
+cudaError_t launch_adj_init(const LbView &L, const AdjView &J, const void *lam0, cudaStream_t s);
 
 // records a message for ibl_last_error() and returns `code` (iblb_api.cpp)
 int iblb_set_error(int code, const char *msg);

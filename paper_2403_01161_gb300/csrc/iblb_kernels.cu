@@ -499,25 +499,6 @@ __device__ void patch_from_rows(const LbView &L, const MeshView &M, int buf)
     if (lane == 0) write_patch(L, mn, mx, buf, 1);
 }
 
-// Scaled unit normal of every triangle, m_t = -sigma/2 N/|N| with
-// N = (x1 - x0) x (x2 - x0), so that the force of Eq. (pi_drop) on vertex k
-// of the triangle is m_t x (x_{k+2} - x_{k+1}).  FP64.
-__device__ __forceinline__ void tri_body(const MeshView &M, const int t)
-{
-    if (t >= M.nt) return;
-    const int v0 = M.tris[3 * t], v1 = M.tris[3 * t + 1], v2 = M.tris[3 * t + 2];
-    double e1[3], e2[3], N[3];
-    for (int a = 0; a < 3; ++a) {
-        e1[a] = M.r[3 * v1 + a] - M.r[3 * v0 + a];
-        e2[a] = M.r[3 * v2 + a] - M.r[3 * v0 + a];
-    }
-    cross3(e1, e2, N);
-    const double s = -0.5 * M.sigma / sqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
-    M.tn[3 * t] = s * N[0];
-    M.tn[3 * t + 1] = s * N[1];
-    M.tn[3 * t + 2] = s * N[2];
-}
-
 __global__ void __launch_bounds__(256) k_tri(MeshView M) { tri_body(M, blockIdx.x * blockDim.x + threadIdx.x); }
 
 // Nodal force F_i = -sigma dA/dx_i (Eq. (pi_drop)) gathered over the

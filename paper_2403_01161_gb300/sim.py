@@ -230,6 +230,25 @@ class Sim:
         L.check(self.lib.ibl_run_frames(self.h, self.mesh_h, _dp(fr), fr.shape[0], int(steps_per_frame), out))
         return [out[k].as_dict() for k in range(fr.shape[0])]
 
+    def adjoint(self, n_steps: int, K: int = 100) -> dict:
+        """Runs n_steps steps from step 0 and returns the Taylor deformation D
+        of the final droplet with its gradients by the library's discrete
+        adjoint (checkpoint every K steps, recomputation per segment):
+        {"D", "dD_dsigma", "dD_dA" (n_frames, 3, 3), "dD_dr0" (nv, 3)}.
+        Leaves the box at step n_steps."""
+        nbytes = ctypes.c_size_t()
+        L.check(self.lib.ibl_adjoint_workspace_size(self.h, int(n_steps), int(K), ctypes.byref(nbytes)))
+        ws = _workspace(nbytes.value, self.device)
+        D = np.zeros(1)
+        ds = np.zeros(1)
+        dA = np.zeros(9 * self.n_frames)
+        dr = np.zeros(3 * self.nv)
+        L.check(self.lib.ibl_adjoint(self.h, int(n_steps), int(K), ctypes.c_void_p(ws.data_ptr()), nbytes.value,
+                                     _dp(D), _dp(ds), _dp(dA), _dp(dr)))
+        del ws
+        return {"D": float(D[0]), "dD_dsigma": float(ds[0]), "dD_dA": dA.reshape(self.n_frames, 3, 3),
+                "dD_dr0": dr.reshape(self.nv, 3)}
+
     def patch(self):
         """(lo (3,), ext (3,)) of the droplet patch of the next step."""
         lo = np.zeros(3, dtype=np.int32)
