@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -69,7 +70,7 @@ bool lb_layout(const ibl_lb_params *p, int n_frames, Layout &L)
 }
 
 struct MeshLayout {
-    size_t r = 0, fn = 0, tn = 0, tris = 0, n2t_ptr = 0, n2t = 0, nb_ptr = 0, nb_idx = 0, s0 = 0, s1 = 0, s2 = 0,
+    size_t r = 0, fn = 0, tris = 0, n2t_ptr = 0, n2t = 0, nb_ptr = 0, nb_idx = 0, s0 = 0, s1 = 0, s2 = 0,
            part = 0, obs_part = 0, ring = 0, total = 0;
 };
 
@@ -84,7 +85,6 @@ bool mesh_layout(int nv, int nt, MeshLayout &L)
     };
     L.r = take(sizeof(double) * 3 * nv);
     L.fn = take(sizeof(double) * 3 * nv);
-    L.tn = take(sizeof(double) * 3 * nt);
     L.tris = take(sizeof(int) * 3 * nt);
     L.n2t_ptr = take(sizeof(int) * (nv + 1));
     L.n2t = take(sizeof(int) * 3 * nt);
@@ -466,7 +466,6 @@ int mesh_attach(ibl_lb *lb, int nv, const double *r, int nt, const int *tri_in, 
     m->v.sigma = sigma;
     m->v.r = reinterpret_cast<double *>(w + L.r);
     m->v.fn = reinterpret_cast<double *>(w + L.fn);
-    m->v.tn = reinterpret_cast<double *>(w + L.tn);
     m->v.tris = reinterpret_cast<const int *>(w + L.tris);
     m->v.n2t_ptr = reinterpret_cast<const int *>(w + L.n2t_ptr);
     m->v.n2t = reinterpret_cast<const int *>(w + L.n2t);
@@ -560,10 +559,12 @@ int ensure_streams(ibl_lb *lb)
     return IBL_OK;
 }
 
-// Captures one chunk starting at an aligned step (host_step % chunk == 0):
-// fork the helper capture stream off the main one, re-record the step
-// events inside the capture, run the steps, join back.
-int capture_chunk(ibl_lb *lb, int chunk)
+// Captures n steps from host_step into *out: fork the helper capture stream
+// off the main one, re-record the step events inside the capture, run the
+// steps (hook(k, main, helper) first enqueues whatever step k needs before
+// it), join back.  host_step is left unchanged.
+template <typename Hook>
+int capture_steps(ibl_lb *lb, int n, bool record, Hook &&hook, cudaGraphExec_t *out)
 {
     int st = ensure_streams(lb);
     if (st != IBL_OK) return st;
@@ -578,7 +579,10 @@ int capture_chunk(ibl_lb *lb, int chunk)
         if (e == cudaSuccess) e = cudaEventRecord(lb->cFar[k], cL);
     }
     if (e != cudaSuccess) st = cuda_fail(e, "capture fork");
-    for (int k = 0; k < chunk && st == IBL_OK; ++k) st = one_step(lb, false, cL, cH);
+    for (int k = 0; k < n && st == IBL_OK; ++k) {
+        st = hook(k, cL, cH);
+        if (st == IBL_OK) st = one_step(lb, record, cL, cH);
+    }
     if (st == IBL_OK) {
         e = join(cH, cL, lb->cJoin);
         if (e != cudaSuccess) st = cuda_fail(e, "capture join");
@@ -588,11 +592,19 @@ int capture_chunk(ibl_lb *lb, int chunk)
     const cudaError_t e2 = cudaStreamEndCapture(cL, &g);
     if (e2 != cudaSuccess && st == IBL_OK) st = cuda_fail(e2, "end capture");
     if (st == IBL_OK) {
-        const cudaError_t e3 = cudaGraphInstantiateWithFlags(&lb->gexec, g, cudaGraphInstantiateFlagUseNodePriority);
+        const cudaError_t e3 = cudaGraphInstantiateWithFlags(out, g, cudaGraphInstantiateFlagUseNodePriority);
         if (e3 != cudaSuccess) st = cuda_fail(e3, "graph instantiate");
     }
     if (g) cudaGraphDestroy(g);
     lb->host_step = saved;
+    return st;
+}
+
+// Captures one chunk of plain steps starting at an aligned step
+// (host_step % chunk == 0).
+int capture_chunk(ibl_lb *lb, int chunk)
+{
+    const int st = capture_steps(lb, chunk, false, [](int, cudaStream_t, cudaStream_t) { return IBL_OK; }, &lb->gexec);
     if (st == IBL_OK) lb->chunk = chunk;
     else drop_graph(lb);
     return st;
@@ -617,9 +629,8 @@ struct ibl_ensemble {
 namespace {
 
 struct EnsembleLayout {
-    size_t lv = 0, mv = 0, lat_member = 0, lat_start = 0, node_member = 0, node_start = 0, tri_member = 0,
-           tri_start = 0, total = 0;
-    int lat_blocks = 0, node_blocks = 0, tri_blocks = 0;
+    size_t lv = 0, mv = 0, lat_member = 0, lat_start = 0, node_member = 0, node_start = 0, total = 0;
+    int lat_blocks = 0, node_blocks = 0;
 };
 
 int ensemble_layout(int n, ibl_lb *const *members, EnsembleLayout &L, std::string &why)
@@ -628,7 +639,7 @@ int ensemble_layout(int n, ibl_lb *const *members, EnsembleLayout &L, std::strin
         why = "need at least one member";
         return IBL_EINVAL;
     }
-    long long lat = 0, node = 0, tri = 0;
+    long long lat = 0, node = 0;
     for (int k = 0; k < n; ++k) {
         const ibl_lb *lb = members[k];
         if (!lb || !lb->mesh) {
@@ -637,7 +648,6 @@ int ensemble_layout(int n, ibl_lb *const *members, EnsembleLayout &L, std::strin
         }
         lat += (lb->v.nodes + 255) / 256;
         node += ((long long)lb->mesh->v.nv * 16 + 127) / 128;
-        tri += (lb->mesh->v.nt + 255) / 256;
     }
     if (lat > 0x7fffffffLL) {
         why = "ensemble too large";
@@ -653,12 +663,9 @@ int ensemble_layout(int n, ibl_lb *const *members, EnsembleLayout &L, std::strin
     L.lat_start = take(sizeof(int) * (n + 1));
     L.node_member = take(sizeof(int) * node);
     L.node_start = take(sizeof(int) * (n + 1));
-    L.tri_member = take(sizeof(int) * tri);
-    L.tri_start = take(sizeof(int) * (n + 1));
     L.total = off;
     L.lat_blocks = (int)lat;
     L.node_blocks = (int)node;
-    L.tri_blocks = (int)tri;
     return IBL_OK;
 }
 
@@ -733,9 +740,11 @@ int ensemble_capture(ibl_ensemble *e, int chunk)
 // The force field is zero between steps and the velocity field is written
 // before it is read, so neither is saved.
 struct AdjLayout {
-    size_t lam[2] = {0, 0}, lam_u = 0, lam_F = 0, rec = 0, traj = 0, lam_r = 0, lam_Fn = 0, tri_w = 0, acc = 0,
-           obs = 0, ck = 0, total = 0;
+    size_t lam[2] = {0, 0}, lam_u = 0, lam_F = 0, rec = 0, traj = 0, lam_r = 0, a_part = 0, s_part = 0, acc = 0,
+           obs = 0, t0 = 0, ck = 0, total = 0;
+    int lat_blocks = 0, near_blocks = 0, tri_blocks = 0;
     size_t rec_step = 0, traj_step = 0;                  // bytes per recorded step
+    size_t traj_ctl = 0;                                 // control block copy inside a trajectory slot
     size_t ck_f = 0, ck_ctl = 0, ck_r = 0, ck_part = 0;  // offsets inside one checkpoint
     size_t f_bytes = 0, r_bytes = 0, part_bytes = 0, ck_step = 0;
     long long n_seg = 0;
@@ -758,7 +767,8 @@ bool adj_layout(const ibl_lb *lb, const ibl_mesh *m, long long T, int K, AdjLayo
     A.ck_part = A.ck_r + align256(A.r_bytes);
     A.ck_step = A.ck_part + align256(A.part_bytes);
     A.rec_step = align256(es * 7 * nodes);
-    A.traj_step = align256(A.r_bytes);
+    A.traj_ctl = align256(A.r_bytes);
+    A.traj_step = A.traj_ctl + align256(sizeof(Ctl));
     size_t off = 0;
     auto take = [&](size_t b) {
         const size_t o = off;
@@ -770,10 +780,12 @@ bool adj_layout(const ibl_lb *lb, const ibl_mesh *m, long long T, int K, AdjLayo
     A.lam_u = take(es * 3 * nodes);
     A.lam_F = take(es * 3 * nodes);
     A.lam_r = take(A.r_bytes);
-    A.lam_Fn = take(A.r_bytes);
-    A.tri_w = take(sizeof(double) * 7 * (size_t)nt);
+    iblb::adj_grid(lb->v, nt, &A.lat_blocks, &A.near_blocks, &A.tri_blocks);
+    A.a_part = take(sizeof(double) * 9 * (size_t)lb->v.n_frames * (size_t)(A.lat_blocks + A.near_blocks));
+    A.s_part = take(sizeof(double) * (size_t)A.tri_blocks);
     A.acc = take(sizeof(double) * (1 + 9 * (size_t)lb->v.n_frames));
     A.obs = take(sizeof(double) * 11);
+    A.t0 = take(sizeof(long long));
     A.rec = take(A.rec_step * (size_t)kmax);
     A.traj = take(A.traj_step * (size_t)kmax);
     A.ck = take(A.ck_step * (size_t)(A.n_seg + 1));
@@ -1301,7 +1313,7 @@ int ibl_ensemble_create(int n, ibl_lb *const *members, void *workspace, size_t b
     const ibl_lb *m0 = members[0];
     std::vector<LbView> lv;
     std::vector<MeshView> mv;
-    std::vector<int> lat_member, lat_start, node_member, node_start, tri_member, tri_start;
+    std::vector<int> lat_member, lat_start, node_member, node_start;
     for (int k = 0; k < n; ++k) {
         const ibl_lb *lb = members[k];
         if (lb->p.precision != m0->p.precision) return fail(IBL_EINVAL, "members differ in precision");
@@ -1315,12 +1327,9 @@ int ibl_ensemble_create(int n, ibl_lb *const *members, void *workspace, size_t b
         for (int b = 0; b < (lb->v.nodes + 255) / 256; ++b) lat_member.push_back(k);
         node_start.push_back((int)node_member.size());
         for (int b = 0; b < (lb->mesh->v.nv * 16 + 127) / 128; ++b) node_member.push_back(k);
-        tri_start.push_back((int)tri_member.size());
-        for (int b = 0; b < (lb->mesh->v.nt + 255) / 256; ++b) tri_member.push_back(k);
     }
     lat_start.push_back((int)lat_member.size());
     node_start.push_back((int)node_member.size());
-    tri_start.push_back((int)tri_member.size());
     char *w = static_cast<char *>(workspace);
     cudaStream_t s = m0->stream;
     cudaError_t e = cudaSuccess;
@@ -1331,8 +1340,6 @@ int ibl_ensemble_create(int n, ibl_lb *const *members, void *workspace, size_t b
     up(L.lat_start, lat_start.data(), sizeof(int) * lat_start.size());
     up(L.node_member, node_member.data(), sizeof(int) * node_member.size());
     up(L.node_start, node_start.data(), sizeof(int) * node_start.size());
-    up(L.tri_member, tri_member.data(), sizeof(int) * tri_member.size());
-    up(L.tri_start, tri_start.data(), sizeof(int) * tri_start.size());
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host tables are temporaries
     if (e != cudaSuccess) return cuda_fail(e, "ensemble upload");
     ibl_ensemble *en = new ibl_ensemble();
@@ -1345,11 +1352,8 @@ int ibl_ensemble_create(int n, ibl_lb *const *members, void *workspace, size_t b
     v.lat_start_d = reinterpret_cast<const int *>(w + L.lat_start);
     v.node_member = reinterpret_cast<const int *>(w + L.node_member);
     v.node_start_d = reinterpret_cast<const int *>(w + L.node_start);
-    v.tri_member = reinterpret_cast<const int *>(w + L.tri_member);
-    v.tri_start_d = reinterpret_cast<const int *>(w + L.tri_start);
     v.lat_start = lat_start;
     v.node_start = node_start;
-    v.tri_start = tri_start;
     v.precision = m0->p.precision;
     *out = en;
     return IBL_OK;
@@ -1472,72 +1476,182 @@ int ibl_adjoint(ibl_lb *lb, long long n_steps, int K, void *workspace, size_t by
     J.lam_u = ws + A.lam_u;
     J.lam_F = ws + A.lam_F;
     J.lam_r = reinterpret_cast<double *>(ws + A.lam_r);
-    J.lam_Fn = reinterpret_cast<double *>(ws + A.lam_Fn);
-    J.tri_w = reinterpret_cast<double *>(ws + A.tri_w);
+    J.a_part = reinterpret_cast<double *>(ws + A.a_part);
+    J.s_part = reinterpret_cast<double *>(ws + A.s_part);
+    J.lat_blocks = A.lat_blocks;
+    J.acc_blocks = A.lat_blocks + A.near_blocks;
+    J.tri_blocks = A.tri_blocks;
     J.acc = reinterpret_cast<double *>(ws + A.acc);
     J.obs = reinterpret_cast<double *>(ws + A.obs);
+    J.t0 = reinterpret_cast<long long *>(ws + A.t0);
     void *lam[2] = {ws + A.lam[0], ws + A.lam[1]};
     cudaError_t e = cudaMemsetAsync(lam[0], 0, es * 19 * nodes, s);  // D does not depend on the final populations
     if (e == cudaSuccess) e = cudaMemsetAsync(J.lam_u, 0, es * 3 * nodes, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(J.acc, 0, sizeof(double) * (1 + 9 * (size_t)nf), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(J.a_part, 0, sizeof(double) * 9 * (size_t)nf * J.acc_blocks, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(J.s_part, 0, sizeof(double) * (size_t)A.tri_blocks, s);
     // the initial state is the equilibrium of the current frame 0
     if (e == cudaSuccess) e = iblb::launch_init(lb->v, s);
     if (e != cudaSuccess) return cuda_fail(e, "adjoint set-up");
 
-    // forward pass with a checkpoint at the start of every segment and one
-    // of the final state
-    for (long long sg = 0; sg < A.n_seg; ++sg) {
-        e = adj_save(lb, A, ws, sg, s);
-        if (e != cudaSuccess) return cuda_fail(e, "checkpoint");
-        st = ibl_step(lb, std::min<long long>(K, n_steps - sg * K));
-        if (st != IBL_OK) return st;
-    }
-    e = adj_save(lb, A, ws, A.n_seg, s);
-    // seed: D of the final mesh and dD/dr_T
-    if (e == cudaSuccess) e = iblb::launch_adj_seed(m->v, J, s);
-    if (e != cudaSuccess) return cuda_fail(e, "adjoint seed");
-
-    // reverse sweep: recompute each segment eagerly on the bound stream,
-    // keeping r_t and the moments of every step, then step back through it
     const int readout = m->readout_every;
-    m->readout_every = 0;  // the recomputation writes no shape records
     void *rec_saved = lb->v.rec;
-    int cur = 0;  // lam[cur] holds the adjoint of the populations of step t + 1
-    st = IBL_OK;
-    for (long long sg = A.n_seg - 1; sg >= 0 && st == IBL_OK; --sg) {
-        const long long t0 = sg * K;
-        const int len = (int)std::min<long long>(K, n_steps - t0);
-        e = adj_restore(lb, A, ws, sg, s);
-        if (e != cudaSuccess) {
-            st = cuda_fail(e, "checkpoint restore");
-            break;
-        }
+    std::vector<cudaGraphExec_t> graphs;  // destroyed on return (they hold workspace addresses)
+    // Recording run of segment [t0, t0 + len): before each step, the node
+    // positions r_t go to the trajectory slot (on the stream of the droplet
+    // kernels, which wrote them) and the lattice records its moments into
+    // the step's slot.  Full-length segments replay a captured graph (one
+    // per t0 mod 6 -- parity and patch buffer -- and shape-record setting);
+    // a shorter one runs eagerly.  Shape records are taken only in the
+    // forward pass, never when a segment is recorded again.
+    std::map<int, cudaGraphExec_t> rec_graph;
+    const size_t patch_off = offsetof(Ctl, patch_lo);
+    auto record_hook = [&](int k, cudaStream_t, cudaStream_t sH) -> int {
+        char *slot = ws + A.traj + A.traj_step * k;
+        cudaError_t ee = cudaMemcpyAsync(slot, m->v.r, A.r_bytes, cudaMemcpyDeviceToDevice, sH);
+        // the patch of the step (written by the previous force kernel on this stream)
+        if (ee == cudaSuccess)
+            ee = cudaMemcpyAsync(slot + A.traj_ctl + patch_off, reinterpret_cast<char *>(lb->v.ctl) + patch_off,
+                                 sizeof(Ctl) - patch_off, cudaMemcpyDeviceToDevice, sH);
+        if (ee != cudaSuccess) return cuda_fail(ee, "trajectory copy");
+        lb->v.rec = ws + A.rec + A.rec_step * k;
+        return IBL_OK;
+    };
+    auto record_segment = [&](long long t0, int len, bool shape_records) -> int {
         lb->host_step = t0;
-        for (int k = 0; k < len && st == IBL_OK; ++k) {
-            e = cudaMemcpyAsync(ws + A.traj + A.traj_step * k, m->v.r, A.r_bytes, cudaMemcpyDeviceToDevice, s);
-            if (e != cudaSuccess) {
-                st = cuda_fail(e, "trajectory copy");
-                break;
+        m->readout_every = shape_records ? readout : 0;
+        int r = IBL_OK;
+        if (len == K) {
+            const int key = (int)(t0 % 6) + (shape_records ? 6 : 0);
+            auto it = rec_graph.find(key);
+            if (it == rec_graph.end()) {
+                cudaGraphExec_t g = nullptr;
+                r = capture_steps(lb, len, true, record_hook, &g);
+                lb->v.rec = rec_saved;
+                m->readout_every = readout;
+                if (r != IBL_OK) return r;
+                graphs.push_back(g);
+                it = rec_graph.emplace(key, g).first;
             }
-            lb->v.rec = ws + A.rec + A.rec_step * k;
-            st = one_step(lb, true, s, s);
+            m->readout_every = readout;
+            const cudaError_t ee = cudaGraphLaunch(it->second, s);
+            if (ee != cudaSuccess) return cuda_fail(ee, "recording graph launch");
+            lb->host_step = t0 + len;
+            return IBL_OK;
+        }
+        for (int k = 0; k < len && r == IBL_OK; ++k) {
+            r = record_hook(k, s, s);
+            if (r == IBL_OK) r = one_step(lb, true, s, s);
         }
         lb->v.rec = rec_saved;
-        for (int k = len - 1; k >= 0 && st == IBL_OK; --k) {
-            MeshView Mt = m->v;
-            Mt.r = reinterpret_cast<double *>(ws + A.traj + A.traj_step * k);
-            const long long t = t0 + k;
-            const int frame = (int)std::min<long long>(t / lb->v.n_hold, nf - 1);
-            e = iblb::launch_adj_step(lb->v, Mt, J, ws + A.rec + A.rec_step * k, lam[cur], lam[cur ^ 1], frame, s);
-            if (e != cudaSuccess) st = cuda_fail(e, "adjoint step launch");
-            cur ^= 1;
-        }
+        m->readout_every = readout;
+        return r;
+    };
+    // Reverse sweep of a recorded segment on two streams, as the forward
+    // step: the helper stream (high priority) runs the interpolation
+    // adjoint, the patch nodes and the surface adjoint, the bound stream the
+    // nodes outside the patch; step k's patch update waits for step k+1's
+    // outside update and vice versa.  Full-length segments replay a captured
+    // graph (one per parity of the adjoint buffer pair).
+    int cur = 0;  // lam[cur] holds the adjoint of the populations of step t + 1
+    cudaGraphExec_t rev_graph[2] = {nullptr, nullptr};
+    cudaEvent_t ev[8] = {};
+    for (int k = 0; k < 8 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        for (cudaEvent_t x : ev)
+            if (x) cudaEventDestroy(x);
+        return cuda_fail(e, "adjoint events");
     }
-    m->readout_every = readout;
+    auto enqueue_reverse = [&](int len, int c0, cudaStream_t sL, cudaStream_t sH, bool capture) -> cudaError_t {
+        cudaEvent_t *eN = capture ? ev : ev + 4, *eF = eN + 2;
+        cudaError_t ee = join(sL, sH, capture ? lb->cFork : lb->evFork);
+        int c = c0;
+        for (int k = len - 1; k >= 0 && ee == cudaSuccess; --k) {
+            const int p = k & 1;
+            char *slot = ws + A.traj + A.traj_step * k;
+            MeshView Mt = m->v;
+            Mt.r = reinterpret_cast<double *>(slot);
+            const Ctl *pc = reinterpret_cast<const Ctl *>(slot + A.traj_ctl);
+            const void *rec = ws + A.rec + A.rec_step * k;
+            ee = iblb::launch_adj_interp(lb->v, Mt, J, rec, sH, lb->hi_prio);
+            if (ee == cudaSuccess && k < len - 1) ee = cudaStreamWaitEvent(sH, eF[p ^ 1], 0);
+            if (ee == cudaSuccess) ee = iblb::launch_adj_near(lb->v, J, rec, lam[c], lam[c ^ 1], pc, k, sH, lb->hi_prio);
+            if (ee == cudaSuccess) ee = cudaEventRecord(eN[p], sH);
+            if (ee == cudaSuccess) ee = iblb::launch_adj_surface(lb->v, Mt, J, sH, lb->hi_prio);
+            if (ee == cudaSuccess && k < len - 1) ee = cudaStreamWaitEvent(sL, eN[p ^ 1], 0);
+            if (ee == cudaSuccess) ee = iblb::launch_adj_far(lb->v, J, rec, lam[c], lam[c ^ 1], pc, k, sL);
+            if (ee == cudaSuccess) ee = cudaEventRecord(eF[p], sL);
+            c ^= 1;
+        }
+        if (ee == cudaSuccess) ee = join(sH, sL, capture ? lb->cJoin : lb->evJoin);
+        return ee;
+    };
+    auto reverse_segment = [&](long long t0, int len) -> int {
+        cudaError_t ee = iblb::launch_adj_set_t0(J, t0, s);
+        if (ee != cudaSuccess) return cuda_fail(ee, "adjoint segment start");
+        if (len == K) {
+            if (!rev_graph[cur]) {
+                cudaStream_t cL = lb->cap_stream, cH = lb->cap_helper;
+                ee = cudaStreamBeginCapture(cL, cudaStreamCaptureModeThreadLocal);
+                if (ee != cudaSuccess) return cuda_fail(ee, "begin capture");
+                const cudaError_t e1 = enqueue_reverse(len, cur, cL, cH, true);
+                cudaGraph_t g = nullptr;
+                const cudaError_t e2 = cudaStreamEndCapture(cL, &g);
+                ee = e1 != cudaSuccess ? e1 : e2;
+                if (ee == cudaSuccess)
+                    ee = cudaGraphInstantiateWithFlags(&rev_graph[cur], g, cudaGraphInstantiateFlagUseNodePriority);
+                if (g) cudaGraphDestroy(g);
+                if (ee != cudaSuccess) return cuda_fail(ee, "adjoint graph capture");
+                graphs.push_back(rev_graph[cur]);
+            }
+            ee = cudaGraphLaunch(rev_graph[cur], s);
+        } else {
+            ee = enqueue_reverse(len, cur, s, lb->helper, false);
+        }
+        if (ee != cudaSuccess) return cuda_fail(ee, "adjoint step launch");
+        cur ^= (len & 1);
+        return IBL_OK;
+    };
+
+    // forward pass: checkpoints at the segment starts; the last segment is
+    // recorded on the way, so it needs no recomputation
+    const long long last = A.n_seg - 1;
+    for (long long sg = 0; sg < A.n_seg && st == IBL_OK; ++sg) {
+        e = adj_save(lb, A, ws, sg, s);
+        if (e != cudaSuccess) {
+            st = cuda_fail(e, "checkpoint");
+            break;
+        }
+        const int len = (int)std::min<long long>(K, n_steps - sg * K);
+        if (sg < last) st = ibl_step(lb, len);
+        else st = record_segment(sg * K, len, true);
+    }
+    if (st == IBL_OK) {
+        e = adj_save(lb, A, ws, A.n_seg, s);
+        // seed: D of the final mesh and dD/dr_T
+        if (e == cudaSuccess) e = iblb::launch_adj_seed(m->v, J, s);
+        if (e != cudaSuccess) st = cuda_fail(e, "adjoint seed");
+    }
+    // reverse sweep: the last segment from its recording, the others after
+    // restoring their checkpoint and recording them again
+    for (long long sg = last; sg >= 0 && st == IBL_OK; --sg) {
+        const long long t0 = sg * K;
+        const int len = (int)std::min<long long>(K, n_steps - t0);
+        if (sg < last) {
+            e = adj_restore(lb, A, ws, sg, s);
+            if (e != cudaSuccess) {
+                st = cuda_fail(e, "checkpoint restore");
+                break;
+            }
+            st = record_segment(t0, len, false);
+            if (st != IBL_OK) break;
+        }
+        st = reverse_segment(t0, len);
+    }
     lb->v.rec = rec_saved;
     // the initial populations depend on frame 0
     if (st == IBL_OK) {
         e = iblb::launch_adj_init(lb->v, J, lam[cur], s);
+        if (e == cudaSuccess) e = iblb::launch_adj_reduce(J, nf, s);
         if (e != cudaSuccess) st = cuda_fail(e, "adjoint initial state");
     }
     // leave the lattice and droplet at the final step, as ibl_step would
@@ -1546,14 +1660,19 @@ int ibl_adjoint(ibl_lb *lb, long long n_steps, int K, void *workspace, size_t by
         if (e != cudaSuccess) st = cuda_fail(e, "final state restore");
     }
     lb->host_step = n_steps;
-    if (st != IBL_OK) return st;
     std::vector<double> acc(1 + 9 * (size_t)nf);
     double obs0 = 0.0;
-    e = cudaMemcpyAsync(acc.data(), J.acc, sizeof(double) * acc.size(), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&obs0, J.obs, sizeof(double), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess && dD_dr0) e = cudaMemcpyAsync(dD_dr0, J.lam_r, A.r_bytes, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return cuda_fail(e, "adjoint readout");
+    if (st == IBL_OK) {
+        e = cudaMemcpyAsync(acc.data(), J.acc, sizeof(double) * acc.size(), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&obs0, J.obs, sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && dD_dr0) e = cudaMemcpyAsync(dD_dr0, J.lam_r, A.r_bytes, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) st = cuda_fail(e, "adjoint readout");
+    }
+    const cudaError_t es2 = cudaStreamSynchronize(s);
+    for (cudaGraphExec_t g : graphs) cudaGraphExecDestroy(g);
+    for (cudaEvent_t x : ev) cudaEventDestroy(x);
+    if (st != IBL_OK) return st;
+    if (es2 != cudaSuccess) return cuda_fail(es2, "adjoint synchronize");
     st = lb_status_from_device(lb);
     if (st != IBL_OK) return st;
     if (D) *D = obs0;

@@ -1,8 +1,8 @@
 // iblb_device.cuh -- device helpers shared by the step kernels
 // (iblb_kernels.cu) and the adjoint kernels (iblb_adjoint.cu): the D3Q19
 // velocity set, compile-time loops, the Peskin 4-point stencil and its
-// per-node broadcast, the scaled triangle normals of the surface-tension
-// force, block reductions and the 3x3 Jacobi eigen-solver.
+// per-node broadcast, the surface-tension force of a triangle, block
+// reductions and the 3x3 Jacobi eigen-solver.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -69,7 +69,8 @@ __device__ __forceinline__ T peskin_phi(T x)
     return T(0);
 }
 
-__device__ __forceinline__ void cross3(const double a[3], const double b[3], double o[3])
+template <typename V>
+__device__ __forceinline__ void cross3(const V a[3], const V b[3], V o[3])
 {
     o[0] = a[1] * b[2] - a[2] * b[1];
     o[1] = a[2] * b[0] - a[0] * b[2];
@@ -160,23 +161,45 @@ __device__ __forceinline__ void stencil_weights(const NodeStencil &S, int b, int
     }
 }
 
-// Scaled unit normal of every triangle, m_t = -sigma/2 N/|N| with
-// N = (x1 - x0) x (x2 - x0), so that the force of Eq. (pi_drop) on vertex k
-// of the triangle is m_t x (x_{k+2} - x_{k+1}).  FP64.
-__device__ __forceinline__ void tri_body(const MeshView &M, const int t)
+// Whether lattice node (x, y, z) lies in the droplet patch stored in buffer
+// `buf` of control block c (periodic axes wrap).
+__device__ __forceinline__ bool node_in_patch(const LbView &L, const Ctl *c, int buf, int x, int y, int z)
 {
-    if (t >= M.nt) return;
-    const int v0 = M.tris[3 * t], v1 = M.tris[3 * t + 1], v2 = M.tris[3 * t + 2];
-    double e1[3], e2[3], N[3];
+    int dx = x - c->patch_lo[buf][0], dy = y - c->patch_lo[buf][1], dz = z - c->patch_lo[buf][2];
+    if (L.bc[0] == IBL_BC_PERIODIC && dx < 0) dx += L.n[0];
+    if (L.bc[1] == IBL_BC_PERIODIC && dy < 0) dy += L.n[1];
+    if (L.bc[2] == IBL_BC_PERIODIC && dz < 0) dz += L.n[2];
+    // an empty patch has extent -1: no node is inside
+    return c->patch_ext[buf][0] >= 0 && (unsigned)dx <= (unsigned)c->patch_ext[buf][0] &&
+           (unsigned)dy <= (unsigned)c->patch_ext[buf][1] && (unsigned)dz <= (unsigned)c->patch_ext[buf][2];
+}
+
+// Surface-tension force of triangle t on its vertex in position `slot`
+// (Eq. (pi_drop), F_i = -sigma dA/dx_i summed over the triangles around i):
+// m_t x (x_{slot+2} - x_{slot+1}) with the scaled unit normal
+// m_t = -sigma/2 N/|N|, N = (x1 - x0) x (x2 - x0).  Positions are FP64; the
+// edge vectors are formed in FP64 and the rest runs in G (FP64 for FP64
+// storage; FP32 for FP32 storage, whose spread rounds the force to FP32
+// anyway -- the FP64 pipe of this GPU is 1/64 of the FP32 one).
+template <typename G>
+__device__ __forceinline__ void tri_force(const MeshView &M, const int t, const int slot, G g[3])
+{
+    double x[3][3];
+    for (int k = 0; k < 3; ++k) {
+        const int v = M.tris[3 * t + k];
+        for (int a = 0; a < 3; ++a) x[k][a] = M.r[3 * v + a];
+    }
+    G e1[3], e2[3], N[3];
     for (int a = 0; a < 3; ++a) {
-        e1[a] = M.r[3 * v1 + a] - M.r[3 * v0 + a];
-        e2[a] = M.r[3 * v2 + a] - M.r[3 * v0 + a];
+        e1[a] = G(x[1][a] - x[0][a]);
+        e2[a] = G(x[2][a] - x[0][a]);
     }
     cross3(e1, e2, N);
-    const double s = -0.5 * M.sigma / sqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
-    M.tn[3 * t] = s * N[0];
-    M.tn[3 * t + 1] = s * N[1];
-    M.tn[3 * t + 2] = s * N[2];
+    const G s = G(-0.5) * G(M.sigma) / sqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
+    const G m[3] = {s * N[0], s * N[1], s * N[2]};
+    const int kp = slot == 2 ? 0 : slot + 1, km = slot == 0 ? 2 : slot - 1;
+    const G dd[3] = {G(x[km][0] - x[kp][0]), G(x[km][1] - x[kp][1]), G(x[km][2] - x[kp][2])};
+    cross3(m, dd, g);
 }
 
 // ---------------------------------------------------------------------------
@@ -257,4 +280,24 @@ __device__ void jacobi3(double a[3][3], double lam[3], double v[3][3])
 
 
 }  // namespace
+
+// Launch with an explicit scheduling priority (0 = the stream's own).  The
+// attribute is recorded into the kernel node under stream capture, which the
+// stream priority alone is not.
+template <typename... KArgs, typename... Args>
+static inline cudaError_t launch_p(void (*k)(KArgs...), dim3 g, dim3 b, cudaStream_t s, int prio, Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = g;
+    cfg.blockDim = b;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributePriority;
+    attr[0].val.priority = prio;
+    cfg.attrs = attr;
+    cfg.numAttrs = prio != 0 ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
+}
+
 }  // namespace iblb

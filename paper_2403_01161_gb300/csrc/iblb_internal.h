@@ -54,7 +54,6 @@ struct MeshView {
     double sigma;
     double *r;          // [nv][3]
     double *fn;         // [nv][3] nodal forces of the last step
-    double *tn;         // [nt][3] scaled triangle normals of the last step
     const int *tris;    // [nt][3]
     const int *n2t_ptr; // [nv+1]
     const int *n2t;     // [3 nt] entries 3*t + slot
@@ -89,11 +88,9 @@ struct EnsembleView {
     std::vector<MeshView> mv;
     const int *lat_member;       // [lat blocks] member of each lattice block (device)
     const int *node_member;      // [node blocks]
-    const int *tri_member;       // [tri blocks]
     const int *lat_start_d;      // [n+1] first block of each member (device)
     const int *node_start_d;
-    const int *tri_start_d;
-    std::vector<int> lat_start, node_start, tri_start;  // host copies
+    std::vector<int> lat_start, node_start;  // host copies
     int precision;
 };
 
@@ -102,9 +99,13 @@ struct AdjView {
     void *lam_u;     // [3][nodes] adjoint of the lattice velocity seen by the interpolation (storage type); kept zero between steps
     void *lam_F;     // [3][nodes] adjoint of the Eulerian force (storage type)
     double *lam_r;   // [nv][3] adjoint of the node positions
-    double *lam_Fn;  // [nv][3] adjoint of the nodal forces
-    double *tri_w;   // [nt][7] per-triangle unit normal, 1/|N| and W of the force adjoint
-    double *acc;     // [1 + 9 n_frames] dD/dsigma, then dD/dA_k row-major
+    double *a_part;  // [n_frames][acc_blocks][9] per-block partial sums of dD/dA_k (block-private)
+    double *s_part;  // [tri_blocks] per-block partial sums of dD/dsigma (block-private)
+    int lat_blocks;  // blocks of the lattice adjoint grid (nodes outside the patch)
+    int acc_blocks;  // partial-sum slots per frame: lat_blocks, then the patch kernel's blocks
+    int tri_blocks;  // blocks of the triangle kernel
+    long long *t0;   // first step of the segment being swept (device, set before each segment)
+    double *acc;     // [1 + 9 n_frames] dD/dsigma, then dD/dA_k row-major (written by the final reduction)
     double *obs;     // [11] D and the adjoints of the volume sums of the readout
 };
 
@@ -125,11 +126,21 @@ cudaError_t launch_observables(const LbView &L, const MeshView &M, cudaStream_t 
 cudaError_t launch_patch_from_mesh(const LbView &L, const MeshView &M, int buf, cudaStream_t s);
 cudaError_t launch_ensemble_step(const EnsembleView &E, long long step, cudaStream_t s);
 
-// adjoint kernels (iblb_adjoint.cu); Mt.r holds the positions r_t of the step
+// adjoint kernels (iblb_adjoint.cu); Mt.r holds the positions r_t of the
+// step, pc the control block recorded before it (its patch)
+constexpr int kAdjNearBlocks = 304;
 cudaError_t launch_adj_seed(const MeshView &M, const AdjView &J, cudaStream_t s);
-cudaError_t launch_adj_step(const LbView &L, const MeshView &Mt, const AdjView &J, const void *rec,
-                            const void *lam_next, void *lam_cur, int frame, cudaStream_t s);
+cudaError_t launch_adj_interp(const LbView &L, const MeshView &Mt, const AdjView &J, const void *rec, cudaStream_t s,
+                              int prio);
+cudaError_t launch_adj_near(const LbView &L, const AdjView &J, const void *rec, const void *lam_next, void *lam_cur,
+                            const Ctl *pc, int k_in_segment, cudaStream_t s, int prio);
+cudaError_t launch_adj_far(const LbView &L, const AdjView &J, const void *rec, const void *lam_next, void *lam_cur,
+                           const Ctl *pc, int k_in_segment, cudaStream_t s);
+cudaError_t launch_adj_surface(const LbView &L, const MeshView &Mt, const AdjView &J, cudaStream_t s, int prio);
+cudaError_t launch_adj_set_t0(const AdjView &J, long long t0, cudaStream_t s);
 cudaError_t launch_adj_init(const LbView &L, const AdjView &J, const void *lam0, cudaStream_t s);
+cudaError_t launch_adj_reduce(const AdjView &J, int n_frames, cudaStream_t s);
+void adj_grid(const LbView &L, int nt, int *lat_blocks, int *near_blocks, int *tri_blocks);
 
 // records a message for ibl_last_error() and returns `code` (iblb_api.cpp)
 int iblb_set_error(int code, const char *msg);

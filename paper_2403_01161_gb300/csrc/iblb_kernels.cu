@@ -172,17 +172,6 @@ __device__ __forceinline__ void bc_dispatch(T (&f)[19], const T (&uw)[3], int ru
 // and written by one node only within a step.
 enum { LAT_FULL = 0, LAT_FAR = 1, LAT_NEAR = 2 };
 
-__device__ __forceinline__ bool node_in_patch(const LbView &L, const Ctl *c, int buf, int x, int y, int z)
-{
-    int dx = x - c->patch_lo[buf][0], dy = y - c->patch_lo[buf][1], dz = z - c->patch_lo[buf][2];
-    if (L.bc[0] == IBL_BC_PERIODIC && dx < 0) dx += L.n[0];
-    if (L.bc[1] == IBL_BC_PERIODIC && dy < 0) dy += L.n[1];
-    if (L.bc[2] == IBL_BC_PERIODIC && dz < 0) dz += L.n[2];
-    // an empty patch has extent -1: no node is inside
-    return c->patch_ext[buf][0] >= 0 && (unsigned)dx <= (unsigned)c->patch_ext[buf][0] &&
-           (unsigned)dy <= (unsigned)c->patch_ext[buf][1] && (unsigned)dz <= (unsigned)c->patch_ext[buf][2];
-}
-
 template <typename T, bool ODD, bool REC, int MODE>
 __device__ __forceinline__ bool lattice_node(const LbView &L, const int x, const int y, const int z, const int pbuf)
 {
@@ -499,8 +488,6 @@ __device__ void patch_from_rows(const LbView &L, const MeshView &M, int buf)
     if (lane == 0) write_patch(L, mn, mx, buf, 1);
 }
 
-__global__ void __launch_bounds__(256) k_tri(MeshView M) { tri_body(M, blockIdx.x * blockDim.x + threadIdx.x); }
-
 // Nodal force F_i = -sigma dA/dx_i (Eq. (pi_drop)) gathered over the
 // triangles around node i, then spread with the 4-point delta
 // (Eq. (ibm_force_d)(a)) by atomic adds into the Eulerian force.  Sixteen
@@ -514,25 +501,20 @@ __device__ __forceinline__ void spread_body(const LbView &L, const MeshView &M, 
     const int lane = threadIdx.x % kLanesPerNode;
     const bool valid = gid < M.nv;
     const int i = valid ? gid : M.nv - 1;
-    double F[3] = {0.0, 0.0, 0.0};
+    T F[3] = {T(0), T(0), T(0)};
     for (int k = M.n2t_ptr[i] + lane; k < M.n2t_ptr[i + 1]; k += kLanesPerNode) {
         const int e = M.n2t[k];
-        const int t = e / 3, slot = e - 3 * t;
-        const int vp = M.tris[3 * t + (slot == 2 ? 0 : slot + 1)];
-        const int vm = M.tris[3 * t + (slot == 0 ? 2 : slot - 1)];
-        const double d[3] = {M.r[3 * vm] - M.r[3 * vp], M.r[3 * vm + 1] - M.r[3 * vp + 1],
-                             M.r[3 * vm + 2] - M.r[3 * vp + 2]};
-        const double m[3] = {M.tn[3 * t], M.tn[3 * t + 1], M.tn[3 * t + 2]};
-        double g[3];
-        cross3(m, d, g);
+        const int t = e / 3;
+        T g[3];
+        tri_force<T>(M, t, e - 3 * t, g);
         for (int a = 0; a < 3; ++a) F[a] += g[a];
     }
     for (int o = kLanesPerNode / 2; o > 0; o >>= 1)
         for (int a = 0; a < 3; ++a) F[a] += __shfl_xor_sync(0xffffffffu, F[a], o, kLanesPerNode);
     if (valid && lane == 0) {
-        M.fn[3 * i] = F[0];
-        M.fn[3 * i + 1] = F[1];
-        M.fn[3 * i + 2] = F[2];
+        M.fn[3 * i] = (double)F[0];
+        M.fn[3 * i + 1] = (double)F[1];
+        M.fn[3 * i + 2] = (double)F[2];
     }
     const NodeStencil S = node_stencil(L, M.r + 3 * i, lane);
     if (!valid) return;
@@ -548,7 +530,7 @@ __device__ __forceinline__ void spread_body(const LbView &L, const MeshView &M, 
     const int nx = L.n[0], nxy = L.n[0] * L.n[1], nodes = L.nodes;
     const int row = wrap_index(S.base[1] + b, L.n[1], pery) * nx + wrap_index(S.base[2] + c, L.n[2], perz) * nxy;
     T *force = static_cast<T *>(L.force);
-    const T Fx = T(F[0]), Fy = T(F[1]), Fz = T(F[2]);
+    const T Fx = F[0], Fy = F[1], Fz = F[2];
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
         const T dl = w[a] * wy * wz;
@@ -655,14 +637,7 @@ __global__ void k_advance_batched(const __grid_constant__ LbGroup LG, const int 
 
 // Ensemble versions: block b works for member blk_member[b0 + b] as its
 // local block b0 + b - blk_start[member]; node-group kernels use ceil(nv/8)
-// blocks per member, the triangle kernel ceil(nt/256).
-__global__ void __launch_bounds__(256)
-    k_tri_batched(const __grid_constant__ MeshGroup MG, const int m0, const int b0, const int *__restrict__ blk_member,
-                  const int *__restrict__ blk_start)
-{
-    const int mi = blk_member[b0 + blockIdx.x];
-    tri_body(MG.v[mi - m0], (b0 + (int)blockIdx.x - blk_start[mi]) * blockDim.x + threadIdx.x);
-}
+// blocks per member.
 
 template <typename T>
 __global__ void __launch_bounds__(128)
@@ -897,25 +872,6 @@ __global__ void __launch_bounds__(256) k_observables(LbView L, MeshView M)
 // launchers
 static inline unsigned blocks_for(long long n, int b) { return (unsigned)((n + b - 1) / b); }
 
-// Launch with an explicit scheduling priority (0 = the stream's own).  The
-// attribute is recorded into the kernel node under stream capture, which the
-// stream priority alone is not.
-template <typename... KArgs, typename... Args>
-static cudaError_t launch_p(void (*k)(KArgs...), dim3 g, dim3 b, cudaStream_t s, int prio, Args &&...args)
-{
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = g;
-    cfg.blockDim = b;
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributePriority;
-    attr[0].val.priority = prio;
-    cfg.attrs = attr;
-    cfg.numAttrs = prio != 0 ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
-}
-
 cudaError_t launch_init(const LbView &L, cudaStream_t s)
 {
     const unsigned g = blocks_for(L.nodes, 256);
@@ -1005,8 +961,6 @@ cudaError_t launch_advance(const LbView &L, cudaStream_t s)
 
 cudaError_t launch_spread(const LbView &L, const MeshView &M, int next_buf, cudaStream_t s, int prio)
 {
-    cudaError_t e = launch_p(k_tri, dim3(blocks_for(M.nt, 256)), dim3(256), s, prio, M);
-    if (e != cudaSuccess) return e;
     const dim3 g(blocks_for((long long)M.nv * kLanesPerNode, kIbThreads)), b(kIbThreads);
     if (L.precision == IBL_FP64) return launch_p(k_spread<double>, g, b, s, prio, L, M, next_buf);
     return launch_p(k_spread<float>, g, b, s, prio, L, M, next_buf);
@@ -1052,11 +1006,9 @@ cudaError_t launch_ensemble_step(const EnsembleView &E, long long step, cudaStre
             lg.v[k - m0] = E.lv[k];
             mg.v[k - m0] = E.mv[k];
         }
-        const int tb0 = E.tri_start[m0], tb = E.tri_start[m1] - tb0;
         const int nb0 = E.node_start[m0], nb = E.node_start[m1] - nb0;
         const int lb0 = E.lat_start[m0], lbn = E.lat_start[m1] - lb0;
         const int nxt = (int)((step + 1) % 3);  // patch buffer of the next step
-        k_tri_batched<<<tb, 256, 0, s>>>(mg, m0, tb0, E.tri_member, E.tri_start_d);
         if (E.precision == IBL_FP64) {
             k_spread_batched<double>
                 <<<nb, kIbThreads, 0, s>>>(lg, mg, m0, nb0, E.node_member, E.node_start_d, nxt);

@@ -234,3 +234,22 @@ def test_autograd_function(adj64):
     with torch.no_grad():
         D2 = deformation(sigma.detach(), frames.detach(), spec)
     assert abs(D2.item() - adj64["D"]) < 1e-13
+
+
+def test_forward_shape_records_are_kept():
+    """With shape records on, the adjoint's forward pass leaves exactly the
+    records a plain run takes (the recomputations take none)."""
+    a = _sim()
+    a.set_readout(5)
+    g = a.adjoint(STEPS, K)
+    ra = a.series()
+    b = _sim()
+    b.set_readout(5)
+    b.step(STEPS)
+    rb = b.series()
+    assert [r["step"] for r in ra] == [r["step"] for r in rb] == list(range(5, STEPS + 1, 5))
+    for x, y in zip(ra, rb):
+        assert abs(x["D"] - y["D"]) < 1e-12
+    assert abs(ra[-1]["D"] - g["D"]) < 1e-12
+    a.close()
+    b.close()
