@@ -246,6 +246,73 @@ def measure_ensemble(dev, steps, warmup, rank, world):
                       "the single-droplet kernels (graph replay each)"}
 
 
+def measure_adjoint(dev, rank, world, seeds=range(500, 516), steps=2000, K=100):
+    """Adjoint sweep of the 64^3 droplet (R 8, level 3, own OU gradients per
+    seed) against its forward run: wall time of one ibl_adjoint call (its
+    forward pass with checkpoints every K steps, the recomputations and the
+    reverse steps) over the wall time of the same trajectory stepped plainly
+    (graph replay).  Also the same with every step's moments kept resident
+    (K = steps: no recomputation).  Seeds are shared out over the ranks."""
+    import numpy as np
+    import torch
+
+    from paper_2403_01161_gb300 import config
+    from paper_2403_01161_gb300.sim import Sim
+
+    def make(w):
+        s = Sim(w.n, w.tau, w.frames, w.n_hold, precision=w.precision, device=dev)
+        s.add_icosphere(w.level, w.R, w.sigma)
+        torch.cuda.synchronize(dev)
+        return s
+
+    def timed(fn):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize(dev)
+        return time.perf_counter() - t0, out
+
+    mine = [s for k, s in enumerate(seeds) if k % world == rank]
+    w0 = config.adjoint_member(seeds[0], steps)
+    s = make(w0)
+    s.adjoint(steps, K)  # warm-up (module load, allocator)
+    s.close()
+    fwd, adj, adj_all, grads = [], [], [], []
+    for seed in mine:
+        w = config.adjoint_member(seed, steps)
+        s = make(w)
+        tf, _ = timed(lambda: (s.step(steps), s.sync()))
+        s.close()
+        s = make(w)
+        ta, g = timed(lambda: s.adjoint(steps, K))
+        s.close()
+        s = make(w)
+        tall, _ = timed(lambda: s.adjoint(steps, steps))
+        s.close()
+        fwd.append(tf)
+        adj.append(ta)
+        adj_all.append(tall)
+        grads.append((g["D"], g["dD_dsigma"], float(np.linalg.norm(g["dD_dA"]))))
+    tot = [sum(fwd), sum(adj), sum(adj_all)]
+    if world > 1:
+        t = torch.tensor(tot, dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t)
+        tot = t.tolist()
+    if rank != 0:
+        return None
+    return {"metric": "adjoint/forward wall-time ratio", "value": tot[1] / tot[0], "unit": "x",
+            "higher_is_better": False, "K": K, "steps": steps, "seeds": len(seeds),
+            "forward_ms": 1e3 * tot[0] / len(seeds), "adjoint_ms": 1e3 * tot[1] / len(seeds),
+            "resident_ratio": tot[2] / tot[0], "resident_adjoint_ms": 1e3 * tot[2] / len(seeds),
+            "forward_us_per_step": 1e6 * tot[0] / len(seeds) / steps,
+            "example_rank0_seed": {"seed": mine[0], "D": grads[0][0], "dD_dsigma": grads[0][1],
+                                   "norm_dD_dA": grads[0][2]} if grads else None,
+            "config": "64^3, R 8, icosphere level 3, FP32, own OU gradients per seed (seeds 500-515), "
+                      "2000 steps; adjoint = one ibl_adjoint call (forward pass with checkpoints every K "
+                      "steps, recomputation per segment, reverse steps); resident = every step's moments "
+                      "kept in HBM (K = 2000)"}
+
+
 def run_reference(args):
     rank, world, _ = dist_info()
     if rank != 0:
@@ -351,6 +418,7 @@ def run_ours(args):
            "steps": e2e_steps, "api": "ibl_run_frames (host gradients in, host shape records out)"}
 
     ens = measure_ensemble(dev, args.ensemble_steps, 20, rank, world)
+    adj = measure_adjoint(dev, rank, world) if args.adjoint else None
 
     if rank == 0:
         cb = cpu_baseline(w) if world == 1 else None
@@ -365,7 +433,7 @@ def run_ours(args):
                              "kernel_us": t_launch * 1e6 if t_launch else None, "launches_timed": lb_n,
                              "bytes_per_launch": BYTES_PER_NODE * far_nodes, "patch_nodes": patch_nodes},
                 "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches * world, "clocks": clk,
-                "ensemble": ens,
+                "ensemble": ens, "adjoint": adj,
                 "droplet_steps_per_s": world * args.steps / (ms * 1e-3),
                 "lagrangian_updates_per_s": world * (10 * 4 ** w.level + 2) * args.steps / (ms * 1e-3)}
         print(json.dumps(line))
@@ -382,6 +450,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ensemble-steps", type=int, default=200,
                     help="timed steps of the 64-droplet ensemble measurement")
+    ap.add_argument("--no-adjoint", dest="adjoint", action="store_false",
+                    help="skip the adjoint/forward measurement (16 seeds of the 64^3 droplet)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

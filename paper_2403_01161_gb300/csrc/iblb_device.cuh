@@ -178,9 +178,8 @@ __device__ __forceinline__ bool node_in_patch(const LbView &L, const Ctl *c, int
 // (Eq. (pi_drop), F_i = -sigma dA/dx_i summed over the triangles around i):
 // m_t x (x_{slot+2} - x_{slot+1}) with the scaled unit normal
 // m_t = -sigma/2 N/|N|, N = (x1 - x0) x (x2 - x0).  Positions are FP64; the
-// edge vectors are formed in FP64 and the rest runs in G (FP64 for FP64
-// storage; FP32 for FP32 storage, whose spread rounds the force to FP32
-// anyway -- the FP64 pipe of this GPU is 1/64 of the FP32 one).
+// edge vectors are formed in FP64 and the rest runs in G (the step uses
+// FP64 mesh geometry for either population precision).
 template <typename G>
 __device__ __forceinline__ void tri_force(const MeshView &M, const int t, const int slot, G g[3])
 {
@@ -195,7 +194,7 @@ __device__ __forceinline__ void tri_force(const MeshView &M, const int t, const 
         e2[a] = G(x[2][a] - x[0][a]);
     }
     cross3(e1, e2, N);
-    const G s = G(-0.5) * G(M.sigma) / sqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
+    const G s = G(-0.5) * G(M.sigma) * rsqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
     const G m[3] = {s * N[0], s * N[1], s * N[2]};
     const int kp = slot == 2 ? 0 : slot + 1, km = slot == 0 ? 2 : slot - 1;
     const G dd[3] = {G(x[km][0] - x[kp][0]), G(x[km][1] - x[kp][1]), G(x[km][2] - x[kp][2])};

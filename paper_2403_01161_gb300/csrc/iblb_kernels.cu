@@ -501,20 +501,20 @@ __device__ __forceinline__ void spread_body(const LbView &L, const MeshView &M, 
     const int lane = threadIdx.x % kLanesPerNode;
     const bool valid = gid < M.nv;
     const int i = valid ? gid : M.nv - 1;
-    T F[3] = {T(0), T(0), T(0)};
+    double F[3] = {0.0, 0.0, 0.0};
     for (int k = M.n2t_ptr[i] + lane; k < M.n2t_ptr[i + 1]; k += kLanesPerNode) {
         const int e = M.n2t[k];
         const int t = e / 3;
-        T g[3];
-        tri_force<T>(M, t, e - 3 * t, g);
+        double g[3];
+        tri_force<double>(M, t, e - 3 * t, g);
         for (int a = 0; a < 3; ++a) F[a] += g[a];
     }
     for (int o = kLanesPerNode / 2; o > 0; o >>= 1)
         for (int a = 0; a < 3; ++a) F[a] += __shfl_xor_sync(0xffffffffu, F[a], o, kLanesPerNode);
     if (valid && lane == 0) {
-        M.fn[3 * i] = (double)F[0];
-        M.fn[3 * i + 1] = (double)F[1];
-        M.fn[3 * i + 2] = (double)F[2];
+        M.fn[3 * i] = F[0];
+        M.fn[3 * i + 1] = F[1];
+        M.fn[3 * i + 2] = F[2];
     }
     const NodeStencil S = node_stencil(L, M.r + 3 * i, lane);
     if (!valid) return;
@@ -530,7 +530,7 @@ __device__ __forceinline__ void spread_body(const LbView &L, const MeshView &M, 
     const int nx = L.n[0], nxy = L.n[0] * L.n[1], nodes = L.nodes;
     const int row = wrap_index(S.base[1] + b, L.n[1], pery) * nx + wrap_index(S.base[2] + c, L.n[2], perz) * nxy;
     T *force = static_cast<T *>(L.force);
-    const T Fx = F[0], Fy = F[1], Fz = F[2];
+    const T Fx = T(F[0]), Fy = T(F[1]), Fz = T(F[2]);
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
         const T dl = w[a] * wy * wz;

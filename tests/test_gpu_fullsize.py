@@ -38,11 +38,7 @@ def _one_step_check(w, k, tol_f, tol_r):
     r_g, F_g, _ = g.mesh()
     r_o, F_o = o.mesh()
     assert np.abs(r_g - r_o).max() < tol_r
-    # nodal forces (Eq. pi_drop): FP64 arithmetic for FP64 storage; FP32
-    # arithmetic on FP64 edge differences for FP32 storage (the spread rounds
-    # them to FP32), a few tens of FP32 ulp of the largest force
-    tol_F = 1e-12 * max(1.0, np.abs(F_o).max()) if w.precision == "fp64" else 1e-5 * np.abs(F_o).max()
-    assert np.abs(F_g - F_o).max() < tol_F
+    assert np.abs(F_g - F_o).max() < 1e-12 * max(1.0, np.abs(F_o).max())
     _, u_g, Fe_g = g.fields()
     _, u_o, Fe_o = o.fields()
     assert rel(u_g, u_o) < 1e-5
