@@ -313,6 +313,50 @@ def measure_adjoint(dev, rank, world, seeds=range(500, 516), steps=2000, K=100):
                       "kept in HBM (K = 2000)"}
 
 
+PAPER_TRAJECTORY_HOURS = 3.0   # Sec. 3.2: about 3 h per trajectory on one A100
+PAPER_TRAJECTORY_FRAMES = 2000  # Sec. 3.2: about 2000 gradient frames per trajectory
+
+
+def measure_production(dev, steps, warmup):
+    """The paper's production setup (200^3, R 19, level 5, tau_f 1.5, 496 steps
+    per frame, a shape record per frame) timed with the same graph replay:
+    step time, MLUPS and the projected time of a 2000-frame trajectory next to
+    the paper's A100 figure."""
+    import torch
+
+    from paper_2403_01161_gb300 import config
+    from paper_2403_01161_gb300.sim import Sim
+
+    w = config.production_200(steps=warmup + steps)
+    s = Sim(w.n, w.tau, w.frames, w.n_hold, precision=w.precision, device=dev)
+    s.add_icosphere(w.level, w.R, w.sigma)
+    s.set_readout(w.n_hold)
+    s.step(warmup)
+    s.sync()
+    stream = torch.cuda.current_stream(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    s.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    st = s.status()
+    D = s.readout()["D"]
+    s.close()
+    if st != 0:
+        raise RuntimeError("device error status %d in the production run" % st)
+    traj_steps = PAPER_TRAJECTORY_FRAMES * w.n_hold
+    hours = ms / steps * 1e-3 * traj_steps / 3600.0
+    return {"metric": "hours per 2000-frame trajectory", "value": hours, "unit": "h", "higher_is_better": False,
+            "paper_a100_hours": PAPER_TRAJECTORY_HOURS, "speedup_vs_paper": PAPER_TRAJECTORY_HOURS / hours,
+            "us_per_step": 1e3 * ms / steps, "mlups": w.nodes * steps / (ms * 1e-3) / 1e6, "steps": steps,
+            "warmup": warmup, "steps_per_frame": w.n_hold, "final_D": D,
+            "config": "200^3, R 19, icosphere level 5 (20480 triangles), tau_f 1.5, R/eta 0.472, Ca 0.2, "
+                      "OU gradients (seed 6), FP32 populations, shape record per frame"}
+
+
 def run_reference(args):
     rank, world, _ = dist_info()
     if rank != 0:
@@ -419,6 +463,7 @@ def run_ours(args):
 
     ens = measure_ensemble(dev, args.ensemble_steps, 20, rank, world)
     adj = measure_adjoint(dev, rank, world) if args.adjoint else None
+    prod = measure_production(dev, 2 * 1488, 1488) if args.production else None
 
     if rank == 0:
         cb = cpu_baseline(w) if world == 1 else None
@@ -433,7 +478,7 @@ def run_ours(args):
                              "kernel_us": t_launch * 1e6 if t_launch else None, "launches_timed": lb_n,
                              "bytes_per_launch": BYTES_PER_NODE * far_nodes, "patch_nodes": patch_nodes},
                 "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches * world, "clocks": clk,
-                "ensemble": ens, "adjoint": adj,
+                "ensemble": ens, "adjoint": adj, "production": prod,
                 "droplet_steps_per_s": world * args.steps / (ms * 1e-3),
                 "lagrangian_updates_per_s": world * (10 * 4 ** w.level + 2) * args.steps / (ms * 1e-3)}
         print(json.dumps(line))
@@ -452,6 +497,12 @@ def main():
                     help="timed steps of the 64-droplet ensemble measurement")
     ap.add_argument("--no-adjoint", dest="adjoint", action="store_false",
                     help="skip the adjoint/forward measurement (16 seeds of the 64^3 droplet)")
+    ap.add_argument("--no-production", dest="production", action="store_false",
+                    help="skip the 200^3 production-setup measurement")
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="run only the adjoint/forward measurement and print its JSON (profiling aid)")
+    ap.add_argument("--adjoint-seeds", type=int, default=16)
+    ap.add_argument("--adjoint-steps", type=int, default=2000)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -459,6 +510,14 @@ def main():
         ap.error("--ensemble-steps must be >= 1")
     if args.impl == "reference":
         return run_reference(args)
+    if args.adjoint_only:
+        import torch
+
+        torch.cuda.set_device(0)
+        out = measure_adjoint(torch.device("cuda", 0), 0, 1, seeds=range(500, 500 + args.adjoint_seeds),
+                              steps=args.adjoint_steps)
+        print(json.dumps(out))
+        return 0
     return run_ours(args)
 
 

@@ -109,6 +109,22 @@ def precision_stress_256(steps: int = 5000, Ca_rms: float = 0.5) -> Workload:
                         reg_every=50)
 
 
+def production_200(steps: int = 2 * 1488, seed: int = 6, Ca: float = 0.2, R_over_eta: float = 0.472) -> Workload:
+    """The paper's production setup (Sec. 3.2): 200^3 box, R = 19 lattice
+    units, 20480-triangle mesh (icosphere level 5), tau_f = 1.5, with the DNS
+    conversion of Eqs. (cl), (ct), (N_Reta), (capillary) and
+    (surfacetensionconversion) at R/eta = 0.472: N = 496 steps per frame,
+    rms gradient 1/tau_eta in lattice units, sigma from Ca.  OU gradients
+    (seed) stand in for the database trajectory; one shape record per frame."""
+    d = dns_to_lbu(R_over_eta, 19.0, 1.5, Ca)
+    n_hold = int(round(d["N"]))
+    tau_eta = d["tau_eta_lbu"]
+    n_frames = steps // n_hold + 2
+    frames = inputs.ou_gradients(seed, n_frames, n_hold, 20.0 * tau_eta, 1.0 / tau_eta)
+    return Workload("production_200", (200, 200, 200), 1.5, 5, 19.0, d["sigma_lbu"], frames, n_hold, steps,
+                    readout_every=n_hold)
+
+
 def adjoint_member(seed: int, steps: int = 2000) -> Workload:
     """64^3 box, R = 8, icosphere level 3, OU gradients (seed), rms Ca 0.2."""
     return _ou_workload("adjoint_64_seed%d" % seed, 64, 8.0, 3, seed, steps)

@@ -51,6 +51,13 @@ def test_single_droplet_128_one_step():
     _one_step_check(config.single_droplet_128(steps=100), 61, 2e-6, 1e-8)
 
 
+def test_production_200_one_step():
+    """The paper's production setup (200^3, R = 19, level 5, tau_f = 1.5,
+    one shape record per 496-step frame): state after 61 GPU steps."""
+    w = config.production_200(steps=100)
+    _one_step_check(w, 61, 2e-6, 1e-8)
+
+
 @pytest.mark.slow
 def test_precision_stress_256_one_step():
     """256^3, R = 24, level 5 (10242 nodes), regularisation every 50 steps:
