@@ -63,7 +63,8 @@ def config_dict(w, extra=None):
 def traffic_from_profiles():
     """Per-launch DRAM bytes of the lattice kernel from the committed ncu
     record, if it was taken on the current lattice source (the part of the
-    kernel file up to the end of the lattice kernel)."""
+    kernel file up to the end of the lattice kernel, plus the shared device
+    header it includes)."""
     p = os.path.join(ROOT, "profiles", "lattice_traffic.json")
     if not os.path.exists(p):
         return None
@@ -75,7 +76,8 @@ def traffic_from_profiles():
     marker = "// Advances the step counter when no droplet kernel follows the lattice kernel."
     if marker not in src:
         return None
-    h = hashlib.sha256(src[: src.index(marker)].encode()).hexdigest()
+    hdr = open(os.path.join(ROOT, "paper_2403_01161_gb300", "csrc", "iblb_device.cuh")).read()
+    h = hashlib.sha256((src[: src.index(marker)] + hdr).encode()).hexdigest()
     if d.get("lattice_source_sha256") != h:
         return None
     return float(d["bytes_per_launch_full_size"])
