@@ -291,15 +291,30 @@ __device__ __forceinline__ bool lattice_node(const LbView &L, const int x, const
                 f[opp(i) * qs + node] = g[i];
             });
         } else {
-            // destination x + c_i, slot i
+            // destination x + c_i, slot i.  The node coordinates pass through
+            // an opaque move, so the neighbour offsets are recomputed here
+            // instead of being held in registers across the collision (which
+            // made this kernel spill).
+            int xs = x, ys = y, zs = z;
+            asm volatile("mov.b32 %0, %0;" : "+r"(xs));
+            asm volatile("mov.b32 %0, %0;" : "+r"(ys));
+            asm volatile("mov.b32 %0, %0;" : "+r"(zs));
+            const int nodes_ = xs + nx * ys + nxy * zs;
+            int sxm = -1, sxp = 1, sym = -nx, syp = nx, szm = -nxy, szp = nxy, smiss = 0;
+            if (xs == 0) { if (px) sxm = nx - 1; else smiss |= 1; }
+            if (xs == nx - 1) { if (px) sxp = -(nx - 1); else smiss |= 2; }
+            if (ys == 0) { if (py) sym = (ny - 1) * nx; else smiss |= 4; }
+            if (ys == ny - 1) { if (py) syp = -(ny - 1) * nx; else smiss |= 8; }
+            if (zs == 0) { if (pz) szm = (nz - 1) * nxy; else smiss |= 16; }
+            if (zs == nz - 1) { if (pz) szp = -(nz - 1) * nxy; else smiss |= 32; }
             sfor<19>([&](auto I) {
                 constexpr int i = decltype(I)::value;
                 constexpr int cx = cxf(i), cy = cyf(i), cz = czf(i);
                 constexpr int need = (cx > 0 ? 2 : (cx < 0 ? 1 : 0)) | (cy > 0 ? 8 : (cy < 0 ? 4 : 0)) |
                                      (cz > 0 ? 32 : (cz < 0 ? 16 : 0));
-                const int off = (cx > 0 ? oxp : (cx < 0 ? oxm : 0)) + (cy > 0 ? oyp : (cy < 0 ? oym : 0)) +
-                                (cz > 0 ? ozp : (cz < 0 ? ozm : 0));
-                if ((miss & need) == 0) f[i * qs + node + off] = g[i];
+                const int off = (cx > 0 ? sxp : (cx < 0 ? sxm : 0)) + (cy > 0 ? syp : (cy < 0 ? sym : 0)) +
+                                (cz > 0 ? szp : (cz < 0 ? szm : 0));
+                if ((smiss & need) == 0) f[i * qs + nodes_ + off] = g[i];
             });
         }
         if (in_patch) {
@@ -323,7 +338,7 @@ __device__ __forceinline__ bool lattice_node(const LbView &L, const int x, const
 }
 
 template <typename T, bool ODD, bool REC, int MODE>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? (ODD ? 3 : 4) : 2) k_lattice(LbView L, int pbuf)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_lattice(LbView L, int pbuf)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -367,7 +382,7 @@ __global__ void __launch_bounds__(256) k_lattice_near(LbView L, int buf)
 // kernel parameters) and covers its 256 consecutive nodes starting at
 // 256 * (b0 + b - blk_start[member]) in x-fastest order.
 template <typename T, bool ODD>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? (ODD ? 3 : 4) : 2)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
     k_lattice_batched(const __grid_constant__ LbGroup G, const int m0, const int b0,
                       const int *__restrict__ blk_member, const int *__restrict__ blk_start, const int pbuf)
 {
