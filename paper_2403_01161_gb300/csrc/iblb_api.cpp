@@ -748,6 +748,7 @@ struct AdjLayout {
     size_t ck_f = 0, ck_ctl = 0, ck_r = 0, ck_part = 0;  // offsets inside one checkpoint
     size_t f_bytes = 0, r_bytes = 0, part_bytes = 0, ck_step = 0;
     long long n_seg = 0;
+    long long kmax = 0;                                  // steps per slot set
 };
 
 bool adj_layout(const ibl_lb *lb, const ibl_mesh *m, long long T, int K, AdjLayout &A)
@@ -786,8 +787,10 @@ bool adj_layout(const ibl_lb *lb, const ibl_mesh *m, long long T, int K, AdjLayo
     A.acc = take(sizeof(double) * (1 + 9 * (size_t)lb->v.n_frames));
     A.obs = take(sizeof(double) * 11);
     A.t0 = take(sizeof(long long));
-    A.rec = take(A.rec_step * (size_t)kmax);
-    A.traj = take(A.traj_step * (size_t)kmax);
+    // two slot sets: one segment is recorded while the next is swept back
+    A.kmax = kmax;
+    A.rec = take(A.rec_step * (size_t)kmax * 2);
+    A.traj = take(A.traj_step * (size_t)kmax * 2);
     A.ck = take(A.ck_step * (size_t)(A.n_seg + 1));
     A.total = off;
     return true;
@@ -1503,25 +1506,33 @@ int ibl_adjoint(ibl_lb *lb, long long n_steps, int K, void *workspace, size_t by
     // per t0 mod 6 -- parity and patch buffer -- and shape-record setting);
     // a shorter one runs eagerly.  Shape records are taken only in the
     // forward pass, never when a segment is recorded again.
+    // slot set `set` (segment sg uses set sg % 2) holds step k's moments and
+    // positions + patch
+    auto rec_slot = [&](int set, int k) -> char * { return ws + A.rec + A.rec_step * ((size_t)set * A.kmax + k); };
+    auto traj_slot = [&](int set, int k) -> char * {
+        return ws + A.traj + A.traj_step * ((size_t)set * A.kmax + k);
+    };
     std::map<int, cudaGraphExec_t> rec_graph;
     const size_t patch_off = offsetof(Ctl, patch_lo);
+    int hook_set = 0;
     auto record_hook = [&](int k, cudaStream_t, cudaStream_t sH) -> int {
-        char *slot = ws + A.traj + A.traj_step * k;
+        char *slot = traj_slot(hook_set, k);
         cudaError_t ee = cudaMemcpyAsync(slot, m->v.r, A.r_bytes, cudaMemcpyDeviceToDevice, sH);
         // the patch of the step (written by the previous force kernel on this stream)
         if (ee == cudaSuccess)
             ee = cudaMemcpyAsync(slot + A.traj_ctl + patch_off, reinterpret_cast<char *>(lb->v.ctl) + patch_off,
                                  sizeof(Ctl) - patch_off, cudaMemcpyDeviceToDevice, sH);
         if (ee != cudaSuccess) return cuda_fail(ee, "trajectory copy");
-        lb->v.rec = ws + A.rec + A.rec_step * k;
+        lb->v.rec = rec_slot(hook_set, k);
         return IBL_OK;
     };
-    auto record_segment = [&](long long t0, int len, bool shape_records) -> int {
+    auto record_segment = [&](long long t0, int len, bool shape_records, int set, cudaStream_t q) -> int {
         lb->host_step = t0;
+        hook_set = set;
         m->readout_every = shape_records ? readout : 0;
         int r = IBL_OK;
         if (len == K) {
-            const int key = (int)(t0 % 6) + (shape_records ? 6 : 0);
+            const int key = (int)(t0 % 6) + (shape_records ? 6 : 0) + 12 * set;
             auto it = rec_graph.find(key);
             if (it == rec_graph.end()) {
                 cudaGraphExec_t g = nullptr;
@@ -1533,14 +1544,14 @@ int ibl_adjoint(ibl_lb *lb, long long n_steps, int K, void *workspace, size_t by
                 it = rec_graph.emplace(key, g).first;
             }
             m->readout_every = readout;
-            const cudaError_t ee = cudaGraphLaunch(it->second, s);
+            const cudaError_t ee = cudaGraphLaunch(it->second, q);
             if (ee != cudaSuccess) return cuda_fail(ee, "recording graph launch");
             lb->host_step = t0 + len;
             return IBL_OK;
         }
         for (int k = 0; k < len && r == IBL_OK; ++k) {
-            r = record_hook(k, s, s);
-            if (r == IBL_OK) r = one_step(lb, true, s, s);
+            r = record_hook(k, q, q);
+            if (r == IBL_OK) r = one_step(lb, true, q, q);
         }
         lb->v.rec = rec_saved;
         m->readout_every = readout;
@@ -1548,30 +1559,36 @@ int ibl_adjoint(ibl_lb *lb, long long n_steps, int K, void *workspace, size_t by
     };
     // Reverse sweep of a recorded segment on two streams, as the forward
     // step: the helper stream (high priority) runs the interpolation
-    // adjoint, the patch nodes and the surface adjoint, the bound stream the
+    // adjoint, the patch nodes and the surface adjoint, the main stream the
     // nodes outside the patch; step k's patch update waits for step k+1's
     // outside update and vice versa.  Full-length segments replay a captured
-    // graph (one per parity of the adjoint buffer pair).
+    // graph (one per slot set and parity of the adjoint buffer pair).
     int cur = 0;  // lam[cur] holds the adjoint of the populations of step t + 1
-    cudaGraphExec_t rev_graph[2] = {nullptr, nullptr};
-    cudaEvent_t ev[8] = {};
-    for (int k = 0; k < 8 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
+    cudaGraphExec_t rev_graph[4] = {nullptr, nullptr, nullptr, nullptr};
+    // events: 0-3 the reverse chain inside a capture, 4-7 eager, 8-9 a
+    // recorded set ready, 10-11 a set released by its reverse sweep, 12 start
+    cudaEvent_t ev[13] = {};
+    cudaStream_t s_rec = nullptr;  // stream of the recordings that overlap the reverse sweep
+    for (int k = 0; k < 13 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s_rec, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         for (cudaEvent_t x : ev)
             if (x) cudaEventDestroy(x);
+        if (s_rec) cudaStreamDestroy(s_rec);
         return cuda_fail(e, "adjoint events");
     }
-    auto enqueue_reverse = [&](int len, int c0, cudaStream_t sL, cudaStream_t sH, bool capture) -> cudaError_t {
+    auto enqueue_reverse = [&](int len, int c0, int set, cudaStream_t sL, cudaStream_t sH,
+                               bool capture) -> cudaError_t {
         cudaEvent_t *eN = capture ? ev : ev + 4, *eF = eN + 2;
         cudaError_t ee = join(sL, sH, capture ? lb->cFork : lb->evFork);
         int c = c0;
         for (int k = len - 1; k >= 0 && ee == cudaSuccess; --k) {
             const int p = k & 1;
-            char *slot = ws + A.traj + A.traj_step * k;
+            char *slot = traj_slot(set, k);
             MeshView Mt = m->v;
             Mt.r = reinterpret_cast<double *>(slot);
             const Ctl *pc = reinterpret_cast<const Ctl *>(slot + A.traj_ctl);
-            const void *rec = ws + A.rec + A.rec_step * k;
+            const void *rec = rec_slot(set, k);
             ee = iblb::launch_adj_interp(lb->v, Mt, J, rec, sH, lb->hi_prio);
             if (ee == cudaSuccess && k < len - 1) ee = cudaStreamWaitEvent(sH, eF[p ^ 1], 0);
             if (ee == cudaSuccess) ee = iblb::launch_adj_near(lb->v, J, rec, lam[c], lam[c ^ 1], pc, k, sH, lb->hi_prio);
@@ -1585,27 +1602,27 @@ int ibl_adjoint(ibl_lb *lb, long long n_steps, int K, void *workspace, size_t by
         if (ee == cudaSuccess) ee = join(sH, sL, capture ? lb->cJoin : lb->evJoin);
         return ee;
     };
-    auto reverse_segment = [&](long long t0, int len) -> int {
+    auto reverse_segment = [&](long long t0, int len, int set) -> int {
         cudaError_t ee = iblb::launch_adj_set_t0(J, t0, s);
         if (ee != cudaSuccess) return cuda_fail(ee, "adjoint segment start");
         if (len == K) {
-            if (!rev_graph[cur]) {
+            cudaGraphExec_t &g = rev_graph[cur + 2 * set];
+            if (!g) {
                 cudaStream_t cL = lb->cap_stream, cH = lb->cap_helper;
                 ee = cudaStreamBeginCapture(cL, cudaStreamCaptureModeThreadLocal);
                 if (ee != cudaSuccess) return cuda_fail(ee, "begin capture");
-                const cudaError_t e1 = enqueue_reverse(len, cur, cL, cH, true);
-                cudaGraph_t g = nullptr;
-                const cudaError_t e2 = cudaStreamEndCapture(cL, &g);
+                const cudaError_t e1 = enqueue_reverse(len, cur, set, cL, cH, true);
+                cudaGraph_t gr = nullptr;
+                const cudaError_t e2 = cudaStreamEndCapture(cL, &gr);
                 ee = e1 != cudaSuccess ? e1 : e2;
-                if (ee == cudaSuccess)
-                    ee = cudaGraphInstantiateWithFlags(&rev_graph[cur], g, cudaGraphInstantiateFlagUseNodePriority);
-                if (g) cudaGraphDestroy(g);
+                if (ee == cudaSuccess) ee = cudaGraphInstantiateWithFlags(&g, gr, cudaGraphInstantiateFlagUseNodePriority);
+                if (gr) cudaGraphDestroy(gr);
                 if (ee != cudaSuccess) return cuda_fail(ee, "adjoint graph capture");
-                graphs.push_back(rev_graph[cur]);
+                graphs.push_back(g);
             }
-            ee = cudaGraphLaunch(rev_graph[cur], s);
+            ee = cudaGraphLaunch(g, s);
         } else {
-            ee = enqueue_reverse(len, cur, s, lb->helper, false);
+            ee = enqueue_reverse(len, cur, set, s, lb->helper, false);
         }
         if (ee != cudaSuccess) return cuda_fail(ee, "adjoint step launch");
         cur ^= (len & 1);
@@ -1623,30 +1640,53 @@ int ibl_adjoint(ibl_lb *lb, long long n_steps, int K, void *workspace, size_t by
         }
         const int len = (int)std::min<long long>(K, n_steps - sg * K);
         if (sg < last) st = ibl_step(lb, len);
-        else st = record_segment(sg * K, len, true);
+        else st = record_segment(sg * K, len, true, (int)(sg & 1), s);
     }
     if (st == IBL_OK) {
         e = adj_save(lb, A, ws, A.n_seg, s);
         // seed: D of the final mesh and dD/dr_T
         if (e == cudaSuccess) e = iblb::launch_adj_seed(m->v, J, s);
+        // the recordings start after the forward pass
+        if (e == cudaSuccess) e = cudaEventRecord(ev[12], s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s_rec, ev[12], 0);
         if (e != cudaSuccess) st = cuda_fail(e, "adjoint seed");
     }
-    // reverse sweep: the last segment from its recording, the others after
-    // restoring their checkpoint and recording them again
+    // Reverse sweep, last segment first.  While segment sg is swept back on
+    // the main stream, segment sg - 1 is restored from its checkpoint and
+    // recorded on its own stream into the other slot set; it waits for the
+    // sweep of sg + 1, which used that set.  Both chains are latency-bound,
+    // so they share the GPU well.
     for (long long sg = last; sg >= 0 && st == IBL_OK; --sg) {
         const long long t0 = sg * K;
         const int len = (int)std::min<long long>(K, n_steps - t0);
+        const int set = (int)(sg & 1);
         if (sg < last) {
-            e = adj_restore(lb, A, ws, sg, s);
+            e = cudaStreamWaitEvent(s, ev[8 + set], 0);
             if (e != cudaSuccess) {
-                st = cuda_fail(e, "checkpoint restore");
+                st = cuda_fail(e, "adjoint ordering");
                 break;
             }
-            st = record_segment(t0, len, false);
-            if (st != IBL_OK) break;
         }
-        st = reverse_segment(t0, len);
+        st = reverse_segment(t0, len, set);
+        if (st != IBL_OK) break;
+        e = cudaEventRecord(ev[10 + set], s);
+        if (e == cudaSuccess && sg >= 1) {
+            const long long prev = sg - 1;
+            const int pset = (int)(prev & 1);
+            if (sg + 1 <= last) e = cudaStreamWaitEvent(s_rec, ev[10 + pset], 0);
+            if (e == cudaSuccess) e = adj_restore(lb, A, ws, prev, s_rec);
+            if (e == cudaSuccess) {
+                st = record_segment(prev * K, K, false, pset, s_rec);
+                if (st != IBL_OK) break;
+                e = cudaEventRecord(ev[8 + pset], s_rec);
+            }
+        }
+        if (e != cudaSuccess) st = cuda_fail(e, "adjoint recording");
     }
+    // the main stream resumes after every recording
+    if (e == cudaSuccess) e = cudaEventRecord(ev[12], s_rec);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[12], 0);
+    if (e != cudaSuccess && st == IBL_OK) st = cuda_fail(e, "adjoint join");
     lb->v.rec = rec_saved;
     // the initial populations depend on frame 0
     if (st == IBL_OK) {
@@ -1669,8 +1709,10 @@ int ibl_adjoint(ibl_lb *lb, long long n_steps, int K, void *workspace, size_t by
         if (e != cudaSuccess) st = cuda_fail(e, "adjoint readout");
     }
     const cudaError_t es2 = cudaStreamSynchronize(s);
+    cudaStreamSynchronize(s_rec);
     for (cudaGraphExec_t g : graphs) cudaGraphExecDestroy(g);
     for (cudaEvent_t x : ev) cudaEventDestroy(x);
+    cudaStreamDestroy(s_rec);
     if (st != IBL_OK) return st;
     if (es2 != cudaSuccess) return cuda_fail(es2, "adjoint synchronize");
     st = lb_status_from_device(lb);

@@ -338,7 +338,7 @@ __device__ __forceinline__ bool lattice_node(const LbView &L, const int x, const
 }
 
 template <typename T, bool ODD, bool REC, int MODE>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_lattice(LbView L, int pbuf)
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 4) k_lattice(LbView L, int pbuf)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -897,8 +897,11 @@ cudaError_t launch_init(const LbView &L, cudaStream_t s)
 
 static void lattice_grid(const LbView &L, dim3 &grid, dim3 &block)
 {
+    // 128-thread blocks (8 per SM at 64 registers): a concurrently running
+    // droplet-kernel block then displaces an eighth of an SM's lattice work
+    // rather than a quarter
     const int bx = L.n[0] >= 128 ? 128 : ((L.n[0] + 31) / 32) * 32;
-    const int by = 256 / bx;
+    const int by = 128 / bx;
     block = dim3(bx, by, 1);
     grid = dim3((L.n[0] + bx - 1) / bx, (L.n[1] + by - 1) / by, L.n[2]);
 }
