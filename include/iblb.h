@@ -303,8 +303,9 @@ void ibl_ensemble_destroy(ibl_ensemble *e);
  * the recomputation writes none).  The workspace (device, 256-byte
  * aligned, caller-owned, `bytes` from ibl_adjoint_workspace_size) holds
  * ceil(n_steps / K) + 1 checkpoints (populations, control block, positions)
- * plus min(K, n_steps) steps of recorded moments (7 values per lattice
- * node) and positions, and the adjoint fields.  Errors: IBL_EINVAL for a
+ * plus two sets of min(K, n_steps) steps of recorded moments (7 values per
+ * lattice node), positions and patches (one segment is recorded again on a
+ * second stream while the next is swept back), and the adjoint fields.  Errors: IBL_EINVAL for a
  * bad state or argument, IBL_ENOMEM for a short workspace, and the sticky
  * device errors of the forward and recomputed steps. */
 int ibl_adjoint_workspace_size(const ibl_lb *lb, long long n_steps, int K, size_t *bytes);
