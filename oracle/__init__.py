@@ -7,7 +7,8 @@ and neither imports the other.
 
 The lattice and immersed-boundary step is plain C (``iblb_oracle.c``, built
 with gcc and loaded through ctypes); the mesh generator, the one-ring
-neighbourhoods and the shape observables are plain numpy in ``oracle.py``.
+neighbourhoods and the shape observables are plain numpy in ``oracle.py``;
+the linear theory of Eq. (LT) is plain numpy in ``theory.py``.
 """
 from .oracle import (  # noqa: F401
     build,
@@ -32,3 +33,4 @@ from .oracle import (  # noqa: F401
     ERR_NOCONV,
     ERR_WALL,
 )
+from .theory import lt_coefficients, lt_observables, lt_propagate, lt_trajectory, strain  # noqa: F401,E402
