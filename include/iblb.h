@@ -312,6 +312,28 @@ int ibl_adjoint_workspace_size(const ibl_lb *lb, long long n_steps, int K, size_
 int ibl_adjoint(ibl_lb *lb, long long n_steps, int K, void *workspace, size_t bytes, double *D, double *dD_dsigma,
                 double *dD_dA, double *dD_dr0);
 
+/* ---- linear theory ---------------------------------------------------- */
+
+/* The small-deformation theory of Eq. (LT) (Sec. 2), the paper's reference
+ * for the Ca -> 0 limit, along many gradient trajectories at once:
+ *   dS/dt = -(40(chi+1) / ((2chi+3)(19chi+16))) (S - R^2 I) / tau_sigma
+ *           + 2 R^2 (5/(2chi+3)) E(t),   S(0) = R^2 I,
+ * E the symmetric part of the frame in force, each frame held for `hold`
+ * time units (lattice steps for the IBLB frames, Sec. 3.2), integrated by
+ * the classical fourth-order Runge-Kutta method with `substeps` steps per
+ * frame in FP64.  Device arrays (caller-owned): A [n_traj][n_frames][9]
+ * row-major frames as in ibl_lb_create; params [n_traj][4] = tau_sigma, R,
+ * chi, hold per trajectory; out [n_traj][n_frames][9] = S_xx, S_yy, S_zz,
+ * S_xy, S_xz, S_yz, lambda_max / R^2, beta (Eq. (beta); NaN when E = 0) and
+ * D at the end of every frame (D takes the smallest eigenvalue as 0 if the
+ * theory has been driven past positive definiteness).  A trajectory with
+ * tau_sigma <= 0, R <= 0, chi < 0, hold <= 0 or a non-finite parameter gets
+ * NaN throughout.  Asynchronous on `stream` (a cudaStream_t, NULL = legacy
+ * default stream); allocates nothing.  IBL_EINVAL for counts < 1, substeps
+ * outside 1..2^20 or a null pointer. */
+int ibl_linear_theory(int n_traj, int n_frames, const double *A, const double *params, int substeps,
+                      double *out, void *stream);
+
 /* ---- introspection --------------------------------------------------- */
 
 /* Synchronises and returns the droplet patch of the next step: lower

@@ -84,6 +84,7 @@ SIGNATURES = [
     ("ibl_run_frames", ctypes.c_int, [_P, _P, _D, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Observables)]),
     ("ibl_adjoint_workspace_size", ctypes.c_int, [_P, ctypes.c_longlong, ctypes.c_int, _SZ]),
     ("ibl_adjoint", ctypes.c_int, [_P, ctypes.c_longlong, ctypes.c_int, _P, ctypes.c_size_t, _D, _D, _D, _D]),
+    ("ibl_linear_theory", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P, ctypes.c_int, _P, _P]),
     ("ibl_ensemble_workspace_size", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_P), _SZ]),
     ("ibl_ensemble_create", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_P), _P, ctypes.c_size_t,
                                            ctypes.POINTER(_P)]),

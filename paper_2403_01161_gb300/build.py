@@ -24,7 +24,7 @@ def nvcc_path() -> str:
 
 
 def sources():
-    return [os.path.join(CSRC, f) for f in ("iblb_kernels.cu", "iblb_adjoint.cu", "iblb_api.cpp")]
+    return [os.path.join(CSRC, f) for f in ("iblb_kernels.cu", "iblb_adjoint.cu", "iblb_theory.cu", "iblb_api.cpp")]
 
 
 def _deps():
