@@ -359,6 +359,51 @@ def measure_production(dev, steps, warmup):
                       "OU gradients (seed 6), FP32 populations, shape record per frame"}
 
 
+def measure_linear_theory(dev, n_traj=1000, n_frames=2000, Ca_values=(0.05, 0.2), seed=700):
+    """The linear theory of Eq. (LT) along n_traj synthetic OU trajectories of
+    n_frames frames at the production conversion (R 19 lattice units, tau_f
+    1.5, R/eta 0.472, N = 496 steps per frame, chi 1): GPU time of the batched
+    RK4 integration and the distributions of lambda_max/R^2 and beta (a
+    synthetic analogue of the paper's ensemble statistics, first 50 frames of
+    each trajectory dropped)."""
+    import numpy as np
+    import torch
+
+    from paper_2403_01161_gb300 import config, inputs
+    from paper_2403_01161_gb300.theory import linear_theory
+
+    out = {"metric": "trajectory-frames/s", "trajectories": n_traj, "frames": n_frames, "substeps": 8,
+           "config": "R 19, tau_f 1.5, R/eta 0.472, 496 steps per frame, chi 1, OU gradients (rms 1/tau_eta, "
+                     "correlation 20 tau_eta), seed %d; quantiles 5/25/50/75/95 %% after 50 frames" % seed,
+           "by_Ca": {}}
+    q = [5, 25, 50, 75, 95]
+    for Ca in Ca_values:
+        d = config.dns_to_lbu(0.472, 19.0, 1.5, Ca)
+        hold = float(round(d["N"]))
+        tau_eta = d["tau_eta_lbu"]
+        fr = torch.as_tensor(inputs.ou_gradients_batch(seed, n_traj, n_frames, hold, 20.0 * tau_eta, 1.0 / tau_eta),
+                             device=dev)
+        linear_theory(fr[:2, :8], d["tau_sigma_lbu"], 19.0, hold, 1.0, substeps=8, device=dev)  # warm-up
+        stream = torch.cuda.current_stream(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        res = linear_theory(fr, d["tau_sigma_lbu"], 19.0, hold, 1.0, substeps=8, device=dev)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        r = res[:, 50:].cpu().numpy()
+        lam, beta = r[..., 6].ravel(), r[..., 7].ravel()
+        beta = beta[np.isfinite(beta)]
+        out["by_Ca"]["%g" % Ca] = {"ms": ms, "trajectory_frames_per_s": n_traj * n_frames / (ms * 1e-3),
+                                   "lam_max_R2_quantiles": [float(v) for v in np.percentile(lam, q)],
+                                   "beta_quantiles": [float(v) for v in np.percentile(beta, q)],
+                                   "beta_mean": float(beta.mean())}
+    out["value"] = min(v["trajectory_frames_per_s"] for v in out["by_Ca"].values())
+    return out
+
+
 def run_reference(args):
     rank, world, _ = dist_info()
     if rank != 0:
@@ -466,6 +511,7 @@ def run_ours(args):
     ens = measure_ensemble(dev, args.ensemble_steps, 20, rank, world)
     adj = measure_adjoint(dev, rank, world) if args.adjoint else None
     prod = measure_production(dev, 2 * 1488, 1488) if args.production else None
+    lt = measure_linear_theory(dev) if args.theory and rank == 0 else None
 
     if rank == 0:
         cb = cpu_baseline(w) if world == 1 else None
@@ -480,7 +526,7 @@ def run_ours(args):
                              "kernel_us": t_launch * 1e6 if t_launch else None, "launches_timed": lb_n,
                              "bytes_per_launch": BYTES_PER_NODE * far_nodes, "patch_nodes": patch_nodes},
                 "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches * world, "clocks": clk,
-                "ensemble": ens, "adjoint": adj, "production": prod,
+                "ensemble": ens, "adjoint": adj, "production": prod, "linear_theory": lt,
                 "droplet_steps_per_s": world * args.steps / (ms * 1e-3),
                 "lagrangian_updates_per_s": world * (10 * 4 ** w.level + 2) * args.steps / (ms * 1e-3)}
         print(json.dumps(line))
@@ -501,6 +547,8 @@ def main():
                     help="skip the adjoint/forward measurement (16 seeds of the 64^3 droplet)")
     ap.add_argument("--no-production", dest="production", action="store_false",
                     help="skip the 200^3 production-setup measurement")
+    ap.add_argument("--no-theory", dest="theory", action="store_false",
+                    help="skip the linear-theory ensemble measurement")
     ap.add_argument("--adjoint-only", action="store_true",
                     help="run only the adjoint/forward measurement and print its JSON (profiling aid)")
     ap.add_argument("--adjoint-seeds", type=int, default=16)

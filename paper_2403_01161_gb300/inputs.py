@@ -18,7 +18,8 @@ import numpy as np
 
 
 def traceless(x: np.ndarray) -> np.ndarray:
-    return x - np.trace(x) / 3.0 * np.eye(3)
+    """x minus its trace part (over the last two axes, so stacks work too)."""
+    return x - (np.trace(x, axis1=-2, axis2=-1) / 3.0)[..., None, None] * np.eye(3)
 
 
 def ou_gradients(seed: int, n_frames: int, dt: float, T: float, a_rms: float) -> np.ndarray:
@@ -32,6 +33,21 @@ def ou_gradients(seed: int, n_frames: int, dt: float, T: float, a_rms: float) ->
     for k in range(1, n_frames):
         out[k] = a * out[k - 1] + b * s * traceless(rng.standard_normal((3, 3)))
     return out
+
+
+def ou_gradients_batch(seed: int, n_traj: int, n_frames: int, dt: float, T: float, a_rms: float) -> np.ndarray:
+    """(n_traj, n_frames, 3, 3) float64: n_traj independent traceless OU
+    gradient sequences of the same law as ou_gradients, drawn from one seeded
+    generator (vectorised over trajectories)."""
+    rng = np.random.default_rng(seed)
+    s = a_rms / np.sqrt(8.0)
+    a = np.exp(-dt / T)
+    b = np.sqrt(1.0 - np.exp(-2.0 * dt / T))
+    out = np.empty((n_frames, n_traj, 3, 3), dtype=np.float64)
+    out[0] = s * traceless(rng.standard_normal((n_traj, 3, 3)))
+    for k in range(1, n_frames):
+        out[k] = a * out[k - 1] + b * s * traceless(rng.standard_normal((n_traj, 3, 3)))
+    return np.ascontiguousarray(out.transpose(1, 0, 2, 3))
 
 
 def simple_shear(rate: float, flow_axis: int = 0, gradient_axis: int = 2) -> np.ndarray:
