@@ -1526,29 +1526,44 @@ int ibl_adjoint(ibl_lb *lb, long long n_steps, int K, void *workspace, size_t by
         lb->v.rec = rec_slot(hook_set, k);
         return IBL_OK;
     };
+    // graph of a full-length recording starting at t0 (captured on first use)
+    auto record_graph = [&](long long t0, bool shape_records, int set, cudaGraphExec_t *out) -> int {
+        const int key = (int)(t0 % 6) + (shape_records ? 6 : 0) + 12 * set;
+        auto it = rec_graph.find(key);
+        if (it == rec_graph.end()) {
+            const long long saved = lb->host_step;
+            lb->host_step = t0;
+            hook_set = set;
+            m->readout_every = shape_records ? readout : 0;
+            cudaGraphExec_t g = nullptr;
+            const int r = capture_steps(lb, K, true, record_hook, &g);
+            lb->v.rec = rec_saved;
+            m->readout_every = readout;
+            lb->host_step = saved;
+            if (r != IBL_OK) return r;
+            graphs.push_back(g);
+            // move the graph's device upload off the first launch
+            const cudaError_t eu = cudaGraphUpload(g, lb->cap_stream);
+            if (eu != cudaSuccess) return cuda_fail(eu, "recording graph upload");
+            it = rec_graph.emplace(key, g).first;
+        }
+        if (out) *out = it->second;
+        return IBL_OK;
+    };
     auto record_segment = [&](long long t0, int len, bool shape_records, int set, cudaStream_t q) -> int {
-        lb->host_step = t0;
-        hook_set = set;
-        m->readout_every = shape_records ? readout : 0;
         int r = IBL_OK;
         if (len == K) {
-            const int key = (int)(t0 % 6) + (shape_records ? 6 : 0) + 12 * set;
-            auto it = rec_graph.find(key);
-            if (it == rec_graph.end()) {
-                cudaGraphExec_t g = nullptr;
-                r = capture_steps(lb, len, true, record_hook, &g);
-                lb->v.rec = rec_saved;
-                m->readout_every = readout;
-                if (r != IBL_OK) return r;
-                graphs.push_back(g);
-                it = rec_graph.emplace(key, g).first;
-            }
-            m->readout_every = readout;
-            const cudaError_t ee = cudaGraphLaunch(it->second, q);
+            cudaGraphExec_t g = nullptr;
+            r = record_graph(t0, shape_records, set, &g);
+            if (r != IBL_OK) return r;
+            const cudaError_t ee = cudaGraphLaunch(g, q);
             if (ee != cudaSuccess) return cuda_fail(ee, "recording graph launch");
             lb->host_step = t0 + len;
             return IBL_OK;
         }
+        lb->host_step = t0;
+        hook_set = set;
+        m->readout_every = shape_records ? readout : 0;
         for (int k = 0; k < len && r == IBL_OK; ++k) {
             r = record_hook(k, q, q);
             if (r == IBL_OK) r = one_step(lb, true, q, q);
@@ -1602,25 +1617,33 @@ int ibl_adjoint(ibl_lb *lb, long long n_steps, int K, void *workspace, size_t by
         if (ee == cudaSuccess) ee = join(sH, sL, capture ? lb->cJoin : lb->evJoin);
         return ee;
     };
+    // graph of a full-length reverse sweep for buffer parity c0 and slot set
+    // `set` (captured on first use)
+    auto reverse_graph = [&](int c0, int set) -> int {
+        cudaGraphExec_t &g = rev_graph[c0 + 2 * set];
+        if (g) return IBL_OK;
+        cudaStream_t cL = lb->cap_stream, cH = lb->cap_helper;
+        cudaError_t ee = cudaStreamBeginCapture(cL, cudaStreamCaptureModeThreadLocal);
+        if (ee != cudaSuccess) return cuda_fail(ee, "begin capture");
+        const cudaError_t e1 = enqueue_reverse(K, c0, set, cL, cH, true);
+        cudaGraph_t gr = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(cL, &gr);
+        ee = e1 != cudaSuccess ? e1 : e2;
+        if (ee == cudaSuccess) ee = cudaGraphInstantiateWithFlags(&g, gr, cudaGraphInstantiateFlagUseNodePriority);
+        if (gr) cudaGraphDestroy(gr);
+        if (ee != cudaSuccess) return cuda_fail(ee, "adjoint graph capture");
+        graphs.push_back(g);
+        ee = cudaGraphUpload(g, lb->cap_stream);
+        if (ee != cudaSuccess) return cuda_fail(ee, "adjoint graph upload");
+        return IBL_OK;
+    };
     auto reverse_segment = [&](long long t0, int len, int set) -> int {
         cudaError_t ee = iblb::launch_adj_set_t0(J, t0, s);
         if (ee != cudaSuccess) return cuda_fail(ee, "adjoint segment start");
         if (len == K) {
-            cudaGraphExec_t &g = rev_graph[cur + 2 * set];
-            if (!g) {
-                cudaStream_t cL = lb->cap_stream, cH = lb->cap_helper;
-                ee = cudaStreamBeginCapture(cL, cudaStreamCaptureModeThreadLocal);
-                if (ee != cudaSuccess) return cuda_fail(ee, "begin capture");
-                const cudaError_t e1 = enqueue_reverse(len, cur, set, cL, cH, true);
-                cudaGraph_t gr = nullptr;
-                const cudaError_t e2 = cudaStreamEndCapture(cL, &gr);
-                ee = e1 != cudaSuccess ? e1 : e2;
-                if (ee == cudaSuccess) ee = cudaGraphInstantiateWithFlags(&g, gr, cudaGraphInstantiateFlagUseNodePriority);
-                if (gr) cudaGraphDestroy(gr);
-                if (ee != cudaSuccess) return cuda_fail(ee, "adjoint graph capture");
-                graphs.push_back(g);
-            }
-            ee = cudaGraphLaunch(g, s);
+            const int r = reverse_graph(cur, set);
+            if (r != IBL_OK) return r;
+            ee = cudaGraphLaunch(rev_graph[cur + 2 * set], s);
         } else {
             ee = enqueue_reverse(len, cur, set, s, lb->helper, false);
         }
@@ -1650,6 +1673,17 @@ int ibl_adjoint(ibl_lb *lb, long long n_steps, int K, void *workspace, size_t by
         if (e == cudaSuccess) e = cudaEventRecord(ev[12], s);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s_rec, ev[12], 0);
         if (e != cudaSuccess) st = cuda_fail(e, "adjoint seed");
+    }
+    // Capture every graph the sweep below will replay while the GPU runs the
+    // forward pass just enqueued (capture and instantiation are host work).
+    {
+        int c = cur;
+        for (long long sg = last; sg >= 0 && st == IBL_OK; --sg) {
+            const int len = (int)std::min<long long>(K, n_steps - sg * K);
+            if (len == K) st = reverse_graph(c, (int)(sg & 1));
+            if (st == IBL_OK && sg >= 1) st = record_graph((sg - 1) * K, false, (int)((sg - 1) & 1), nullptr);
+            c ^= (len & 1);
+        }
     }
     // Reverse sweep, last segment first.  While segment sg is swept back on
     // the main stream, segment sg - 1 is restored from its checkpoint and
