@@ -404,6 +404,57 @@ def measure_linear_theory(dev, n_traj=1000, n_frames=2000, Ca_values=(0.05, 0.2)
     return out
 
 
+def regularization_study(dev, steps=50000, sample=2000):
+    """Sec. 3.3 in practice: one sub-critical droplet trajectory (96^3, R 10,
+    level 4, rms Ca 0.2, OU gradients changing direction every 2 tau_eta)
+    without regularisation, with the paper's smoothing on fixed schedules,
+    and with the adaptive trigger (smooth when the longest/shortest edge
+    ratio exceeds a threshold, checked every step).  Per mode: steps run
+    before a device error (or all), volume relative to the initial sphere,
+    edge-ratio extremes at the samples, smoothings performed, step time."""
+    import numpy as np
+    import torch
+
+    from paper_2403_01161_gb300 import config
+    from paper_2403_01161_gb300.sim import Sim
+
+    w = config.small_ou(N=96, R=10.0, level=4, seed=77, steps=steps + 10000, Ca_rms=0.2, T_over_tau_eta=2.0)
+    V0 = 4.0 / 3.0 * np.pi * w.R ** 3
+    # (name, schedule, trigger); "none" checks quality on the sampling schedule but never smooths
+    modes = [("none", sample, 1e300), ("every50", 50, 0.0), ("every10", 10, 0.0), ("every1", 1, 0.0),
+             ("adaptive3", 1, 3.0), ("adaptive2", 1, 2.0)]
+    out = {"config": "96^3, R 10, icosphere level 4, FP32, rms Ca 0.2, OU seed 77 with correlation 2 tau_eta, "
+                     "%d steps, samples every %d; paper parameters alpha 0.1, gamma 0.51, tol 0.01" % (steps, sample),
+           "modes": {}}
+    for name, every, trig in modes:
+        s = Sim(w.n, w.tau, w.frames, w.n_hold, precision=w.precision, device=dev)
+        s.add_icosphere(w.level, w.R, w.sigma)
+        s.set_regularization(every=every)
+        s.set_regularization_trigger(trig)
+        qs, vs, done, ms = [], [], 0, 0.0
+        for _ in range(steps // sample):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            s.step(sample)
+            e1.record()
+            if s.status() != 0:
+                break
+            ms += e0.elapsed_time(e1)
+            done += sample
+            n_reg, q = s.regularization_stats()
+            qs.append(q)
+            vs.append(s.readout()["V"] / V0)
+        out["modes"][name] = {"schedule": every, "trigger": trig if trig < 1e299 else None, "steps_run": done,
+                              "V_over_V0_final": vs[-1] if vs else None, "V_over_V0_min": min(vs) if vs else None,
+                              "edge_ratio_max": max(qs) if qs else None, "edge_ratio_final": qs[-1] if qs else None,
+                              "smoothings": n_reg if name != "none" else 0,
+                              "us_per_step": 1e3 * ms / done if done else None,
+                              "V_samples": [round(v, 4) for v in vs], "edge_ratio_samples": [round(q, 2) for q in qs]}
+        s.close()
+    return out
+
+
 def run_reference(args):
     rank, world, _ = dist_info()
     if rank != 0:
@@ -549,6 +600,8 @@ def main():
                     help="skip the 200^3 production-setup measurement")
     ap.add_argument("--no-theory", dest="theory", action="store_false",
                     help="skip the linear-theory ensemble measurement")
+    ap.add_argument("--regularization-study", action="store_true",
+                    help="run only the mesh-regularisation study (Sec. 3.3) and print its JSON")
     ap.add_argument("--adjoint-only", action="store_true",
                     help="run only the adjoint/forward measurement and print its JSON (profiling aid)")
     ap.add_argument("--adjoint-seeds", type=int, default=16)
@@ -560,6 +613,12 @@ def main():
         ap.error("--ensemble-steps must be >= 1")
     if args.impl == "reference":
         return run_reference(args)
+    if args.regularization_study:
+        import torch
+
+        torch.cuda.set_device(0)
+        print(json.dumps(regularization_study(torch.device("cuda", 0))))
+        return 0
     if args.adjoint_only:
         import torch
 

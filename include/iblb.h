@@ -161,6 +161,24 @@ void ibl_mesh_destroy(ibl_mesh *m);
 int ibl_set_regularization(ibl_mesh *m, double alpha, double gamma, double tol, int max_iter,
                            int every, int plus_sign);
 
+/* Adaptive trigger for the scheduled regularisation (the paper regularises
+ * unconditionally; this makes the smoothing conditional on the mesh
+ * degrading, Sec. 3.3's motivation: clustered nodes and loose triangles).
+ * At each scheduled regularisation the kernel first measures the mesh
+ * quality q = max over triangles of (longest edge / shortest edge), which is
+ * 1 for equilateral triangles; with max_edge_ratio > 0 it smooths only when
+ * q > max_edge_ratio, otherwise the step is left as it is.  0 (the default)
+ * smooths at every scheduled step.  Values in (0, 1) are rejected
+ * (IBL_EINVAL).  ibl_regularize_now always smooths.  Synchronises the
+ * lattice's stream. */
+int ibl_set_regularization_trigger(ibl_mesh *m, double max_edge_ratio);
+
+/* Synchronising: *count = regularisations performed so far (triggered
+ * scheduled ones and ibl_regularize_now calls), *mesh_quality = q measured
+ * at the latest regularisation check (0 before the first).  Either pointer
+ * may be NULL. */
+int ibl_regularization_stats(ibl_mesh *m, int *count, double *mesh_quality);
+
 /* Take a shape record every `every` steps (0 = off) into a device ring of
  * 4096 records, read with ibl_read_series. */
 int ibl_set_readout(ibl_mesh *m, int every);

@@ -24,6 +24,7 @@ from .oracle import (  # noqa: F401
     icosphere,
     one_ring,
     observables,
+    mesh_quality,
     OracleSim,
     BC_ZOU_HE,
     BC_PERIODIC,

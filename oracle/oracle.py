@@ -244,6 +244,16 @@ def one_ring(tris: np.ndarray, nv: int):
     return ptr, np.array(idx, dtype=np.int32)
 
 
+def mesh_quality(r, tris) -> float:
+    """Largest ratio of longest to shortest edge over the triangles (1 for an
+    equilateral mesh); the degradation Sec. 3.3 regularises against shows as
+    clustered nodes (short edges) and loose triangles (long edges)."""
+    r = np.asarray(r, dtype=np.float64)
+    t = np.asarray(tris)
+    e = np.stack([np.linalg.norm(r[t[:, (k + 1) % 3]] - r[t[:, k]], axis=1) for k in range(3)], axis=1)
+    return float((e.max(axis=1) / e.min(axis=1)).max())
+
+
 def observables(r, tris, A=None) -> dict:
     """Volume, area, centroid, S, eigenvalues, v_max, Taylor D and beta (Sec. 2).
 

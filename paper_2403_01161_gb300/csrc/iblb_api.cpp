@@ -1019,12 +1019,37 @@ int ibl_set_regularization(ibl_mesh *m, double alpha, double gamma, double tol, 
     if (!m) return fail(IBL_EINVAL, "null mesh");
     if (!(alpha >= 0 && alpha <= 1) || !(gamma >= 0 && gamma <= 1) || !(tol > 0) || max_iter < 1 || every < 0)
         return fail(IBL_EINVAL, "regularisation parameters out of range");
-    m->reg = iblb::RegParams{alpha, gamma, tol, max_iter, plus_sign ? 1 : 0};
+    m->reg = iblb::RegParams{alpha, gamma, tol, max_iter, plus_sign ? 1 : 0, m->reg.trigger};
     m->reg_every = every;
     if (m->lb) {
         cudaStreamSynchronize(m->lb->stream);
         drop_graph(m->lb);
     }
+    return IBL_OK;
+}
+
+int ibl_set_regularization_trigger(ibl_mesh *m, double max_edge_ratio)
+{
+    if (!m || !(max_edge_ratio >= 0.0) || !std::isfinite(max_edge_ratio))
+        return fail(IBL_EINVAL, "the trigger must be a finite ratio >= 0 (0 = always regularise)");
+    if (max_edge_ratio > 0.0 && max_edge_ratio < 1.0) return fail(IBL_EINVAL, "an edge ratio below 1 never occurs");
+    m->reg.trigger = max_edge_ratio;
+    if (m->lb) {
+        cudaStreamSynchronize(m->lb->stream);
+        drop_graph(m->lb);  // captured chunks hold the parameters by value
+    }
+    return IBL_OK;
+}
+
+int ibl_regularization_stats(ibl_mesh *m, int *count, double *mesh_quality)
+{
+    if (!m || !m->lb) return fail(IBL_EINVAL, "null mesh");
+    Ctl c;
+    cudaError_t e = cudaMemcpyAsync(&c, m->lb->v.ctl, sizeof c, cudaMemcpyDeviceToHost, m->lb->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->lb->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "regularisation stats");
+    if (count) *count = c.reg_count;
+    if (mesh_quality) *mesh_quality = c.mesh_q;
     return IBL_OK;
 }
 
@@ -1255,7 +1280,9 @@ int ibl_regularize_now(ibl_mesh *m, int *iters)
 {
     if (!m || !m->lb) return fail(IBL_EINVAL, "null mesh");
     ibl_lb *lb = m->lb;
-    cudaError_t e = iblb::launch_regularize(lb->v, m->v, m->reg, (int)(lb->host_step % 3), lb->stream);
+    iblb::RegParams now = m->reg;
+    now.trigger = 0.0;  // unconditional, whatever the schedule's trigger
+    cudaError_t e = iblb::launch_regularize(lb->v, m->v, now, (int)(lb->host_step % 3), lb->stream);
     if (e != cudaSuccess) return cuda_fail(e, "regularisation launch");
     Ctl c;
     e = cudaMemcpyAsync(&c, lb->v.ctl, sizeof c, cudaMemcpyDeviceToHost, lb->stream);

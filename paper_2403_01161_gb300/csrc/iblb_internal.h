@@ -24,6 +24,8 @@ struct alignas(128) Ctl {
     int reg_iters;               // iterations of the latest regularisation
     int n_records;               // shape records written
     int frame;                   // frame index applied by the next step
+    int reg_count;               // regularisations performed (scheduled checks that triggered)
+    double mesh_q;               // mesh quality at the last scheduled check: max over triangles of longest/shortest edge
     int patch_lo[3][4];          // droplet patch of step t in buffer t % 3: lower corner (inside the box)
     int patch_ext[3][4];         // extent (hi - lo), -1 = empty
 };
@@ -70,6 +72,7 @@ struct RegParams {
     double alpha, gamma, tol;
     int max_iter;
     int plus_sign;
+    double trigger;  // > 0: smooth only when the mesh quality exceeds it; 0: always
 };
 
 // An ensemble step launches each phase once per group of up to kGroup

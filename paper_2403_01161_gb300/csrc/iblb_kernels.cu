@@ -705,6 +705,27 @@ __global__ void __launch_bounds__(1024) k_regularize(LbView L, MeshView M, RegPa
 {
     __shared__ double sh[32];
     const int nv = M.nv;
+    // mesh quality: the largest ratio of longest to shortest edge over the
+    // triangles (node clustering and loose, stretched elements both raise it)
+    double q = 1.0;
+    for (int t = threadIdx.x; t < M.nt; t += blockDim.x) {
+        const int v[3] = {M.tris[3 * t], M.tris[3 * t + 1], M.tris[3 * t + 2]};
+        double e2[3];
+        for (int k = 0; k < 3; ++k) {
+            const double *a = M.r + 3 * v[k], *b = M.r + 3 * v[(k + 1) % 3];
+            const double dx = b[0] - a[0], dy = b[1] - a[1], dz = b[2] - a[2];
+            e2[k] = dx * dx + dy * dy + dz * dz;
+        }
+        const double lo = fmin(e2[0], fmin(e2[1], e2[2])), hi = fmax(e2[0], fmax(e2[1], e2[2]));
+        q = fmax(q, lo > 0.0 ? sqrt(hi / lo) : 1e300);
+    }
+    q = block_max(q, sh);
+    if (threadIdx.x == 0) L.ctl->mesh_q = q;
+    if (p.trigger > 0.0 && !(q > p.trigger)) {
+        // adaptive schedule: the mesh is still regular enough, nothing to do
+        if (threadIdx.x == 0) L.ctl->reg_iters = 0;
+        return;
+    }
     double *xo = M.s0, *xb = M.s2;
     double *buf[2] = {M.r, M.s1};
     for (int i = threadIdx.x; i < 3 * nv; i += blockDim.x) xo[i] = M.r[i];
@@ -757,6 +778,7 @@ __global__ void __launch_bounds__(1024) k_regularize(LbView L, MeshView M, RegPa
     block_bbox_patch(L, M, M.r, nv, patch_buf);
     if (threadIdx.x == 0) {
         L.ctl->reg_iters = it;
+        L.ctl->reg_count += 1;
         if (!conv) atomicOr(&L.ctl->err, IBL_ERRBIT_NOCONV);
     }
 }

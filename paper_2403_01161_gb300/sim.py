@@ -144,6 +144,18 @@ class Sim:
         L.check(self.lib.ibl_set_regularization(self.mesh_h, alpha, gamma, tol, max_iter, every,
                                                 1 if plus_sign else 0))
 
+    def set_regularization_trigger(self, max_edge_ratio: float):
+        """Smooth at a scheduled step only when the mesh quality (max over
+        triangles of longest/shortest edge) exceeds max_edge_ratio; 0 = always."""
+        L.check(self.lib.ibl_set_regularization_trigger(self.mesh_h, float(max_edge_ratio)))
+
+    def regularization_stats(self):
+        """(regularisations performed, mesh quality at the latest check)."""
+        n = ctypes.c_int()
+        q = np.zeros(1)
+        L.check(self.lib.ibl_regularization_stats(self.mesh_h, ctypes.byref(n), _dp(q)))
+        return n.value, float(q[0])
+
     def set_readout(self, every: int):
         L.check(self.lib.ibl_set_readout(self.mesh_h, int(every)))
 

@@ -87,3 +87,30 @@ def test_taylor_shear_fp64_full_run():
     assert abs(ob["beta"] - ref["beta"]) < 1e-10
     # confined, finite-resolution droplet: deformation near 1.36 x Taylor's 35/32 Ca
     assert 1.2 < ob["D"] / (35 / 32 * 0.1) < 1.5
+
+
+def test_long_trajectory_matches_oracle_through_mesh_degradation():
+    """5000 steps of a 40^3 box, R = 5, level 3, FP64, OU gradients at rms
+    Ca 0.3 changing direction every 2 tau_eta, no regularisation: the mesh
+    degrades (longest/shortest edge ratio from 1.2 past 10) and the droplet
+    starts losing volume, and the GPU trajectory stays on the oracle's to
+    round-off all the way (node positions, volume, mesh quality, lambda_max)."""
+    w = config.small_ou(N=40, R=5.0, level=3, seed=77, steps=20000, Ca_rms=0.3, T_over_tau_eta=2.0)
+    c = config.box_center(w.n)
+    g = Sim(w.n, w.tau, w.frames, w.n_hold, precision="fp64")
+    g.add_icosphere(w.level, w.R, w.sigma, center=c)
+    o = O.OracleSim(w.n, w.tau, w.frames, w.n_hold)
+    r0, t = O.icosphere(w.level, w.R, c)
+    o.set_mesh(r0, t, w.sigma)
+    for _ in range(5):
+        g.step(1000)
+        o.step(1000)
+    r_g, _, _ = g.mesh()
+    r_o, _ = o.mesh()
+    assert g.status() == 0 and o.error == 0
+    assert np.abs(r_g - r_o).max() < 1e-9
+    assert O.mesh_quality(r_o, t) > 10.0
+    ob_g, ob_o = O.observables(r_g, t), O.observables(r_o, t)
+    assert abs(ob_g["V"] - ob_o["V"]) < 1e-9 * ob_o["V"]
+    assert ob_o["V"] < 0.96 * 4 / 3 * np.pi * w.R ** 3
+    assert abs(ob_g["lam"][2] - ob_o["lam"][2]) < 1e-9 * ob_o["lam"][2]

@@ -191,3 +191,17 @@ def test_beta_steady_shear(golden):
                / (np.sqrt(ob["lam"][2]) + np.sqrt(ob["lam"][0]))) < 1e-15
     assert abs(ob["D"] - (1.2 - 0.9) / (1.2 + 0.9)) < 5e-3
     assert np.isnan(O.observables(r, t, np.zeros((3, 3)))["beta"])
+
+
+def test_mesh_quality_pins():
+    """Equilateral meshes give exactly 1 (the regular icosahedron, a regular
+    tetrahedron); a 3-4-5 right triangle gives 5/3."""
+    r, t = O.icosphere(0, 3.0)
+    assert abs(O.mesh_quality(r, t) - 1.0) < 1e-12
+    tet = np.array([[1, 1, 1], [1, -1, -1], [-1, 1, -1], [-1, -1, 1]], dtype=float)
+    assert abs(O.mesh_quality(tet, np.array([[0, 1, 2], [0, 3, 1], [0, 2, 3], [1, 3, 2]])) - 1.0) < 1e-12
+    tri = np.array([[0, 0, 0], [3, 0, 0], [0, 4, 0]], dtype=float)
+    assert abs(O.mesh_quality(tri, np.array([[0, 1, 2]])) - 5 / 3) < 1e-12
+    # subdivision keeps the icosphere close to equilateral
+    r3, t3 = O.icosphere(3, 1.0)
+    assert 1.0 < O.mesh_quality(r3, t3) < 1.3
