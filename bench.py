@@ -408,8 +408,9 @@ def regularization_study(dev, steps=50000, sample=2000):
     """Sec. 3.3 in practice: one sub-critical droplet trajectory (96^3, R 10,
     level 4, rms Ca 0.2, OU gradients changing direction every 2 tau_eta)
     without regularisation, with the paper's smoothing on fixed schedules,
-    and with the adaptive trigger (smooth when the longest/shortest edge
-    ratio exceeds a threshold, checked every step).  Per mode: steps run
+    with the adaptive trigger (smooth when the longest/shortest edge ratio
+    exceeds a threshold, checked every step), and with the volume-restoring
+    option.  Per mode: steps run
     before a device error (or all), volume relative to the initial sphere,
     edge-ratio extremes at the samples, smoothings performed, step time."""
     import numpy as np
@@ -421,16 +422,20 @@ def regularization_study(dev, steps=50000, sample=2000):
     w = config.small_ou(N=96, R=10.0, level=4, seed=77, steps=steps + 10000, Ca_rms=0.2, T_over_tau_eta=2.0)
     V0 = 4.0 / 3.0 * np.pi * w.R ** 3
     # (name, schedule, trigger); "none" checks quality on the sampling schedule but never smooths
-    modes = [("none", sample, 1e300), ("every50", 50, 0.0), ("every10", 10, 0.0), ("every1", 1, 0.0),
-             ("adaptive3", 1, 3.0), ("adaptive2", 1, 2.0)]
+    # (name, schedule, trigger, keep volume); "none" checks quality on the
+    # sampling schedule but never smooths
+    modes = [("none", sample, 1e300, False), ("every50", 50, 0.0, False), ("every10", 10, 0.0, False),
+             ("every1", 1, 0.0, False), ("adaptive3", 1, 3.0, False), ("every1_keep_volume", 1, 0.0, True),
+             ("adaptive3_keep_volume", 1, 3.0, True), ("every10_keep_volume", 10, 0.0, True)]
     out = {"config": "96^3, R 10, icosphere level 4, FP32, rms Ca 0.2, OU seed 77 with correlation 2 tau_eta, "
                      "%d steps, samples every %d; paper parameters alpha 0.1, gamma 0.51, tol 0.01" % (steps, sample),
            "modes": {}}
-    for name, every, trig in modes:
+    for name, every, trig, keep in modes:
         s = Sim(w.n, w.tau, w.frames, w.n_hold, precision=w.precision, device=dev)
         s.add_icosphere(w.level, w.R, w.sigma)
         s.set_regularization(every=every)
         s.set_regularization_trigger(trig)
+        s.set_regularization_keep_volume(keep)
         qs, vs, done, ms = [], [], 0, 0.0
         for _ in range(steps // sample):
             e0 = torch.cuda.Event(enable_timing=True)
@@ -445,7 +450,8 @@ def regularization_study(dev, steps=50000, sample=2000):
             n_reg, q = s.regularization_stats()
             qs.append(q)
             vs.append(s.readout()["V"] / V0)
-        out["modes"][name] = {"schedule": every, "trigger": trig if trig < 1e299 else None, "steps_run": done,
+        out["modes"][name] = {"schedule": every, "trigger": trig if trig < 1e299 else None, "keep_volume": keep,
+                              "steps_run": done,
                               "V_over_V0_final": vs[-1] if vs else None, "V_over_V0_min": min(vs) if vs else None,
                               "edge_ratio_max": max(qs) if qs else None, "edge_ratio_final": qs[-1] if qs else None,
                               "smoothings": n_reg if name != "none" else 0,

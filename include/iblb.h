@@ -173,6 +173,13 @@ int ibl_set_regularization(ibl_mesh *m, double alpha, double gamma, double tol, 
  * lattice's stream. */
 int ibl_set_regularization_trigger(ibl_mesh *m, double max_edge_ratio);
 
+/* keep != 0: after every regularisation (scheduled or ibl_regularize_now),
+ * scale the mesh about its volume centroid back to the volume it enclosed
+ * before the smoothing (the paper has no such step; the smoothing of
+ * Sec. 3.3 alone shrinks a curved mesh a little at each application, which
+ * adds up over long runs).  Default 0.  Synchronises the lattice's stream. */
+int ibl_set_regularization_keep_volume(ibl_mesh *m, int keep);
+
 /* Synchronising: *count = regularisations performed so far (triggered
  * scheduled ones and ibl_regularize_now calls), *mesh_quality = q measured
  * at the latest regularisation check (0 before the first).  Either pointer

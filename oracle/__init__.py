@@ -25,6 +25,8 @@ from .oracle import (  # noqa: F401
     one_ring,
     observables,
     mesh_quality,
+    enclosed_volume,
+    restore_volume,
     OracleSim,
     BC_ZOU_HE,
     BC_PERIODIC,

@@ -299,6 +299,39 @@ void orc_nodal_forces(int nv, const double *r, int nt, const int *tri, double si
 }
 
 /* ---------------------------------------------------------------------------
+ * Enclosed volume and volume centroid of a closed, outward-oriented triangle
+ * mesh, summed over the signed tetrahedra (x_0, a, b, c) of its triangles;
+ * each tetrahedron's centroid is the mean of its four corners.
+ */
+void orc_enclosed_volume(int nv, const double *x, int nt, const int *tri, double *V, double *c)
+{
+    (void)nv;
+    double v = 0.0, m[3] = {0.0, 0.0, 0.0};
+    for (int t = 0; t < nt; ++t) {
+        double p[3][3];
+        for (int k = 0; k < 3; ++k)
+            for (int a = 0; a < 3; ++a) p[k][a] = x[3 * tri[3 * t + k] + a] - x[a];
+        double bc[3];
+        cross(p[1], p[2], bc);
+        double vt = (p[0][0] * bc[0] + p[0][1] * bc[1] + p[0][2] * bc[2]) / 6.0;
+        v += vt;
+        for (int a = 0; a < 3; ++a) m[a] += vt * (p[0][a] + p[1][a] + p[2][a]) / 4.0;
+    }
+    *V = v;
+    for (int a = 0; a < 3; ++a) c[a] = x[a] + m[a] / v;
+}
+
+/* Scales the mesh about its volume centroid so that it encloses V_target. */
+void orc_restore_volume(int nv, double *x, int nt, const int *tri, double V_target)
+{
+    double V, c[3];
+    orc_enclosed_volume(nv, x, nt, tri, &V, c);
+    double f = cbrt(V_target / V);
+    for (int i = 0; i < nv; ++i)
+        for (int a = 0; a < 3; ++a) x[3 * i + a] = c[a] + f * (x[3 * i + a] - c[a]);
+}
+
+/* ---------------------------------------------------------------------------
  * Mesh regularisation, Sec. 3.3 (extended Laplacian smoothing).
  * plus_sign = 1 reads the correction of Eq. (HC_algo_full) as
  *   x_p <- x_p - (gamma b_i + (1-gamma)/N_i sum_j b_j)
@@ -375,7 +408,7 @@ typedef struct {
     int *tri;
     double sigma;
     int *nb_ptr, *nb_idx;
-    int reg_every, reg_max_iter, reg_plus, reg_last_iters;
+    int reg_every, reg_max_iter, reg_plus, reg_last_iters, reg_keep_volume;
     double reg_alpha, reg_gamma, reg_tol;
 } orc_sim;
 
@@ -463,6 +496,10 @@ void orc_sim_set_regularization(orc_sim *s, double alpha, double gamma, double t
     s->reg_alpha = alpha; s->reg_gamma = gamma; s->reg_tol = tol;
     s->reg_max_iter = max_iter; s->reg_every = every; s->reg_plus = plus_sign;
 }
+
+/* keep = 1: every regularisation is followed by orc_restore_volume to the
+ * volume enclosed before it (an option beyond Sec. 3.3). */
+void orc_sim_set_regularization_volume(orc_sim *s, int keep) { s->reg_keep_volume = keep; }
 
 /* Stencil of the 4-point kernel along axis a around coordinate ra: the four
  * nodes floor(ra)-1 .. floor(ra)+2 with their weights.  On a Zou-He axis all
@@ -606,9 +643,12 @@ int orc_sim_step(orc_sim *s, long nsteps)
             interpolate_advect(s);
             if (s->reg_every > 0 && (s->step + 1) % s->reg_every == 0) {
                 int conv = 0;
+                double V0 = 0.0, c0[3];
+                if (s->reg_keep_volume) orc_enclosed_volume(s->nv, s->r, s->nt, s->tri, &V0, c0);
                 s->reg_last_iters = orc_regularize(s->nv, s->r, s->nb_ptr, s->nb_idx, s->reg_alpha,
                                                    s->reg_gamma, s->reg_tol, s->reg_max_iter,
                                                    s->reg_plus, &conv);
+                if (s->reg_keep_volume) orc_restore_volume(s->nv, s->r, s->nt, s->tri, V0);
                 if (!conv) s->err |= ERR_NOCONV;
             }
         }

@@ -66,6 +66,9 @@ def lib():
             L.orc_regularize.argtypes = [ctypes.c_int, _D, _I, _I, ctypes.c_double, ctypes.c_double,
                                          ctypes.c_double, ctypes.c_int, ctypes.c_int, _I]
             L.orc_regularize.restype = ctypes.c_int
+            L.orc_enclosed_volume.argtypes = [ctypes.c_int, _D, ctypes.c_int, _I, _D, _D]
+            L.orc_restore_volume.argtypes = [ctypes.c_int, _D, ctypes.c_int, _I, ctypes.c_double]
+            L.orc_sim_set_regularization_volume.argtypes = [ctypes.c_void_p, ctypes.c_int]
             L.orc_sim_create.argtypes = [_I, _I, ctypes.c_double, ctypes.c_int, _D, ctypes.c_int,
                                          ctypes.c_int]
             L.orc_sim_create.restype = ctypes.c_void_p
@@ -150,14 +153,39 @@ def nodal_forces(r, tris, sigma: float) -> np.ndarray:
     return F
 
 
-def regularize(r, nb_ptr, nb_idx, alpha=0.1, gamma=0.51, tol=0.01, max_iter=100, plus_sign=True):
-    """Sec. 3.3 extended Laplacian smoothing; returns (positions, iterations, converged)."""
+def enclosed_volume(r, tris):
+    """(V, volume centroid) of a closed outward-oriented mesh (signed tetrahedra)."""
+    x = np.ascontiguousarray(r, dtype=np.float64)
+    t = np.ascontiguousarray(tris, dtype=np.int32)
+    V = np.zeros(1)
+    c = np.zeros(3)
+    lib().orc_enclosed_volume(x.shape[0], _dp(x), t.shape[0], _ip(t), _dp(V), _dp(c))
+    return float(V[0]), c
+
+
+def restore_volume(r, tris, V_target):
+    """The mesh scaled about its volume centroid to enclose V_target."""
+    x = np.ascontiguousarray(r, dtype=np.float64).copy()
+    t = np.ascontiguousarray(tris, dtype=np.int32)
+    lib().orc_restore_volume(x.shape[0], _dp(x), t.shape[0], _ip(t), float(V_target))
+    return x
+
+
+def regularize(r, nb_ptr, nb_idx, alpha=0.1, gamma=0.51, tol=0.01, max_iter=100, plus_sign=True, tris=None,
+               keep_volume=False):
+    """Sec. 3.3 extended Laplacian smoothing; returns (positions, iterations,
+    converged).  keep_volume (needs tris): afterwards scale the mesh about its
+    volume centroid back to the volume it enclosed before (an option beyond
+    Sec. 3.3)."""
     x = np.ascontiguousarray(r, dtype=np.float64).copy()
     p = np.ascontiguousarray(nb_ptr, dtype=np.int32)
     q = np.ascontiguousarray(nb_idx, dtype=np.int32)
     conv = np.zeros(1, dtype=np.int32)
+    V0 = enclosed_volume(x, tris)[0] if keep_volume else None
     it = lib().orc_regularize(x.shape[0], _dp(x), _ip(p), _ip(q), alpha, gamma, tol, max_iter,
                               1 if plus_sign else 0, _ip(conv))
+    if keep_volume:
+        x = restore_volume(x, tris, V0)
     return x, int(it), bool(conv[0])
 
 
@@ -339,9 +367,10 @@ class OracleSim:
                                 _ip(ptr), _ip(idx))
 
     def set_regularization(self, alpha=0.1, gamma=0.51, tol=0.01, max_iter=100, every=0,
-                           plus_sign=True):
+                           plus_sign=True, keep_volume=False):
         self.L.orc_sim_set_regularization(self.h, alpha, gamma, tol, max_iter, every,
                                           1 if plus_sign else 0)
+        self.L.orc_sim_set_regularization_volume(self.h, 1 if keep_volume else 0)
 
     def step(self, n=1, body_force=None) -> int:
         if body_force is None:

@@ -1019,7 +1019,7 @@ int ibl_set_regularization(ibl_mesh *m, double alpha, double gamma, double tol, 
     if (!m) return fail(IBL_EINVAL, "null mesh");
     if (!(alpha >= 0 && alpha <= 1) || !(gamma >= 0 && gamma <= 1) || !(tol > 0) || max_iter < 1 || every < 0)
         return fail(IBL_EINVAL, "regularisation parameters out of range");
-    m->reg = iblb::RegParams{alpha, gamma, tol, max_iter, plus_sign ? 1 : 0, m->reg.trigger};
+    m->reg = iblb::RegParams{alpha, gamma, tol, max_iter, plus_sign ? 1 : 0, m->reg.trigger, m->reg.keep_volume};
     m->reg_every = every;
     if (m->lb) {
         cudaStreamSynchronize(m->lb->stream);
@@ -1034,6 +1034,17 @@ int ibl_set_regularization_trigger(ibl_mesh *m, double max_edge_ratio)
         return fail(IBL_EINVAL, "the trigger must be a finite ratio >= 0 (0 = always regularise)");
     if (max_edge_ratio > 0.0 && max_edge_ratio < 1.0) return fail(IBL_EINVAL, "an edge ratio below 1 never occurs");
     m->reg.trigger = max_edge_ratio;
+    if (m->lb) {
+        cudaStreamSynchronize(m->lb->stream);
+        drop_graph(m->lb);  // captured chunks hold the parameters by value
+    }
+    return IBL_OK;
+}
+
+int ibl_set_regularization_keep_volume(ibl_mesh *m, int keep)
+{
+    if (!m) return fail(IBL_EINVAL, "null mesh");
+    m->reg.keep_volume = keep ? 1 : 0;
     if (m->lb) {
         cudaStreamSynchronize(m->lb->stream);
         drop_graph(m->lb);  // captured chunks hold the parameters by value

@@ -73,6 +73,7 @@ struct RegParams {
     int max_iter;
     int plus_sign;
     double trigger;  // > 0: smooth only when the mesh quality exceeds it; 0: always
+    int keep_volume; // rescale about the volume centroid to the volume enclosed before the smoothing
 };
 
 // An ensemble step launches each phase once per group of up to kGroup

@@ -701,6 +701,25 @@ __device__ void block_bbox_patch(const LbView &L, const MeshView &M, const doubl
 // iterate, x_p the new one (ping-pong between r and s1), x_b in s2.
 // patch_buf: patch buffer (parity) of the next step, rewritten from the
 // regularised positions.
+// This thread's share of the enclosed volume and of its first moment, summed
+// over signed tetrahedra (x_0, a, b, c) of the triangles, positions relative
+// to node 0: v[0] = V, v[1..3] = int (x - x_0) dV.
+__device__ __forceinline__ void enclosed_volume_sums(const MeshView &M, double v[4])
+{
+    v[0] = v[1] = v[2] = v[3] = 0.0;
+    const double r0[3] = {M.r[0], M.r[1], M.r[2]};
+    for (int t = threadIdx.x; t < M.nt; t += blockDim.x) {
+        double pp[3][3];
+        for (int k = 0; k < 3; ++k)
+            for (int a = 0; a < 3; ++a) pp[k][a] = M.r[3 * M.tris[3 * t + k] + a] - r0[a];
+        double bc[3];
+        cross3(pp[1], pp[2], bc);
+        const double vt = (pp[0][0] * bc[0] + pp[0][1] * bc[1] + pp[0][2] * bc[2]) / 6.0;
+        v[0] += vt;
+        for (int a = 0; a < 3; ++a) v[1 + a] += vt * (pp[0][a] + pp[1][a] + pp[2][a]) / 4.0;
+    }
+}
+
 __global__ void __launch_bounds__(1024) k_regularize(LbView L, MeshView M, RegParams p, int patch_buf)
 {
     __shared__ double sh[32];
@@ -725,6 +744,14 @@ __global__ void __launch_bounds__(1024) k_regularize(LbView L, MeshView M, RegPa
         // adaptive schedule: the mesh is still regular enough, nothing to do
         if (threadIdx.x == 0) L.ctl->reg_iters = 0;
         return;
+    }
+    __shared__ double shv[32][4];
+    double V0 = 0.0;
+    if (p.keep_volume) {
+        double v4[4];
+        enclosed_volume_sums(M, v4);
+        block_sum<4>(v4, shv);
+        V0 = v4[0];
     }
     double *xo = M.s0, *xb = M.s2;
     double *buf[2] = {M.r, M.s1};
@@ -775,6 +802,18 @@ __global__ void __launch_bounds__(1024) k_regularize(LbView L, MeshView M, RegPa
         for (int i = threadIdx.x; i < 3 * nv; i += blockDim.x) M.r[i] = M.s1[i];
     }
     __syncthreads();
+    if (p.keep_volume) {
+        // scale about the volume centroid back to the volume enclosed before
+        double v4[4];
+        enclosed_volume_sums(M, v4);
+        block_sum<4>(v4, shv);
+        const double c[3] = {M.r[0] + v4[1] / v4[0], M.r[1] + v4[2] / v4[0], M.r[2] + v4[3] / v4[0]};
+        const double f = cbrt(V0 / v4[0]);
+        __syncthreads();  // every thread has read M.r[0..2] before it moves
+        for (int i = threadIdx.x; i < nv; i += blockDim.x)
+            for (int a = 0; a < 3; ++a) M.r[3 * i + a] = c[a] + f * (M.r[3 * i + a] - c[a]);
+        __syncthreads();
+    }
     block_bbox_patch(L, M, M.r, nv, patch_buf);
     if (threadIdx.x == 0) {
         L.ctl->reg_iters = it;

@@ -149,6 +149,11 @@ class Sim:
         triangles of longest/shortest edge) exceeds max_edge_ratio; 0 = always."""
         L.check(self.lib.ibl_set_regularization_trigger(self.mesh_h, float(max_edge_ratio)))
 
+    def set_regularization_keep_volume(self, keep: bool):
+        """Rescale the mesh after every regularisation to the volume it
+        enclosed before (about its volume centroid)."""
+        L.check(self.lib.ibl_set_regularization_keep_volume(self.mesh_h, 1 if keep else 0))
+
     def regularization_stats(self):
         """(regularisations performed, mesh quality at the latest check)."""
         n = ctypes.c_int()

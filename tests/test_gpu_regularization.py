@@ -67,3 +67,45 @@ def test_regularize_now_ignores_the_trigger_and_bad_thresholds():
         assert e.value.code == L.IBL_EINVAL
     a.set_regularization_trigger(0.0)
     a.close()
+
+
+def test_keep_volume_matches_oracle():
+    """The volume-restoring option: a one-off regularisation of a stretched,
+    jittered icosphere and a coupled FP64 run with regularisation every 5
+    steps give the oracle's positions, and the one-off keeps the volume."""
+    from paper_2403_01161_gb300 import inputs
+    from paper_2403_01161_gb300.sim import Sim
+
+    r0, t = O.icosphere(3, 5.0, (15.5, 15.5, 15.5))
+    r0 = inputs.jitter((r0 - 15.5) * [1.5, 0.8, 0.9] + 15.5, 0.15, 3)
+    g = Sim((32, 32, 32), 1.0, np.zeros((1, 3, 3)), 1, precision="fp32")
+    g.add_mesh(r0, t, 0.01)
+    g.set_regularization_keep_volume(True)
+    g.regularize_now()
+    ptr, idx = O.one_ring(t, r0.shape[0])
+    x, _, conv = O.regularize(r0, ptr, idx, tris=t, keep_volume=True)
+    r_g, _, _ = g.mesh()
+    assert conv and np.abs(r_g - x).max() < 1e-12
+    V0 = O.enclosed_volume(r0, t)[0]
+    assert abs(O.enclosed_volume(r_g, t)[0] - V0) < 1e-12 * V0
+    assert O.enclosed_volume(O.regularize(r0, ptr, idx)[0], t)[0] < (1 - 1e-4) * V0
+    g.close()
+
+    fr = frames_ou(31, 3, 6e-3)
+    c = (12.5, 12.5, 12.5)
+    g = Sim((26, 26, 26), 1.0, fr, 8, precision="fp64")
+    g.add_icosphere(2, 5.0, 0.01, center=c)
+    g.set_regularization(every=5)
+    g.set_regularization_keep_volume(True)
+    o = O.OracleSim((26, 26, 26), 1.0, fr, 8)
+    rr, tt = O.icosphere(2, 5.0, c)
+    o.set_mesh(rr, tt, 0.01)
+    o.set_regularization(every=5, keep_volume=True)
+    g.step(20)
+    o.step(20)
+    r_g, _, _ = g.mesh()
+    r_o, _ = o.mesh()
+    assert np.abs(r_g - r_o).max() < 1e-11
+    assert g.regularization_stats()[0] == 4
+    g.close()
+    o.close()

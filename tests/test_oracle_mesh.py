@@ -205,3 +205,29 @@ def test_mesh_quality_pins():
     # subdivision keeps the icosphere close to equilateral
     r3, t3 = O.icosphere(3, 1.0)
     assert 1.0 < O.mesh_quality(r3, t3) < 1.3
+
+
+def test_volume_restoring_pins():
+    """The enclosed volume of a fine icosphere approaches 4/3 pi R^3 from
+    below; a mesh shrunk by s about a point p and restored to its volume is
+    the original moved by (1 - s)(p - c), c its volume centroid (the
+    restoring scales about the shrunk mesh's centroid, the image of c); a
+    regularisation with keep_volume keeps the volume."""
+    r, t = O.icosphere(5, 2.0, (1.0, -2.0, 0.5))
+    V, c = O.enclosed_volume(r, t)
+    assert 0.999 * 4 / 3 * np.pi * 8 < V < 4 / 3 * np.pi * 8
+    assert np.abs(c - np.array([1.0, -2.0, 0.5])).max() < 1e-12
+    r3, t3 = O.icosphere(3, 5.0, (3.0, 2.0, 1.0))
+    rng = np.random.default_rng(2)
+    r3 = r3 + 0.1 * rng.standard_normal(r3.shape)
+    V3 = O.enclosed_volume(r3, t3)[0]
+    p = np.array([7.0, -1.0, 4.0])
+    shrunk = p + 0.93 * (r3 - p)
+    back = O.restore_volume(shrunk, t3, V3)
+    c3 = O.enclosed_volume(r3, t3)[1]
+    assert np.abs(back - r3 - 0.07 * (p - c3)).max() < 1e-12
+    ptr, idx = O.one_ring(t3, r3.shape[0])
+    x, it, conv = O.regularize(r3, ptr, idx, tris=t3, keep_volume=True)
+    assert conv and abs(O.enclosed_volume(x, t3)[0] - V3) < 1e-12 * V3
+    x_plain, _, _ = O.regularize(r3, ptr, idx)
+    assert O.enclosed_volume(x_plain, t3)[0] < V3  # the smoothing alone shrinks this mesh
