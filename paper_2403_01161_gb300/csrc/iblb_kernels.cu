@@ -15,6 +15,7 @@
 // only the droplet patch (bounding box of the 4x4x4 stencils) is ever
 // touched: the spread adds into it, the lattice kernel reads and re-zeroes it
 // and stores the velocity there, the interpolation reads it.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -822,6 +823,180 @@ __global__ void __launch_bounds__(1024) k_regularize(LbView L, MeshView M, RegPa
     }
 }
 
+// The same regularisation on a thread-block cluster of kRegCluster CTAs
+// (one per SM), for meshes of up to kRegCluster * kRegPerCta nodes.  CTA c
+// owns nodes [c P, c P + P) and keeps their original position, the two
+// iterates and the correction b in its shared memory; neighbours owned by
+// other CTAs are read through distributed shared memory.  The hardware
+// cluster barrier separates the phases, and each CTA reduces the maxima and
+// sums published by all CTAs in the same order, so every CTA takes the same
+// decisions.  The per-triangle passes (quality, volumes) and the node
+// updates spread over the cluster's SMs instead of one.
+namespace cg = cooperative_groups;
+constexpr int kRegCluster = 16;
+constexpr int kRegPerCta = 2048;
+
+__global__ void __launch_bounds__(1024) k_regularize_cluster(LbView L, MeshView M, RegParams p, int patch_buf, int P)
+{
+    cg::cluster_group cluster = cg::this_cluster();
+    const int C = (int)cluster.num_blocks();
+    const int rank = (int)cluster.block_rank();
+    const int nv = M.nv, tid = threadIdx.x, nth = blockDim.x;
+    extern __shared__ double sm[];
+    double *xo = sm, *xa = sm + 3 * P, *xc = sm + 6 * P, *xb = sm + 9 * P;
+    double *red = sm + 12 * P;  // [8] values this CTA publishes to the cluster
+    __shared__ double shr[32];
+    __shared__ double sh4[32][4];
+    const int g0 = rank * P, g1 = min(nv, g0 + P), own = max(0, g1 - g0);
+    // cluster-wide max / sum of values published in red[0..k) by every CTA
+    auto cluster_max = [&](double v) -> double {
+        v = block_max(v, shr);
+        if (tid == 0) red[0] = v;
+        cluster.sync();
+        double m = -1e300;
+        for (int c = 0; c < C; ++c) m = fmax(m, *cluster.map_shared_rank(red, c));
+        cluster.sync();  // the slot is reused by the next reduction
+        return m;
+    };
+    auto cluster_sum4 = [&](double (&v)[4]) {
+        block_sum<4>(v, sh4);
+        if (tid < 4) red[tid] = v[tid];
+        cluster.sync();
+        for (int k = 0; k < 4; ++k) {
+            double s = 0.0;
+            for (int c = 0; c < C; ++c) s += cluster.map_shared_rank(red, c)[k];
+            v[k] = s;
+        }
+        cluster.sync();
+    };
+    // position of node j in the iterate `buf` (xa or xc), wherever it lives
+    auto pos = [&](double *buf, int j, int a) -> double {
+        const int c = j / P;
+        return cluster.map_shared_rank(buf, c)[3 * (j - c * P) + a];
+    };
+    // mesh quality over the triangles, from the positions in global memory
+    double q = 1.0;
+    for (int t = rank * nth + tid; t < M.nt; t += C * nth) {
+        const int v[3] = {M.tris[3 * t], M.tris[3 * t + 1], M.tris[3 * t + 2]};
+        double e2[3];
+        for (int k = 0; k < 3; ++k) {
+            const double *a = M.r + 3 * v[k], *b = M.r + 3 * v[(k + 1) % 3];
+            const double dx = b[0] - a[0], dy = b[1] - a[1], dz = b[2] - a[2];
+            e2[k] = dx * dx + dy * dy + dz * dz;
+        }
+        const double lo = fmin(e2[0], fmin(e2[1], e2[2])), hi = fmax(e2[0], fmax(e2[1], e2[2]));
+        q = fmax(q, lo > 0.0 ? sqrt(hi / lo) : 1e300);
+    }
+    q = cluster_max(q);
+    if (rank == 0 && tid == 0) L.ctl->mesh_q = q;
+    if (p.trigger > 0.0 && !(q > p.trigger)) {
+        if (rank == 0 && tid == 0) L.ctl->reg_iters = 0;
+        return;
+    }
+    const double r0[3] = {M.r[0], M.r[1], M.r[2]};
+    double V0 = 0.0;
+    if (p.keep_volume) {
+        double v4[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int t = rank * nth + tid; t < M.nt; t += C * nth) {
+            double pp[3][3];
+            for (int k = 0; k < 3; ++k)
+                for (int a = 0; a < 3; ++a) pp[k][a] = M.r[3 * M.tris[3 * t + k] + a] - r0[a];
+            double bc[3];
+            cross3(pp[1], pp[2], bc);
+            v4[0] += (pp[0][0] * bc[0] + pp[0][1] * bc[1] + pp[0][2] * bc[2]) / 6.0;
+        }
+        cluster_sum4(v4);
+        V0 = v4[0];
+    }
+    for (int l = tid; l < own; l += nth)
+        for (int a = 0; a < 3; ++a) xo[3 * l + a] = xa[3 * l + a] = M.r[3 * (g0 + l) + a];
+    cluster.sync();
+    const double sg = p.plus_sign ? 1.0 : -1.0;
+    double *xq = xa, *xp = xc;
+    int it = 0;
+    bool conv = false;
+    while (it < p.max_iter) {
+        ++it;
+        // Eq. (extended laplacian smoothing) and Eq. (distanceregularization)
+        for (int l = tid; l < own; l += nth) {
+            const int g = g0 + l, b0 = M.nb_ptr[g], b1 = M.nb_ptr[g + 1], ni = b1 - b0;
+            for (int a = 0; a < 3; ++a) {
+                double s = 0.0;
+                for (int k = b0; k < b1; ++k) s += pos(xq, M.nb_idx[k], a);
+                const double v = p.alpha * xo[3 * l + a] + (1.0 - p.alpha) / ni * s;
+                xp[3 * l + a] = v;
+                xb[3 * l + a] = v - (p.alpha * xo[3 * l + a] + (1.0 - p.alpha) * xq[3 * l + a]);
+            }
+        }
+        cluster.sync();
+        // Eq. (HC_algo_full) and the exit test
+        double dmax = 0.0;
+        for (int l = tid; l < own; l += nth) {
+            const int g = g0 + l, b0 = M.nb_ptr[g], b1 = M.nb_ptr[g + 1], ni = b1 - b0;
+            double d2 = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                double s = 0.0;
+                for (int k = b0; k < b1; ++k) s += pos(xb, M.nb_idx[k], a);
+                const double v = xp[3 * l + a] - (p.gamma * xb[3 * l + a] + sg * (1.0 - p.gamma) / ni * s);
+                xp[3 * l + a] = v;
+                const double d = v - xq[3 * l + a];
+                d2 += d * d;
+            }
+            dmax = fmax(dmax, sqrt(d2));
+        }
+        dmax = cluster_max(dmax);  // its barriers also end every read of xb and xq
+        double *tmp = xq;
+        xq = xp;
+        xp = tmp;
+        if (dmax < p.tol) {
+            conv = true;
+            break;
+        }
+    }
+    // xq holds the result
+    double c[3] = {0.0, 0.0, 0.0}, f = 1.0;
+    if (p.keep_volume) {
+        double v4[4] = {0.0, 0.0, 0.0, 0.0};
+        const double s0[3] = {pos(xq, 0, 0), pos(xq, 0, 1), pos(xq, 0, 2)};
+        for (int t = rank * nth + tid; t < M.nt; t += C * nth) {
+            double pp[3][3];
+            for (int k = 0; k < 3; ++k)
+                for (int a = 0; a < 3; ++a) pp[k][a] = pos(xq, M.tris[3 * t + k], a) - s0[a];
+            double bc[3];
+            cross3(pp[1], pp[2], bc);
+            const double vt = (pp[0][0] * bc[0] + pp[0][1] * bc[1] + pp[0][2] * bc[2]) / 6.0;
+            v4[0] += vt;
+            for (int a = 0; a < 3; ++a) v4[1 + a] += vt * (pp[0][a] + pp[1][a] + pp[2][a]) / 4.0;
+        }
+        cluster_sum4(v4);
+        for (int a = 0; a < 3; ++a) c[a] = s0[a] + v4[1 + a] / v4[0];
+        f = cbrt(V0 / v4[0]);
+    }
+    double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
+    for (int l = tid; l < own; l += nth)
+        for (int a = 0; a < 3; ++a) {
+            const double v = p.keep_volume ? c[a] + f * (xq[3 * l + a] - c[a]) : xq[3 * l + a];
+            M.r[3 * (g0 + l) + a] = v;
+            mn[a] = fmin(mn[a], v);
+            mx[a] = fmax(mx[a], v);
+        }
+    for (int a = 0; a < 3; ++a) {
+        mn[a] = -cluster_max(-mn[a]);
+        mx[a] = cluster_max(mx[a]);
+    }
+    if (rank == 0 && tid == 0) {
+        write_patch(L, mn, mx, patch_buf, 1);
+        for (int a = 0; a < 3; ++a) {
+            M.part[a] = mn[a];
+            M.part[3 + a] = mx[a];
+        }
+        L.ctl->n_part = 1;
+        L.ctl->reg_iters = it;
+        L.ctl->reg_count += 1;
+        if (!conv) atomicOr(&L.ctl->err, IBL_ERRBIT_NOCONV);
+    }
+}
+
 __global__ void __launch_bounds__(256) k_patch(LbView L, MeshView M, int buf)
 {
     block_bbox_patch(L, M, M.r, M.nv, buf);
@@ -1055,7 +1230,51 @@ cudaError_t launch_interp(const LbView &L, const MeshView &M, cudaStream_t s, in
 cudaError_t launch_regularize(const LbView &L, const MeshView &M, const RegParams &p, int buf, cudaStream_t s,
                               int prio)
 {
-    return launch_p(k_regularize, dim3(1), dim3(1024), s, prio, L, M, p, buf);
+    // a cluster of one CTA per SM when the mesh fits (and the device takes
+    // the cluster size), the single-CTA kernel otherwise
+    static int cluster_ok = -1;
+    if (cluster_ok < 0) {
+        cluster_ok = 0;
+        cudaError_t e = cudaFuncSetAttribute(k_regularize_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_regularize_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(sizeof(double) * (12 * kRegPerCta + 8)));
+        if (e == cudaSuccess) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(kRegCluster);
+            cfg.blockDim = dim3(1024);
+            cfg.dynamicSmemBytes = sizeof(double) * (12 * kRegPerCta + 8);
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = kRegCluster;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            int n = 0;
+            e = cudaOccupancyMaxActiveClusters(&n, k_regularize_cluster, &cfg);
+            if (e == cudaSuccess && n > 0) cluster_ok = 1;
+        }
+        cudaGetLastError();  // a refused attribute only selects the fallback
+    }
+    if (!cluster_ok || M.nv > kRegCluster * kRegPerCta)
+        return launch_p(k_regularize, dim3(1), dim3(1024), s, prio, L, M, p, buf);
+    const int P = (M.nv + kRegCluster - 1) / kRegCluster;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kRegCluster);
+    cfg.blockDim = dim3(1024);
+    cfg.dynamicSmemBytes = sizeof(double) * (12 * (size_t)P + 8);
+    cfg.stream = s;
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = kRegCluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributePriority;
+    at[1].val.priority = prio;
+    cfg.attrs = at;
+    cfg.numAttrs = prio != 0 ? 2 : 1;
+    return cudaLaunchKernelEx(&cfg, k_regularize_cluster, L, M, p, buf, P);
 }
 
 cudaError_t launch_observables(const LbView &L, const MeshView &M, cudaStream_t s, int prio)
