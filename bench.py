@@ -321,42 +321,54 @@ PAPER_TRAJECTORY_FRAMES = 2000  # Sec. 3.2: about 2000 gradient frames per traje
 
 def measure_production(dev, steps, warmup):
     """The paper's production setup (200^3, R 19, level 5, tau_f 1.5, 496 steps
-    per frame, a shape record per frame) timed with the same graph replay:
-    step time, MLUPS and the projected time of a 2000-frame trajectory next to
-    the paper's A100 figure."""
+    per frame, a shape record per frame) timed with the same graph replay,
+    with the Sec. 3.3 mesh regularisation after every step (the paper's
+    procedure, its parameters) and without: step time, MLUPS and the
+    projected time of a 2000-frame trajectory next to the paper's A100
+    figure."""
     import torch
 
     from paper_2403_01161_gb300 import config
     from paper_2403_01161_gb300.sim import Sim
 
     w = config.production_200(steps=warmup + steps)
-    s = Sim(w.n, w.tau, w.frames, w.n_hold, precision=w.precision, device=dev)
-    s.add_icosphere(w.level, w.R, w.sigma)
-    s.set_readout(w.n_hold)
-    s.step(warmup)
-    s.sync()
-    stream = torch.cuda.current_stream(dev)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize(dev)
-    e0.record(stream)
-    s.step(steps)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    ms = e0.elapsed_time(e1)
-    st = s.status()
-    D = s.readout()["D"]
-    s.close()
-    if st != 0:
-        raise RuntimeError("device error status %d in the production run" % st)
-    traj_steps = PAPER_TRAJECTORY_FRAMES * w.n_hold
-    hours = ms / steps * 1e-3 * traj_steps / 3600.0
-    return {"metric": "hours per 2000-frame trajectory", "value": hours, "unit": "h", "higher_is_better": False,
-            "paper_a100_hours": PAPER_TRAJECTORY_HOURS, "speedup_vs_paper": PAPER_TRAJECTORY_HOURS / hours,
-            "us_per_step": 1e3 * ms / steps, "mlups": w.nodes * steps / (ms * 1e-3) / 1e6, "steps": steps,
-            "warmup": warmup, "steps_per_frame": w.n_hold, "final_D": D,
+    res = {}
+    for name, every in (("regularised", 1), ("plain", 0)):
+        s = Sim(w.n, w.tau, w.frames, w.n_hold, precision=w.precision, device=dev)
+        s.add_icosphere(w.level, w.R, w.sigma)
+        s.set_readout(w.n_hold)
+        if every:
+            s.set_regularization(every=every)
+        s.step(warmup)
+        s.sync()
+        stream = torch.cuda.current_stream(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        s.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        st = s.status()
+        D = s.readout()["D"]
+        n_reg = s.regularization_stats()[0]
+        s.close()
+        if st != 0:
+            raise RuntimeError("device error status %d in the production run" % st)
+        hours = ms / steps * 1e-3 * PAPER_TRAJECTORY_FRAMES * w.n_hold / 3600.0
+        res[name] = {"us_per_step": 1e3 * ms / steps, "mlups": w.nodes * steps / (ms * 1e-3) / 1e6,
+                     "hours_per_trajectory": hours, "speedup_vs_paper": PAPER_TRAJECTORY_HOURS / hours,
+                     "final_D": D, "regularisations": n_reg}
+    r = res["regularised"]
+    return {"metric": "hours per 2000-frame trajectory", "value": r["hours_per_trajectory"], "unit": "h",
+            "higher_is_better": False, "paper_a100_hours": PAPER_TRAJECTORY_HOURS,
+            "speedup_vs_paper": r["speedup_vs_paper"], "us_per_step": r["us_per_step"], "mlups": r["mlups"],
+            "steps": steps, "warmup": warmup, "steps_per_frame": w.n_hold, "without_regularisation": res["plain"],
+            "regularisations": r["regularisations"],
             "config": "200^3, R 19, icosphere level 5 (20480 triangles), tau_f 1.5, R/eta 0.472, Ca 0.2, "
-                      "OU gradients (seed 6), FP32 populations, shape record per frame"}
+                      "OU gradients (seed 6), FP32 populations, shape record per frame, regularisation "
+                      "(alpha 0.1, gamma 0.51, tol 0.01) after every step"}
 
 
 def measure_linear_theory(dev, n_traj=1000, n_frames=2000, Ca_values=(0.05, 0.2), seed=700):
