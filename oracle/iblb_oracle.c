@@ -21,7 +21,8 @@
  *   face Zou-He rule ......... Eq. (ZH_bulk) and its bounce-back limit Eq. (standard BB)
  *   edge rule ................ Eq. (ZH_edges) + buried links Eq. (zh-buried-links-edges)
  *   corner rule .............. Eq. (zh-buried-links-corners)
- *   wall velocity ............ Eq. (velo_facce_cubo_da_gradiente)
+ *   wall velocity ............ Eq. (velo_facce_cubo_da_gradiente); optionally
+ *                              centred on the droplet's centre of mass (Sec. 3.2)
  *   Peskin 4-point kernel .... Sec. 3.1, phi(x) after Eq. (ibm_force_d)
  *   spread / interpolate ..... Eq. (ibm_force_d) (a) and (b)
  *   advection ................ Eq. (fwd_euler)
@@ -410,6 +411,10 @@ typedef struct {
     int *nb_ptr, *nb_idx;
     int reg_every, reg_max_iter, reg_plus, reg_last_iters, reg_keep_volume;
     double reg_alpha, reg_gamma, reg_tol;
+    /* re-centring: the linear boundary field is centred on the droplet's
+     * centre of mass at the start of each step instead of the box centre */
+    int recentre;
+    double centre[3];
 } orc_sim;
 
 static size_t nid(const orc_sim *s, int x, int y, int z)
@@ -425,10 +430,21 @@ static const double *frame_of(const orc_sim *s, long t)
 }
 
 /* Eq. (velo_facce_cubo_da_gradiente): u_a = sum_b A_ab (l_b - L_b/2), with
- * L_b = n_b - 1 the side length between the two wet boundary planes. */
+ * L_b = n_b - 1 the side length between the two wet boundary planes.  With
+ * re-centring, L_b/2 is replaced by the droplet's centre of mass (the
+ * Sec. 3.2 remark that the linearisation is centred there). */
 static void wall_velocity(const orc_sim *s, const double *A, int x, int y, int z, double uw[3])
 {
-    double l[3] = {x - 0.5 * (s->n[0] - 1), y - 0.5 * (s->n[1] - 1), z - 0.5 * (s->n[2] - 1)};
+    double l[3];
+    if (s->recentre) {
+        l[0] = x - s->centre[0];
+        l[1] = y - s->centre[1];
+        l[2] = z - s->centre[2];
+    } else {
+        l[0] = x - 0.5 * (s->n[0] - 1);
+        l[1] = y - 0.5 * (s->n[1] - 1);
+        l[2] = z - 0.5 * (s->n[2] - 1);
+    }
     for (int a = 0; a < 3; ++a) uw[a] = A[3 * a] * l[0] + A[3 * a + 1] * l[1] + A[3 * a + 2] * l[2];
 }
 
@@ -500,6 +516,15 @@ void orc_sim_set_regularization(orc_sim *s, double alpha, double gamma, double t
 /* keep = 1: every regularisation is followed by orc_restore_volume to the
  * volume enclosed before it (an option beyond Sec. 3.3). */
 void orc_sim_set_regularization_volume(orc_sim *s, int keep) { s->reg_keep_volume = keep; }
+
+/* Re-centring on (1) or off (0); needs a droplet mesh to take effect. */
+void orc_sim_set_recentring(orc_sim *s, int on) { s->recentre = on; }
+
+/* Centre of the linear boundary field used by the last step. */
+void orc_sim_get_centre(const orc_sim *s, double c[3])
+{
+    for (int a = 0; a < 3; ++a) c[a] = s->centre[a];
+}
 
 /* Stencil of the 4-point kernel along axis a around coordinate ra: the four
  * nodes floor(ra)-1 .. floor(ra)+2 with their weights.  On a Zou-He axis all
@@ -630,12 +655,26 @@ static void lattice_update(orc_sim *s)
     s->fn = t;
 }
 
+/* Centre of the boundary field for the step about to run: the droplet's
+ * centre of mass (the volume centroid of the closed mesh) at r_t with
+ * re-centring, else the box centre. */
+static void step_centre(orc_sim *s)
+{
+    if (s->recentre && s->nv > 0) {
+        double V;
+        orc_enclosed_volume(s->nv, s->r, s->nt, s->tri, &V, s->centre);
+    } else {
+        for (int a = 0; a < 3; ++a) s->centre[a] = 0.5 * (s->n[a] - 1);
+    }
+}
+
 /* One IBLB step in the order: forces + spread at r_t, lattice update with
  * F_t, interpolation of u_t at r_t and advection, regularisation when
  * scheduled.  Returns the sticky error bits. */
 int orc_sim_step(orc_sim *s, long nsteps)
 {
     for (long k = 0; k < nsteps; ++k) {
+        step_centre(s);
         if (s->nv > 0) spread(s);
         else memset(s->F, 0, sizeof(double) * 3 * s->nn);
         lattice_update(s);
@@ -662,6 +701,7 @@ int orc_sim_step(orc_sim *s, long nsteps)
 int orc_sim_step_body_force(orc_sim *s, long nsteps, const double g[3])
 {
     for (long k = 0; k < nsteps; ++k) {
+        step_centre(s);
         if (s->nv > 0) spread(s);
         else memset(s->F, 0, sizeof(double) * 3 * s->nn);
         for (int z = 0; z < s->n[2]; ++z)

@@ -69,6 +69,8 @@ def lib():
             L.orc_enclosed_volume.argtypes = [ctypes.c_int, _D, ctypes.c_int, _I, _D, _D]
             L.orc_restore_volume.argtypes = [ctypes.c_int, _D, ctypes.c_int, _I, ctypes.c_double]
             L.orc_sim_set_regularization_volume.argtypes = [ctypes.c_void_p, ctypes.c_int]
+            L.orc_sim_set_recentring.argtypes = [ctypes.c_void_p, ctypes.c_int]
+            L.orc_sim_get_centre.argtypes = [ctypes.c_void_p, _D]
             L.orc_sim_create.argtypes = [_I, _I, ctypes.c_double, ctypes.c_int, _D, ctypes.c_int,
                                          ctypes.c_int]
             L.orc_sim_create.restype = ctypes.c_void_p
@@ -371,6 +373,18 @@ class OracleSim:
         self.L.orc_sim_set_regularization(self.h, alpha, gamma, tol, max_iter, every,
                                           1 if plus_sign else 0)
         self.L.orc_sim_set_regularization_volume(self.h, 1 if keep_volume else 0)
+
+    def set_recentring(self, on=True):
+        """Centre the linear boundary field of each step on the droplet's
+        centre of mass (volume centroid at the start of the step) instead of
+        the box centre (Sec. 3.2)."""
+        self.L.orc_sim_set_recentring(self.h, 1 if on else 0)
+
+    def centre(self):
+        """Centre of the boundary field used by the last step."""
+        c = np.zeros(3)
+        self.L.orc_sim_get_centre(self.h, _dp(c))
+        return c
 
     def step(self, n=1, body_force=None) -> int:
         if body_force is None:

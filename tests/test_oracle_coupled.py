@@ -81,3 +81,76 @@ def test_taylor_small_deformation(golden):
         assert abs(ob["beta"] - golden["beta_steady_shear"]["value"]) < 0.01
         ex.append(ratio - 1)
     assert ex[1] < ex[0] * (4.0 / 5.0) ** 1.5
+
+
+def _recentring_case(centre, recentre, N=20):
+    A = np.array([[0.0, 2e-3, 0.0], [1e-3, 1e-3, 0.0], [0.0, 0.0, -1e-3]])  # traceless
+    s = O.OracleSim((N, N, N), 1.0, A[None], 10 ** 9)
+    r, t = O.icosphere(2, 3.5, centre)
+    s.set_mesh(r, t, 0.01)
+    if recentre:
+        s.set_recentring(True)
+    return s, A, r, t
+
+
+def _face_nodes(N):
+    """(axis, side, index arrays) of the face nodes that are on no edge."""
+    k = np.arange(1, N - 1)
+    for a in range(3):
+        for side in (0, N - 1):
+            yield a, side, k
+
+
+def test_recentring_imposes_the_field_about_the_centre_of_mass():
+    """Sec. 3.2 (boundary conditions): centred on the droplet's centre of mass,
+    the Zou-He faces impose u = A (l - c), c the volume centroid of the
+    mesh at the start of the step.  Read back from the lattice moments of the
+    step at every face node off the edges; the default run imposes
+    A (l - (n - 1)/2) instead, which differs by A (c - (n - 1)/2)."""
+    N = 20
+    cen = (8.3, 10.1, 9.4)
+    for recentre in (True, False):
+        s, A, r, t = _recentring_case(cen, recentre, N)
+        c = O.enclosed_volume(r, t)[1] if recentre else np.full(3, 0.5 * (N - 1))
+        assert s.step(1) == 0
+        assert np.abs(s.centre() - c).max() < 1e-14
+        _, u, _ = s.fields()  # (3, z, y, x)
+        worst = 0.0
+        for a, side, k in _face_nodes(N):
+            J, K = np.meshgrid(k, k, indexing="ij")
+            l = np.zeros((3,) + J.shape)
+            l[a] = side
+            l[(a + 1) % 3] = J
+            l[(a + 2) % 3] = K
+            want = np.einsum("ab,bjk->ajk", A, l - c[:, None, None])
+            idx = [None, None, None]  # (x, y, z) node index arrays
+            idx[a] = np.full(J.shape, side)
+            idx[(a + 1) % 3] = J
+            idx[(a + 2) % 3] = K
+            got = u[:, idx[2], idx[1], idx[0]]
+            worst = max(worst, np.abs(got - want).max())
+        assert worst < 1e-14, (recentre, worst)
+        s.close()
+    # the centroid of this off-centre droplet is visibly away from the box centre
+    assert np.abs(c - O.enclosed_volume(r, t)[1]).max() > 0.5
+
+
+def test_recentring_follows_the_droplet_each_step():
+    """The centre used by step t + 1 is the centroid of the positions that
+    step t left, and a droplet centred in the box (its centroid is the box
+    centre up to rounding) gives the default run."""
+    s, A, r, t = _recentring_case((8.3, 10.1, 9.4), True)
+    s.step(3)
+    r3, _ = s.mesh()
+    s.step(1)
+    assert np.abs(s.centre() - O.enclosed_volume(r3, t)[1]).max() < 1e-15 * 20
+    s.close()
+    c0 = (9.5, 9.5, 9.5)
+    a, _, _, _ = _recentring_case(c0, True)
+    b, _, _, _ = _recentring_case(c0, False)
+    a.step(10)
+    b.step(10)
+    assert np.abs(a.mesh()[0] - b.mesh()[0]).max() < 1e-12
+    assert np.abs(a.fields()[1] - b.fields()[1]).max() < 1e-13
+    a.close()
+    b.close()
