@@ -180,6 +180,18 @@ int ibl_set_regularization_trigger(ibl_mesh *m, double max_edge_ratio);
  * adds up over long runs).  Default 0.  Synchronises the lattice's stream. */
 int ibl_set_regularization_keep_volume(ibl_mesh *m, int keep);
 
+/* Re-centring of the boundary field (Sec. 3.2 says the linearisation of the
+ * velocity field is centred on the droplet's centre of mass, while its
+ * Eq. (velo_facce_cubo_da_gradiente) centres it on the box, L/2).  on != 0:
+ * every step imposes u = A (l - c) on the Zou-He faces, c the centre of
+ * mass (volume centroid) of the region the mesh encloses, measured on the
+ * device from the positions at the start of the step; 0 (the default): the
+ * box centre.  The adjoint (ibl_adjoint) refuses a lattice with re-centring
+ * on (IBL_EINVAL); destroying the mesh switches it off; an ensemble takes
+ * the setting its members have when it is created.  IBL_EINVAL if the mesh
+ * is not attached.  Synchronises the lattice's stream. */
+int ibl_set_recentring(ibl_mesh *m, int on);
+
 /* Synchronising: *count = regularisations performed so far (triggered
  * scheduled ones and ibl_regularize_now calls), *mesh_quality = q measured
  * at the latest regularisation check (0 before the first).  Either pointer

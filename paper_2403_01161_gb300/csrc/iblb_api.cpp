@@ -71,7 +71,7 @@ bool lb_layout(const ibl_lb_params *p, int n_frames, Layout &L)
 
 struct MeshLayout {
     size_t r = 0, fn = 0, tris = 0, n2t_ptr = 0, n2t = 0, nb_ptr = 0, nb_idx = 0, s0 = 0, s1 = 0, s2 = 0,
-           part = 0, obs_part = 0, ring = 0, total = 0;
+           part = 0, cpart = 0, obs_part = 0, ring = 0, total = 0;
 };
 
 bool mesh_layout(int nv, int nt, MeshLayout &L)
@@ -94,6 +94,7 @@ bool mesh_layout(int nv, int nt, MeshLayout &L)
     L.s1 = take(sizeof(double) * 3 * nv);
     L.s2 = take(sizeof(double) * 3 * nv);
     L.part = take(sizeof(double) * 6 * (((size_t)nv + 7) / 8 + 1));  // one row per interpolation block
+    L.cpart = take(sizeof(double) * 4 * iblb::kCentreBlocks);
     L.obs_part = take(sizeof(double) * 11 * iblb::kObsBlocksMax);
     L.ring = take(sizeof(ibl_observables) * iblb::kRingCap);
     L.total = off;
@@ -162,10 +163,11 @@ struct ibl_lb {
     int hi_prio = 0;  // priority of the helper-stream kernels
     cudaEvent_t evNear[2] = {nullptr, nullptr}, evFar[2] = {nullptr, nullptr};
     cudaEvent_t evFork = nullptr, evJoin = nullptr;
+    cudaEvent_t evCentre = nullptr;  // re-centring: the force kernel of the step has written the centre
     // a separate set for graph capture (events recorded inside a capture
     // cannot be waited on by eager launches)
     cudaEvent_t cNear[2] = {nullptr, nullptr}, cFar[2] = {nullptr, nullptr};
-    cudaEvent_t cFork = nullptr, cJoin = nullptr;
+    cudaEvent_t cFork = nullptr, cJoin = nullptr, cCentre = nullptr;
     ~ibl_lb()
     {
         if (gexec) cudaGraphExecDestroy(gexec);
@@ -182,6 +184,8 @@ struct ibl_lb {
         if (evJoin) cudaEventDestroy(evJoin);
         if (cFork) cudaEventDestroy(cFork);
         if (cJoin) cudaEventDestroy(cJoin);
+        if (evCentre) cudaEventDestroy(evCentre);
+        if (cCentre) cudaEventDestroy(cCentre);
     }
 };
 
@@ -260,8 +264,16 @@ int one_step(ibl_lb *lb, bool record, cudaStream_t sL, cudaStream_t sH)
     }
     // helper stream: forces + spread (and the next step's patch), then the
     // patch nodes once the previous outside update has finished
+    // with re-centring, first the step's centre (from the positions the
+    // previous step left), which the outside update reads on its faces
+    cudaEvent_t evCentre = lb->capturing ? lb->cCentre : lb->evCentre;
+    e = cudaSuccess;
+    if (lb->v.recentre) {
+        e = iblb::launch_centre(lb->v, m->v, pbuf, sH, lb->hi_prio);
+        if (e == cudaSuccess) e = cudaEventRecord(evCentre, sH);
+    }
     const int ps = prof_begin(lb, PROF_SPREAD, sH);
-    e = iblb::launch_spread(lb->v, m->v, pnext, sH, lb->hi_prio);
+    if (e == cudaSuccess) e = iblb::launch_spread(lb->v, m->v, pnext, sH, lb->hi_prio);
     prof_end(lb, ps, sH);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(sH, evFar[par ^ 1], 0);
     if (e == cudaSuccess) e = iblb::launch_near(lb->v, odd, record, pbuf, sH, lb->hi_prio);
@@ -270,6 +282,7 @@ int one_step(ibl_lb *lb, bool record, cudaStream_t sL, cudaStream_t sH)
     // bound stream: the outside nodes once the previous patch update (and
     // regularisation) has finished; then the step counter
     e = cudaStreamWaitEvent(sL, evNear[par ^ 1], 0);
+    if (e == cudaSuccess && lb->v.recentre) e = cudaStreamWaitEvent(sL, evCentre, 0);
     const int pl = prof_begin(lb, PROF_LB, sL);
     if (e == cudaSuccess) e = iblb::launch_lattice(lb->v, odd, record, iblb::LAUNCH_FAR, pbuf, sL);
     prof_end(lb, pl, sL);
@@ -475,6 +488,7 @@ int mesh_attach(ibl_lb *lb, int nv, const double *r, int nt, const int *tri_in, 
     m->v.s1 = reinterpret_cast<double *>(w + L.s1);
     m->v.s2 = reinterpret_cast<double *>(w + L.s2);
     m->v.part = reinterpret_cast<double *>(w + L.part);
+    m->v.cpart = reinterpret_cast<double *>(w + L.cpart);
     m->v.obs_part = reinterpret_cast<double *>(w + L.obs_part);
     m->v.ring = reinterpret_cast<ibl_observables *>(w + L.ring);
     m->v.ring_cap = iblb::kRingCap;
@@ -555,6 +569,8 @@ int ensure_streams(ibl_lb *lb)
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&lb->evJoin, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&lb->cFork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&lb->cJoin, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&lb->evCentre, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&lb->cCentre, cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_fail(e, "stream/event creation");
     return IBL_OK;
 }
@@ -1010,8 +1026,18 @@ void ibl_mesh_destroy(ibl_mesh *m)
         cudaStreamSynchronize(m->lb->stream);
         drop_graph(m->lb);
         m->lb->mesh = nullptr;
+        m->lb->v.recentre = 0;  // the centre came from this droplet
     }
     delete m;
+}
+
+int ibl_set_recentring(ibl_mesh *m, int on)
+{
+    if (!m || !m->lb) return fail(IBL_EINVAL, "the mesh is not attached to a lattice");
+    cudaStreamSynchronize(m->lb->stream);
+    m->lb->v.recentre = on ? 1 : 0;
+    drop_graph(m->lb);  // captured chunks hold the lattice view by value, and the step's dependencies change
+    return IBL_OK;
 }
 
 int ibl_set_regularization(ibl_mesh *m, double alpha, double gamma, double tol, int max_iter, int every, int plus_sign)
@@ -1504,6 +1530,7 @@ int ibl_adjoint(ibl_lb *lb, long long n_steps, int K, void *workspace, size_t by
     if (!adj_layout(lb, m, n_steps, K, A)) return fail(IBL_EINVAL, "n_steps and K must be >= 1");
     if (lb->host_step != 0) return fail(IBL_EINVAL, "the adjoint starts from step 0");
     if (m->reg_every != 0) return fail(IBL_EINVAL, "the adjoint needs the regularisation switched off");
+    if (lb->v.recentre) return fail(IBL_EINVAL, "the adjoint does not differentiate the re-centring");
     if (!workspace || bytes < A.total) return fail(IBL_ENOMEM, "adjoint workspace too small");
     if (((uintptr_t)workspace & 255) != 0) return fail(IBL_EINVAL, "workspace must be 256-byte aligned");
     int st = ensure_streams(lb);

@@ -26,6 +26,9 @@ struct alignas(128) Ctl {
     int frame;                   // frame index applied by the next step
     int reg_count;               // regularisations performed (scheduled checks that triggered)
     double mesh_q;               // mesh quality at the last scheduled check: max over triangles of longest/shortest edge
+    unsigned int cen_ticket;     // last-block ticket of the force kernel's centre-of-mass reduction
+    int pad0;
+    double centre[3][4];         // re-centring: centre of the boundary field of step t in buffer t % 3
     int patch_lo[3][4];          // droplet patch of step t in buffer t % 3: lower corner (inside the box)
     int patch_ext[3][4];         // extent (hi - lo), -1 = empty
 };
@@ -48,6 +51,7 @@ struct LbView {
     const void *frames_t;  // the frames in the storage precision
     int n_frames;
     int n_hold;
+    int recentre;       // 1: the boundary field is centred on the droplet's centre of mass (ctl->centre)
     Ctl *ctl;
 };
 
@@ -63,6 +67,7 @@ struct MeshView {
     const int *nb_idx;  // [3 nt]
     double *s0, *s1, *s2;  // regularisation scratch, [nv][3] each
     double *part;          // per-block bounding-box partials of the interpolation kernel, [blocks][6]
+    double *cpart;         // re-centring: per-block volume and first moment, [kCentreBlocks][4]
     double *obs_part;      // per-block partial sums of the shape-record kernel, [kObsBlocksMax][11]
     ibl_observables *ring;
     int ring_cap;
@@ -124,6 +129,9 @@ cudaError_t launch_advance(const LbView &L, cudaStream_t s);
 cudaError_t launch_convert_frames(const LbView &L, int k0, int k1, cudaStream_t s);
 cudaError_t launch_spread(const LbView &L, const MeshView &M, int next_buf, cudaStream_t s, int prio = 0);
 cudaError_t launch_interp(const LbView &L, const MeshView &M, cudaStream_t s, int prio = 0);
+// re-centring: the droplet's centre of mass at the current positions into ctl->centre[buf]
+constexpr int kCentreBlocks = 16;
+cudaError_t launch_centre(const LbView &L, const MeshView &M, int buf, cudaStream_t s, int prio = 0);
 cudaError_t launch_regularize(const LbView &L, const MeshView &M, const RegParams &p, int buf, cudaStream_t s,
                               int prio = 0);
 cudaError_t launch_observables(const LbView &L, const MeshView &M, cudaStream_t s, int prio = 0);

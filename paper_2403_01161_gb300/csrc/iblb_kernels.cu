@@ -226,9 +226,21 @@ __device__ __forceinline__ bool lattice_node(const LbView &L, const int x, const
         }
 
         if (sx | sy | sz) {
-            // Eq. (velo_facce_cubo_da_gradiente) in the storage precision
+            // Eq. (velo_facce_cubo_da_gradiente) in the storage precision,
+            // about the box centre or, with re-centring, about the droplet's
+            // centre of mass at the start of the step (the offset in FP64)
             const T *A = static_cast<const T *>(L.frames_t) + 9 * L.ctl->frame;
-            const T lx = T(x) - T(0.5) * T(nx - 1), ly = T(y) - T(0.5) * T(ny - 1), lz = T(z) - T(0.5) * T(nz - 1);
+            T lx, ly, lz;
+            if (L.recentre) {
+                const double *c = L.ctl->centre[pbuf];
+                lx = T(double(x) - c[0]);
+                ly = T(double(y) - c[1]);
+                lz = T(double(z) - c[2]);
+            } else {
+                lx = T(x) - T(0.5) * T(nx - 1);
+                ly = T(y) - T(0.5) * T(ny - 1);
+                lz = T(z) - T(0.5) * T(nz - 1);
+            }
             const T uw[3] = {A[0] * lx + A[1] * ly + A[2] * lz, A[3] * lx + A[4] * ly + A[5] * lz,
                              A[6] * lx + A[7] * ly + A[8] * lz};
             bc_dispatch<T>(g, uw, L.rule, (sx + 1) + 3 * (sy + 1) + 9 * (sz + 1));
@@ -561,6 +573,65 @@ template <typename T>
 __global__ void __launch_bounds__(128) k_spread(LbView L, MeshView M, int next_buf)
 {
     spread_body<T>(L, M, blockIdx.x, next_buf);
+}
+
+// Re-centring (Sec. 3.2: the linearisation is centred on the droplet's
+// centre of mass).  kCentreBlocks blocks per droplet sum the volume V and
+// first moment m of the region the mesh encloses over the signed tetrahedra
+// (box centre, a, b, c) of the triangles, block b taking triangles b, b +
+// kCentreBlocks, ... thread by thread.  Each block writes its sums to
+// M.cpart; the last block to finish adds the rows in block order
+// (deterministic) and stores the step's centre, box centre + m / V, in
+// buffer `buf`.  Runs after the interpolation of the previous step and
+// before any lattice update of this step.
+constexpr int kCentreThreads = 128;
+
+__device__ __forceinline__ void centre_of_mass(const LbView &L, const MeshView &M, const int blk, const int buf)
+{
+    __shared__ double sh[kCentreThreads / 32][4];
+    __shared__ int last;
+    const double ref[3] = {0.5 * (L.n[0] - 1), 0.5 * (L.n[1] - 1), 0.5 * (L.n[2] - 1)};
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int t = blk * kCentreThreads + (int)threadIdx.x; t < M.nt; t += kCentreBlocks * kCentreThreads) {
+        double p[3][3];
+        for (int c = 0; c < 3; ++c) {
+            const int q = M.tris[3 * t + c];
+            for (int a = 0; a < 3; ++a) p[c][a] = M.r[3 * q + a] - ref[a];
+        }
+        double bc[3];
+        cross3(p[1], p[2], bc);
+        const double vt = (p[0][0] * bc[0] + p[0][1] * bc[1] + p[0][2] * bc[2]) / 6.0;
+        v[0] += vt;
+        for (int a = 0; a < 3; ++a) v[1 + a] += vt * (p[0][a] + p[1][a] + p[2][a]) / 4.0;
+    }
+    block_sum<4>(v, sh);
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 4; ++k) M.cpart[4 * blk + k] = v[k];
+        __threadfence();
+        last = atomicAdd(&L.ctl->cen_ticket, 1u) == (unsigned)(kCentreBlocks - 1) ? 1 : 0;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x == 0) {
+        double w[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int b = 0; b < kCentreBlocks; ++b)
+            for (int k = 0; k < 4; ++k) w[k] += __ldcg(M.cpart + 4 * b + k);
+        for (int a = 0; a < 3; ++a) L.ctl->centre[buf][a] = ref[a] + w[1 + a] / w[0];
+        L.ctl->cen_ticket = 0u;
+    }
+}
+
+__global__ void __launch_bounds__(kCentreThreads) k_centre(LbView L, MeshView M, int buf)
+{
+    centre_of_mass(L, M, blockIdx.x, buf);
+}
+
+// Ensemble version: blockIdx.y is the member within the group.
+__global__ void __launch_bounds__(kCentreThreads)
+    k_centre_batched(const __grid_constant__ LbGroup LG, const __grid_constant__ MeshGroup MG, int buf)
+{
+    centre_of_mass(LG.v[blockIdx.y], MG.v[blockIdx.y], blockIdx.x, buf);
 }
 
 template <typename T>
@@ -1220,6 +1291,11 @@ cudaError_t launch_spread(const LbView &L, const MeshView &M, int next_buf, cuda
     return launch_p(k_spread<float>, g, b, s, prio, L, M, next_buf);
 }
 
+cudaError_t launch_centre(const LbView &L, const MeshView &M, int buf, cudaStream_t s, int prio)
+{
+    return launch_p(k_centre, dim3(kCentreBlocks), dim3(kCentreThreads), s, prio, L, M, buf);
+}
+
 cudaError_t launch_interp(const LbView &L, const MeshView &M, cudaStream_t s, int prio)
 {
     const dim3 g(blocks_for((long long)M.nv * kLanesPerNode, kIbThreads)), b(kIbThreads);
@@ -1307,6 +1383,10 @@ cudaError_t launch_ensemble_step(const EnsembleView &E, long long step, cudaStre
         const int nb0 = E.node_start[m0], nb = E.node_start[m1] - nb0;
         const int lb0 = E.lat_start[m0], lbn = E.lat_start[m1] - lb0;
         const int nxt = (int)((step + 1) % 3);  // patch buffer of the next step
+        bool recentre = false;
+        for (int k = m0; k < m1; ++k) recentre = recentre || E.lv[k].recentre != 0;
+        if (recentre)
+            k_centre_batched<<<dim3(kCentreBlocks, m1 - m0), kCentreThreads, 0, s>>>(lg, mg, pbuf);
         if (E.precision == IBL_FP64) {
             k_spread_batched<double>
                 <<<nb, kIbThreads, 0, s>>>(lg, mg, m0, nb0, E.node_member, E.node_start_d, nxt);

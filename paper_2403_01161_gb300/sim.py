@@ -154,6 +154,12 @@ class Sim:
         enclosed before (about its volume centroid)."""
         L.check(self.lib.ibl_set_regularization_keep_volume(self.mesh_h, 1 if keep else 0))
 
+    def set_recentring(self, on: bool = True):
+        """Centre the linear boundary field of every step on the droplet's
+        centre of mass (volume centroid at the start of the step) instead of
+        the box centre (Sec. 3.2)."""
+        L.check(self.lib.ibl_set_recentring(self.mesh_h, 1 if on else 0))
+
     def regularization_stats(self):
         """(regularisations performed, mesh quality at the latest check)."""
         n = ctypes.c_int()
