@@ -71,7 +71,7 @@ bool lb_layout(const ibl_lb_params *p, int n_frames, Layout &L)
 
 struct MeshLayout {
     size_t r = 0, fn = 0, tris = 0, n2t_ptr = 0, n2t = 0, nb_ptr = 0, nb_idx = 0, s0 = 0, s1 = 0, s2 = 0,
-           part = 0, cpart = 0, obs_part = 0, ring = 0, total = 0;
+           tm = 0, part = 0, cpart = 0, obs_part = 0, ring = 0, total = 0;
 };
 
 bool mesh_layout(int nv, int nt, MeshLayout &L)
@@ -93,6 +93,7 @@ bool mesh_layout(int nv, int nt, MeshLayout &L)
     L.s0 = take(sizeof(double) * 3 * nv);
     L.s1 = take(sizeof(double) * 3 * nv);
     L.s2 = take(sizeof(double) * 3 * nv);
+    L.tm = take(sizeof(double) * 3 * nt);
     L.part = take(sizeof(double) * 6 * (((size_t)nv + 7) / 8 + 1));  // one row per interpolation block
     L.cpart = take(sizeof(double) * 4 * iblb::kCentreBlocks);
     L.obs_part = take(sizeof(double) * 11 * iblb::kObsBlocksMax);
@@ -487,6 +488,7 @@ int mesh_attach(ibl_lb *lb, int nv, const double *r, int nt, const int *tri_in, 
     m->v.s0 = reinterpret_cast<double *>(w + L.s0);
     m->v.s1 = reinterpret_cast<double *>(w + L.s1);
     m->v.s2 = reinterpret_cast<double *>(w + L.s2);
+    m->v.tm = reinterpret_cast<double *>(w + L.tm);
     m->v.part = reinterpret_cast<double *>(w + L.part);
     m->v.cpart = reinterpret_cast<double *>(w + L.cpart);
     m->v.obs_part = reinterpret_cast<double *>(w + L.obs_part);

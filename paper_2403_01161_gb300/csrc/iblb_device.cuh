@@ -201,6 +201,36 @@ __device__ __forceinline__ void tri_force(const MeshView &M, const int t, const 
     cross3(m, dd, g);
 }
 
+// The same force in two stages, so that the FP64 normal of each triangle is
+// evaluated once per step instead of once per corner: tri_moment gives m_t
+// = -sigma N_t / (2 |N_t|) (the m of tri_force<double>, bit for bit), and
+// tri_force_m the force on corner `slot` from a stored m_t.
+__device__ __forceinline__ void tri_moment(const MeshView &M, const int t, double m[3])
+{
+    double x[3][3];
+    for (int k = 0; k < 3; ++k) {
+        const int v = M.tris[3 * t + k];
+        for (int a = 0; a < 3; ++a) x[k][a] = M.r[3 * v + a];
+    }
+    double e1[3], e2[3], N[3];
+    for (int a = 0; a < 3; ++a) {
+        e1[a] = x[1][a] - x[0][a];
+        e2[a] = x[2][a] - x[0][a];
+    }
+    cross3(e1, e2, N);
+    const double s = -0.5 * M.sigma * rsqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
+    for (int a = 0; a < 3; ++a) m[a] = s * N[a];
+}
+
+__device__ __forceinline__ void tri_force_m(const MeshView &M, const int t, const int slot, const double m[3],
+                                            double g[3])
+{
+    const int kp = slot == 2 ? 0 : slot + 1, km = slot == 0 ? 2 : slot - 1;
+    const int vp = M.tris[3 * t + kp], vm = M.tris[3 * t + km];
+    const double dd[3] = {M.r[3 * vm] - M.r[3 * vp], M.r[3 * vm + 1] - M.r[3 * vp + 1], M.r[3 * vm + 2] - M.r[3 * vp + 2]};
+    cross3(m, dd, g);
+}
+
 // ---------------------------------------------------------------------------
 // Single-block reductions.
 template <int K>

@@ -66,6 +66,7 @@ struct MeshView {
     const int *nb_ptr;  // [nv+1]
     const int *nb_idx;  // [3 nt]
     double *s0, *s1, *s2;  // regularisation scratch, [nv][3] each
+    double *tm;            // [nt][3] m_t = -sigma N_t / (2 |N_t|) at the current positions (triangle kernel, read by the force kernel)
     double *part;          // per-block bounding-box partials of the interpolation kernel, [blocks][6]
     double *cpart;         // re-centring: per-block volume and first moment, [kCentreBlocks][4]
     double *obs_part;      // per-block partial sums of the shape-record kernel, [kObsBlocksMax][11]

@@ -533,8 +533,9 @@ __device__ __forceinline__ void spread_body(const LbView &L, const MeshView &M, 
     for (int k = M.n2t_ptr[i] + lane; k < M.n2t_ptr[i + 1]; k += kLanesPerNode) {
         const int e = M.n2t[k];
         const int t = e / 3;
+        const double m[3] = {M.tm[3 * t], M.tm[3 * t + 1], M.tm[3 * t + 2]};
         double g[3];
-        tri_force<double>(M, t, e - 3 * t, g);
+        tri_force_m(M, t, e - 3 * t, m, g);
         for (int a = 0; a < 3; ++a) F[a] += g[a];
     }
     for (int o = kLanesPerNode / 2; o > 0; o >>= 1)
@@ -567,6 +568,28 @@ __device__ __forceinline__ void spread_body(const LbView &L, const MeshView &M, 
         atomicAdd(force + nodes + id, Fy * dl);
         atomicAdd(force + 2 * nodes + id, Fz * dl);
     }
+}
+
+// m_t of every triangle at the current positions (Eq. (pi_drop)), once per
+// step, for the force kernel that follows on the same stream.
+__global__ void __launch_bounds__(128) k_tri_moment(MeshView M)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= M.nt) return;
+    double m[3];
+    tri_moment(M, t, m);
+    for (int a = 0; a < 3; ++a) M.tm[3 * t + a] = m[a];
+}
+
+// Ensemble version: blockIdx.y is the member within the group.
+__global__ void __launch_bounds__(128) k_tri_moment_batched(const __grid_constant__ MeshGroup MG)
+{
+    const MeshView &M = MG.v[blockIdx.y];
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= M.nt) return;
+    double m[3];
+    tri_moment(M, t, m);
+    for (int a = 0; a < 3; ++a) M.tm[3 * t + a] = m[a];
 }
 
 template <typename T>
@@ -1286,6 +1309,8 @@ cudaError_t launch_advance(const LbView &L, cudaStream_t s)
 
 cudaError_t launch_spread(const LbView &L, const MeshView &M, int next_buf, cudaStream_t s, int prio)
 {
+    cudaError_t e = launch_p(k_tri_moment, dim3(blocks_for(M.nt, 128)), dim3(128), s, prio, M);
+    if (e != cudaSuccess) return e;
     const dim3 g(blocks_for((long long)M.nv * kLanesPerNode, kIbThreads)), b(kIbThreads);
     if (L.precision == IBL_FP64) return launch_p(k_spread<double>, g, b, s, prio, L, M, next_buf);
     return launch_p(k_spread<float>, g, b, s, prio, L, M, next_buf);
@@ -1387,6 +1412,9 @@ cudaError_t launch_ensemble_step(const EnsembleView &E, long long step, cudaStre
         for (int k = m0; k < m1; ++k) recentre = recentre || E.lv[k].recentre != 0;
         if (recentre)
             k_centre_batched<<<dim3(kCentreBlocks, m1 - m0), kCentreThreads, 0, s>>>(lg, mg, pbuf);
+        int nt_max = 0;
+        for (int k = m0; k < m1; ++k) nt_max = E.mv[k].nt > nt_max ? E.mv[k].nt : nt_max;
+        k_tri_moment_batched<<<dim3((nt_max + 127) / 128, m1 - m0), 128, 0, s>>>(mg);
         if (E.precision == IBL_FP64) {
             k_spread_batched<double>
                 <<<nb, kIbThreads, 0, s>>>(lg, mg, m0, nb0, E.node_member, E.node_start_d, nxt);
