@@ -107,18 +107,65 @@ constexpr int kIbThreads = 128;    // threads per block of the node-group kernel
 // origin base_a = floor(r_a) - 1 and the exact fraction r_a - floor(r_a) of
 // axis a, and every lane receives all three by shuffles.  The offset of
 // stencil point k is then frac + (1 - k), the correctly rounded r - (base+k).
+// L2 residency of the droplet-side working set.  Every step the outside
+// lattice update streams the whole population array (about twice the L2 of
+// a 128^3 box) through L2, which would evict the mesh arrays, the patch's
+// populations and its force and velocity between two uses, so that each
+// dependent access of the droplet chain would go to DRAM under full load.
+// Accesses through an L2Keep carry an evict_last policy (PTX createpolicy
+// and the .L2::cache_hint qualifier), which keeps those lines resident.
+struct L2Keep {
+    unsigned long long pol;
+    __device__ __forceinline__ L2Keep() { asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol)); }
+    __device__ __forceinline__ double ld(const double *a) const
+    {
+        double v;
+        asm volatile("ld.global.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(a), "l"(pol) : "memory");
+        return v;
+    }
+    __device__ __forceinline__ float ld(const float *a) const
+    {
+        float v;
+        asm volatile("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(a), "l"(pol) : "memory");
+        return v;
+    }
+    __device__ __forceinline__ int ld(const int *a) const
+    {
+        int v;
+        asm volatile("ld.global.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(pol) : "memory");
+        return v;
+    }
+    __device__ __forceinline__ void st(double *a, double v) const
+    {
+        asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(a), "d"(v), "l"(pol) : "memory");
+    }
+    __device__ __forceinline__ void st(float *a, float v) const
+    {
+        asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(a), "f"(v), "l"(pol) : "memory");
+    }
+    __device__ __forceinline__ void red_add(float *a, float v) const
+    {
+        asm volatile("red.global.add.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(a), "f"(v), "l"(pol) : "memory");
+    }
+    __device__ __forceinline__ void red_add(double *a, double v) const
+    {
+        asm volatile("red.global.add.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(a), "d"(v), "l"(pol) : "memory");
+    }
+};
+
 struct NodeStencil {
     int base[3];
     double frac[3];
     bool ok;
 };
-__device__ __forceinline__ NodeStencil node_stencil(const LbView &L, const double *r, int lane)
+__device__ __forceinline__ NodeStencil node_stencil(const LbView &L, const double *r, int lane,
+                                                    const L2Keep *keep = nullptr)
 {
     double ra = 0.0, fr = 0.0;
     int base = 0;
     bool ok = true;
     if (lane < 3) {
-        ra = r[lane];
+        ra = keep ? keep->ld(r + lane) : r[lane];
         // select by value: indexing the parameter arrays with a runtime lane
         // would copy the kernel parameters to local memory
         const int na = lane == 0 ? L.n[0] : (lane == 1 ? L.n[1] : L.n[2]);
@@ -205,12 +252,12 @@ __device__ __forceinline__ void tri_force(const MeshView &M, const int t, const 
 // evaluated once per step instead of once per corner: tri_moment gives m_t
 // = -sigma N_t / (2 |N_t|) (the m of tri_force<double>, bit for bit), and
 // tri_force_m the force on corner `slot` from a stored m_t.
-__device__ __forceinline__ void tri_moment(const MeshView &M, const int t, double m[3])
+__device__ __forceinline__ void tri_moment(const MeshView &M, const int t, double m[3], const L2Keep &K)
 {
     double x[3][3];
     for (int k = 0; k < 3; ++k) {
-        const int v = M.tris[3 * t + k];
-        for (int a = 0; a < 3; ++a) x[k][a] = M.r[3 * v + a];
+        const int v = K.ld(M.tris + 3 * t + k);
+        for (int a = 0; a < 3; ++a) x[k][a] = K.ld(M.r + 3 * v + a);
     }
     double e1[3], e2[3], N[3];
     for (int a = 0; a < 3; ++a) {
@@ -223,11 +270,12 @@ __device__ __forceinline__ void tri_moment(const MeshView &M, const int t, doubl
 }
 
 __device__ __forceinline__ void tri_force_m(const MeshView &M, const int t, const int slot, const double m[3],
-                                            double g[3])
+                                            double g[3], const L2Keep &K)
 {
     const int kp = slot == 2 ? 0 : slot + 1, km = slot == 0 ? 2 : slot - 1;
-    const int vp = M.tris[3 * t + kp], vm = M.tris[3 * t + km];
-    const double dd[3] = {M.r[3 * vm] - M.r[3 * vp], M.r[3 * vm + 1] - M.r[3 * vp + 1], M.r[3 * vm + 2] - M.r[3 * vp + 2]};
+    const int vp = K.ld(M.tris + 3 * t + kp), vm = K.ld(M.tris + 3 * t + km);
+    double dd[3];
+    for (int a = 0; a < 3; ++a) dd[a] = K.ld(M.r + 3 * vm + a) - K.ld(M.r + 3 * vp + a);
     cross3(m, dd, g);
 }
 

@@ -21,6 +21,7 @@
 #include <cmath>
 #include <cstdint>
 #include <mutex>
+#include <type_traits>
 #include <utility>
 
 #include "iblb_internal.h"
@@ -186,6 +187,9 @@ __device__ __forceinline__ bool lattice_node(const LbView &L, const int x, const
         const int nxy = nx * ny;
         const int node = x + nx * y + nxy * z;
         T *__restrict__ f = static_cast<T *>(L.f);
+        // the patch nodes keep their lines in L2 between steps (see L2Keep)
+        struct NoKeep {};
+        [[maybe_unused]] const std::conditional_t<MODE == LAT_NEAR, L2Keep, NoKeep> K;
         const int qs = (int)L.qs;
         const bool px = L.bc[0] == IBL_BC_PERIODIC, py = L.bc[1] == IBL_BC_PERIODIC,
                    pz = L.bc[2] == IBL_BC_PERIODIC;
@@ -210,7 +214,8 @@ __device__ __forceinline__ bool lattice_node(const LbView &L, const int x, const
         if constexpr (!ODD) {
             sfor<19>([&](auto I) {
                 constexpr int i = decltype(I)::value;
-                g[i] = f[i * qs + node];
+                if constexpr (MODE == LAT_NEAR) g[i] = K.ld(f + i * qs + node);
+                else g[i] = f[i * qs + node];
             });
         } else {
             // source x - c_i, slot opp(i)
@@ -221,7 +226,8 @@ __device__ __forceinline__ bool lattice_node(const LbView &L, const int x, const
                                      (cz > 0 ? 16 : (cz < 0 ? 32 : 0));
                 const int off = (cx > 0 ? oxm : (cx < 0 ? oxp : 0)) + (cy > 0 ? oym : (cy < 0 ? oyp : 0)) +
                                 (cz > 0 ? ozm : (cz < 0 ? ozp : 0));
-                g[i] = (miss & need) == 0 ? f[opp(i) * qs + node + off] : T(0);
+                if constexpr (MODE == LAT_NEAR) g[i] = (miss & need) == 0 ? K.ld(f + opp(i) * qs + node + off) : T(0);
+                else g[i] = (miss & need) == 0 ? f[opp(i) * qs + node + off] : T(0);
             });
         }
 
@@ -250,7 +256,14 @@ __device__ __forceinline__ bool lattice_node(const LbView &L, const int x, const
         T Fx = T(0), Fy = T(0), Fz = T(0);
         T *__restrict__ force = static_cast<T *>(L.force);
         const int nodes = L.nodes;
-        if (in_patch) {
+        if constexpr (MODE == LAT_NEAR) {
+            Fx = K.ld(force + node);
+            Fy = K.ld(force + nodes + node);
+            Fz = K.ld(force + 2 * nodes + node);
+            K.st(force + node, T(0));
+            K.st(force + nodes + node, T(0));
+            K.st(force + 2 * nodes + node, T(0));
+        } else if (in_patch) {
             Fx = force[node];
             Fy = force[nodes + node];
             Fz = force[2 * nodes + node];
@@ -301,7 +314,8 @@ __device__ __forceinline__ bool lattice_node(const LbView &L, const int x, const
         if constexpr (!ODD) {
             sfor<19>([&](auto I) {
                 constexpr int i = decltype(I)::value;
-                f[opp(i) * qs + node] = g[i];
+                if constexpr (MODE == LAT_NEAR) K.st(f + opp(i) * qs + node, g[i]);
+                else f[opp(i) * qs + node] = g[i];
             });
         } else {
             // destination x + c_i, slot i.  The node coordinates pass through
@@ -327,14 +341,23 @@ __device__ __forceinline__ bool lattice_node(const LbView &L, const int x, const
                                      (cz > 0 ? 32 : (cz < 0 ? 16 : 0));
                 const int off = (cx > 0 ? sxp : (cx < 0 ? sxm : 0)) + (cy > 0 ? syp : (cy < 0 ? sym : 0)) +
                                 (cz > 0 ? szp : (cz < 0 ? szm : 0));
-                if ((smiss & need) == 0) f[i * qs + nodes_ + off] = g[i];
+                if ((smiss & need) == 0) {
+                    if constexpr (MODE == LAT_NEAR) K.st(f + i * qs + nodes_ + off, g[i]);
+                    else f[i * qs + nodes_ + off] = g[i];
+                }
             });
         }
         if (in_patch) {
             T *__restrict__ vel = static_cast<T *>(L.vel);
-            vel[node] = ux;
-            vel[nodes + node] = uy;
-            vel[2 * nodes + node] = uz;
+            if constexpr (MODE == LAT_NEAR) {
+                K.st(vel + node, ux);
+                K.st(vel + nodes + node, uy);
+                K.st(vel + 2 * nodes + node, uz);
+            } else {
+                vel[node] = ux;
+                vel[nodes + node] = uy;
+                vel[2 * nodes + node] = uz;
+            }
         }
         if constexpr (REC) {
             T *__restrict__ rec = static_cast<T *>(L.rec);
@@ -364,8 +387,14 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 4) k_lattice(LbView 
 }
 
 // The patch nodes of the step (grid-stride over the patch box, x fastest).
+#ifndef IBLB_NEAR_THREADS
+#define IBLB_NEAR_THREADS 256
+#endif
+#ifndef IBLB_NEAR_BLOCKS
+#define IBLB_NEAR_BLOCKS 304
+#endif
 template <typename T, bool ODD, bool REC>
-__global__ void __launch_bounds__(256) k_lattice_near(LbView L, int buf)
+__global__ void __launch_bounds__(IBLB_NEAR_THREADS, 1024 / IBLB_NEAR_THREADS) k_lattice_near(LbView L, int buf)
 {
     const Ctl *c = L.ctl;
     const int ex = c->patch_ext[buf][0] + 1, ey = c->patch_ext[buf][1] + 1, ez = c->patch_ext[buf][2] + 1;
@@ -502,11 +531,12 @@ __device__ void patch_from_rows(const LbView &L, const MeshView &M, int buf)
 {
     const int lane = threadIdx.x & 31;
     const int rows = L.ctl->n_part;
+    const L2Keep K;
     double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
     for (int k = lane; k < rows; k += 32)
         for (int a = 0; a < 3; ++a) {
-            mn[a] = fmin(mn[a], M.part[6 * k + a]);
-            mx[a] = fmax(mx[a], M.part[6 * k + 3 + a]);
+            mn[a] = fmin(mn[a], K.ld(M.part + 6 * k + a));
+            mx[a] = fmax(mx[a], K.ld(M.part + 6 * k + 3 + a));
         }
     for (int a = 0; a < 3; ++a)
         for (int o = 16; o > 0; o >>= 1) {
@@ -529,13 +559,15 @@ __device__ __forceinline__ void spread_body(const LbView &L, const MeshView &M, 
     const int lane = threadIdx.x % kLanesPerNode;
     const bool valid = gid < M.nv;
     const int i = valid ? gid : M.nv - 1;
+    const L2Keep K;
     double F[3] = {0.0, 0.0, 0.0};
-    for (int k = M.n2t_ptr[i] + lane; k < M.n2t_ptr[i + 1]; k += kLanesPerNode) {
-        const int e = M.n2t[k];
+    const int k0 = K.ld(M.n2t_ptr + i), k1 = K.ld(M.n2t_ptr + i + 1);
+    for (int k = k0 + lane; k < k1; k += kLanesPerNode) {
+        const int e = K.ld(M.n2t + k);
         const int t = e / 3;
-        const double m[3] = {M.tm[3 * t], M.tm[3 * t + 1], M.tm[3 * t + 2]};
+        const double m[3] = {K.ld(M.tm + 3 * t), K.ld(M.tm + 3 * t + 1), K.ld(M.tm + 3 * t + 2)};
         double g[3];
-        tri_force_m(M, t, e - 3 * t, m, g);
+        tri_force_m(M, t, e - 3 * t, m, g, K);
         for (int a = 0; a < 3; ++a) F[a] += g[a];
     }
     for (int o = kLanesPerNode / 2; o > 0; o >>= 1)
@@ -545,7 +577,7 @@ __device__ __forceinline__ void spread_body(const LbView &L, const MeshView &M, 
         M.fn[3 * i + 1] = F[1];
         M.fn[3 * i + 2] = F[2];
     }
-    const NodeStencil S = node_stencil(L, M.r + 3 * i, lane);
+    const NodeStencil S = node_stencil(L, M.r + 3 * i, lane, &K);
     if (!valid) return;
     if (!S.ok) {
         if (lane == 0) atomicOr(&L.ctl->err, IBL_ERRBIT_WALL);
@@ -564,9 +596,9 @@ __device__ __forceinline__ void spread_body(const LbView &L, const MeshView &M, 
     for (int a = 0; a < 4; ++a) {
         const T dl = w[a] * wy * wz;
         const int id = row + wrap_index(S.base[0] + a, nx, perx);
-        atomicAdd(force + id, Fx * dl);
-        atomicAdd(force + nodes + id, Fy * dl);
-        atomicAdd(force + 2 * nodes + id, Fz * dl);
+        K.red_add(force + id, Fx * dl);
+        K.red_add(force + nodes + id, Fy * dl);
+        K.red_add(force + 2 * nodes + id, Fz * dl);
     }
 }
 
@@ -576,9 +608,10 @@ __global__ void __launch_bounds__(128) k_tri_moment(MeshView M)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= M.nt) return;
+    const L2Keep K;
     double m[3];
-    tri_moment(M, t, m);
-    for (int a = 0; a < 3; ++a) M.tm[3 * t + a] = m[a];
+    tri_moment(M, t, m, K);
+    for (int a = 0; a < 3; ++a) K.st(M.tm + 3 * t + a, m[a]);
 }
 
 // Ensemble version: blockIdx.y is the member within the group.
@@ -587,9 +620,10 @@ __global__ void __launch_bounds__(128) k_tri_moment_batched(const __grid_constan
     const MeshView &M = MG.v[blockIdx.y];
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= M.nt) return;
+    const L2Keep K;
     double m[3];
-    tri_moment(M, t, m);
-    for (int a = 0; a < 3; ++a) M.tm[3 * t + a] = m[a];
+    tri_moment(M, t, m, K);
+    for (int a = 0; a < 3; ++a) K.st(M.tm + 3 * t + a, m[a]);
 }
 
 template <typename T>
@@ -614,12 +648,13 @@ __device__ __forceinline__ void centre_of_mass(const LbView &L, const MeshView &
     __shared__ double sh[kCentreThreads / 32][4];
     __shared__ int last;
     const double ref[3] = {0.5 * (L.n[0] - 1), 0.5 * (L.n[1] - 1), 0.5 * (L.n[2] - 1)};
+    const L2Keep K;
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     for (int t = blk * kCentreThreads + (int)threadIdx.x; t < M.nt; t += kCentreBlocks * kCentreThreads) {
         double p[3][3];
         for (int c = 0; c < 3; ++c) {
-            const int q = M.tris[3 * t + c];
-            for (int a = 0; a < 3; ++a) p[c][a] = M.r[3 * q + a] - ref[a];
+            const int q = K.ld(M.tris + 3 * t + c);
+            for (int a = 0; a < 3; ++a) p[c][a] = K.ld(M.r + 3 * q + a) - ref[a];
         }
         double bc[3];
         cross3(p[1], p[2], bc);
@@ -664,7 +699,8 @@ __device__ __forceinline__ void interp_body(const LbView &L, const MeshView &M, 
     const int lane = threadIdx.x % kLanesPerNode;
     const bool valid = gid < M.nv;
     const int i = valid ? gid : M.nv - 1;
-    const NodeStencil S = node_stencil(L, M.r + 3 * i, lane);
+    const L2Keep K;
+    const NodeStencil S = node_stencil(L, M.r + 3 * i, lane, &K);
     T v[3] = {T(0), T(0), T(0)};
     if (S.ok) {
         const bool perx = L.bc[0] == IBL_BC_PERIODIC, pery = L.bc[1] == IBL_BC_PERIODIC,
@@ -680,9 +716,9 @@ __device__ __forceinline__ void interp_body(const LbView &L, const MeshView &M, 
         for (int a = 0; a < 4; ++a) {
             const T dl = w[a] * wy * wz;
             const int id = row + wrap_index(S.base[0] + a, nx, perx);
-            v[0] += vel[id] * dl;
-            v[1] += vel[nodes + id] * dl;
-            v[2] += vel[2 * nodes + id] * dl;
+            v[0] += K.ld(vel + id) * dl;
+            v[1] += K.ld(vel + nodes + id) * dl;
+            v[2] += K.ld(vel + 2 * nodes + id) * dl;
         }
     }
     for (int o = kLanesPerNode / 2; o > 0; o >>= 1)
@@ -690,18 +726,18 @@ __device__ __forceinline__ void interp_body(const LbView &L, const MeshView &M, 
     const bool have = valid && lane == 0;
     double r[3] = {0.0, 0.0, 0.0};
     if (have) {
-        r[0] = M.r[3 * i];
-        r[1] = M.r[3 * i + 1];
-        r[2] = M.r[3 * i + 2];
+        r[0] = K.ld(M.r + 3 * i);
+        r[1] = K.ld(M.r + 3 * i + 1);
+        r[2] = K.ld(M.r + 3 * i + 2);
         if (!S.ok) {
             atomicOr(&L.ctl->err, IBL_ERRBIT_WALL);
         } else {
             r[0] += (double)v[0];
             r[1] += (double)v[1];
             r[2] += (double)v[2];
-            M.r[3 * i] = r[0];
-            M.r[3 * i + 1] = r[1];
-            M.r[3 * i + 2] = r[2];
+            K.st(M.r + 3 * i, r[0]);
+            K.st(M.r + 3 * i + 1, r[1]);
+            K.st(M.r + 3 * i + 2, r[2]);
         }
     }
     // block min / max of the new positions -> one partial row per block; the
@@ -726,8 +762,8 @@ __device__ __forceinline__ void interp_body(const LbView &L, const MeshView &M, 
                 mn = fmin(mn, smn[a][w]);
                 mx = fmax(mx, smx[a][w]);
             }
-            M.part[6 * blk + a] = mn;
-            M.part[6 * blk + 3 + a] = mx;
+            K.st(M.part + 6 * blk + a, mn);
+            K.st(M.part + 6 * blk + 3 + a, mx);
         }
         if (blk == 0) L.ctl->n_part = nblk;
     }
@@ -1239,7 +1275,10 @@ static void lattice_grid(const LbView &L, dim3 &grid, dim3 &block)
 template <typename T, bool ODD, bool REC>
 static void lattice_launch_t(const LbView &L, int mode, int pbuf, dim3 g, dim3 b, cudaStream_t s)
 {
-    if (mode == LAT_FAR) k_lattice<T, ODD, REC, LAT_FAR><<<g, b, 0, s>>>(L, pbuf);
+#ifndef IBLB_FAR_SMEM
+#define IBLB_FAR_SMEM 0
+#endif
+    if (mode == LAT_FAR) k_lattice<T, ODD, REC, LAT_FAR><<<g, b, IBLB_FAR_SMEM, s>>>(L, pbuf);
     else k_lattice<T, ODD, REC, LAT_FULL><<<g, b, 0, s>>>(L, pbuf);
 }
 
@@ -1269,7 +1308,7 @@ cudaError_t launch_lattice(const LbView &L, bool odd, bool record, int mode, int
 
 cudaError_t launch_near(const LbView &L, bool odd, bool record, int pbuf, cudaStream_t s, int prio)
 {
-    const dim3 g(2 * 152), b(256);  // grid-stride over the patch box
+    const dim3 g(IBLB_NEAR_BLOCKS), b(IBLB_NEAR_THREADS);  // grid-stride over the patch box
     if (L.precision == IBL_FP64) {
         if (odd) {
             if (record) return launch_p(k_lattice_near<double, true, true>, g, b, s, prio, L, pbuf);
