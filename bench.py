@@ -73,7 +73,7 @@ def traffic_from_profiles():
     import hashlib
 
     src = open(os.path.join(ROOT, "paper_2403_01161_gb300", "csrc", "iblb_kernels.cu")).read()
-    marker = "// Advances the step counter when no droplet kernel follows the lattice kernel."
+    marker = "// ---------------------------------------------------------------------------\n// Immersed boundary."
     if marker not in src:
         return None
     hdr = open(os.path.join(ROOT, "paper_2403_01161_gb300", "csrc", "iblb_device.cuh")).read()

@@ -258,7 +258,6 @@ int one_step(ibl_lb *lb, bool record, cudaStream_t sL, cudaStream_t sH)
         const int pl = prof_begin(lb, PROF_LB, sL);
         e = iblb::launch_lattice(lb->v, odd, record, iblb::LAUNCH_FULL, pbuf, sL);
         prof_end(lb, pl, sL);
-        if (e == cudaSuccess) e = iblb::launch_advance(lb->v, sL);
         if (e != cudaSuccess) return cuda_fail(e, "lattice launch");
         lb->host_step = next;
         return IBL_OK;
@@ -281,13 +280,13 @@ int one_step(ibl_lb *lb, bool record, cudaStream_t sL, cudaStream_t sH)
     if (e == cudaSuccess) e = cudaEventRecord(evNear[par], sH);
     if (e != cudaSuccess) return cuda_fail(e, "droplet-side launch");
     // bound stream: the outside nodes once the previous patch update (and
-    // regularisation) has finished; then the step counter
+    // regularisation) has finished; one thread of that kernel closes the step
+    // (step counter, frame of the next step)
     e = cudaStreamWaitEvent(sL, evNear[par ^ 1], 0);
     if (e == cudaSuccess && lb->v.recentre) e = cudaStreamWaitEvent(sL, evCentre, 0);
     const int pl = prof_begin(lb, PROF_LB, sL);
     if (e == cudaSuccess) e = iblb::launch_lattice(lb->v, odd, record, iblb::LAUNCH_FAR, pbuf, sL);
     prof_end(lb, pl, sL);
-    if (e == cudaSuccess) e = iblb::launch_advance(lb->v, sL);
     if (e == cudaSuccess) e = cudaEventRecord(evFar[par], sL);
     if (e != cudaSuccess) return cuda_fail(e, "lattice launch");
     // helper stream: interpolation + advection, scheduled regularisation

@@ -23,7 +23,7 @@ struct alignas(128) Ctl {
     int err;                     // IBL_ERRBIT_* (sticky)
     int reg_iters;               // iterations of the latest regularisation
     int n_records;               // shape records written
-    int frame;                   // frame index applied by the next step
+    int frame_par[2];            // frame index applied by the next step of parity p (0 even, 1 odd)
     int reg_count;               // regularisations performed (scheduled checks that triggered)
     double mesh_q;               // mesh quality at the last scheduled check: max over triangles of longest/shortest edge
     unsigned int cen_ticket;     // last-block ticket of the force kernel's centre-of-mass reduction
@@ -126,7 +126,6 @@ cudaError_t launch_init(const LbView &L, cudaStream_t s);
 cudaError_t launch_lattice(const LbView &L, bool odd, bool record, int mode, int pbuf, cudaStream_t s);
 cudaError_t launch_near(const LbView &L, bool odd, bool record, int pbuf, cudaStream_t s, int prio = 0);
 enum { LAUNCH_FULL = 0, LAUNCH_FAR = 1 };
-cudaError_t launch_advance(const LbView &L, cudaStream_t s);
 cudaError_t launch_convert_frames(const LbView &L, int k0, int k1, cudaStream_t s);
 cudaError_t launch_spread(const LbView &L, const MeshView &M, int next_buf, cudaStream_t s, int prio = 0);
 cudaError_t launch_interp(const LbView &L, const MeshView &M, cudaStream_t s, int prio = 0);

@@ -235,7 +235,7 @@ __device__ __forceinline__ bool lattice_node(const LbView &L, const int x, const
             // Eq. (velo_facce_cubo_da_gradiente) in the storage precision,
             // about the box centre or, with re-centring, about the droplet's
             // centre of mass at the start of the step (the offset in FP64)
-            const T *A = static_cast<const T *>(L.frames_t) + 9 * L.ctl->frame;
+            const T *A = static_cast<const T *>(L.frames_t) + 9 * L.ctl->frame_par[ODD ? 1 : 0];
             T lx, ly, lz;
             if (L.recentre) {
                 const double *c = L.ctl->centre[pbuf];
@@ -373,12 +373,27 @@ __device__ __forceinline__ bool lattice_node(const LbView &L, const int x, const
     return bad;
 }
 
+// Closes step t: the step counter becomes t + 1 and the frame of step t + 1
+// goes to its parity's slot.  The lattice kernel of step t and the patch
+// update of step t read the other slot, and the kernels of step t - 1, the
+// last readers of this one, have finished (both are ordered before the
+// lattice kernel of step t), so one thread of that kernel can do it while the
+// rest of the step runs: no separate launch sits between two lattice updates.
+__device__ __forceinline__ void close_step(const LbView &L)
+{
+    const long long s = L.ctl->step + 1;
+    L.ctl->step = s;
+    const long long k = s / L.n_hold;
+    L.ctl->frame_par[s & 1] = (int)(k < L.n_frames - 1 ? k : L.n_frames - 1);
+}
+
 template <typename T, bool ODD, bool REC, int MODE>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 4) k_lattice(LbView L, int pbuf)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
+    if ((blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x | threadIdx.y) == 0) close_step(L);
     bool bad = false;
     if (x < L.n[0] && y < L.n[1]) bad = lattice_node<T, ODD, REC, MODE>(L, x, y, z, pbuf);
     // sticky instability flag, one atomic per warp at most
@@ -387,14 +402,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 4) k_lattice(LbView 
 }
 
 // The patch nodes of the step (grid-stride over the patch box, x fastest).
-#ifndef IBLB_NEAR_THREADS
-#define IBLB_NEAR_THREADS 256
-#endif
-#ifndef IBLB_NEAR_BLOCKS
-#define IBLB_NEAR_BLOCKS 304
-#endif
 template <typename T, bool ODD, bool REC>
-__global__ void __launch_bounds__(IBLB_NEAR_THREADS, 1024 / IBLB_NEAR_THREADS) k_lattice_near(LbView L, int buf)
+__global__ void __launch_bounds__(256) k_lattice_near(LbView L, int buf)
 {
     const Ctl *c = L.ctl;
     const int ex = c->patch_ext[buf][0] + 1, ey = c->patch_ext[buf][1] + 1, ez = c->patch_ext[buf][2] + 1;
@@ -451,16 +460,6 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
     if (m != 0u && (threadIdx.x & 31) == 0) atomicOr(&L.ctl->err, IBL_ERRBIT_UNSTABLE);
 }
 
-// Advances the step counter when no droplet kernel follows the lattice kernel.
-__device__ __forceinline__ void close_step(const LbView &L)
-{
-    const long long s = L.ctl->step + 1;
-    L.ctl->step = s;
-    const long long k = s / L.n_hold;
-    L.ctl->frame = (int)(k < L.n_frames - 1 ? k : L.n_frames - 1);
-}
-
-__global__ void k_advance(LbView L) { close_step(L); }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_init(LbView L)
@@ -1275,10 +1274,7 @@ static void lattice_grid(const LbView &L, dim3 &grid, dim3 &block)
 template <typename T, bool ODD, bool REC>
 static void lattice_launch_t(const LbView &L, int mode, int pbuf, dim3 g, dim3 b, cudaStream_t s)
 {
-#ifndef IBLB_FAR_SMEM
-#define IBLB_FAR_SMEM 0
-#endif
-    if (mode == LAT_FAR) k_lattice<T, ODD, REC, LAT_FAR><<<g, b, IBLB_FAR_SMEM, s>>>(L, pbuf);
+    if (mode == LAT_FAR) k_lattice<T, ODD, REC, LAT_FAR><<<g, b, 0, s>>>(L, pbuf);
     else k_lattice<T, ODD, REC, LAT_FULL><<<g, b, 0, s>>>(L, pbuf);
 }
 
@@ -1308,7 +1304,7 @@ cudaError_t launch_lattice(const LbView &L, bool odd, bool record, int mode, int
 
 cudaError_t launch_near(const LbView &L, bool odd, bool record, int pbuf, cudaStream_t s, int prio)
 {
-    const dim3 g(IBLB_NEAR_BLOCKS), b(IBLB_NEAR_THREADS);  // grid-stride over the patch box
+    const dim3 g(2 * 152), b(256);  // grid-stride over the patch box
     if (L.precision == IBL_FP64) {
         if (odd) {
             if (record) return launch_p(k_lattice_near<double, true, true>, g, b, s, prio, L, pbuf);
@@ -1337,12 +1333,6 @@ cudaError_t launch_convert_frames(const LbView &L, int k0, int k1, cudaStream_t 
     const unsigned g = blocks_for(9LL * (k1 - k0), 256);
     if (L.precision == IBL_FP64) k_convert_frames<double><<<g, 256, 0, s>>>(L, k0, k1);
     else k_convert_frames<float><<<g, 256, 0, s>>>(L, k0, k1);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_advance(const LbView &L, cudaStream_t s)
-{
-    k_advance<<<1, 1, 0, s>>>(L);
     return cudaGetLastError();
 }
 
