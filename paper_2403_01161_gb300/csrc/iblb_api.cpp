@@ -664,7 +664,7 @@ int ensemble_layout(int n, ibl_lb *const *members, EnsembleLayout &L, std::strin
             return IBL_EINVAL;
         }
         lat += (lb->v.nodes + 255) / 256;
-        node += ((long long)lb->mesh->v.nv * 16 + 127) / 128;
+        node += ((long long)lb->mesh->v.nv + iblb::kFwdNodesPerBlock - 1) / iblb::kFwdNodesPerBlock;
     }
     if (lat > 0x7fffffffLL) {
         why = "ensemble too large";
@@ -1394,7 +1394,8 @@ int ibl_ensemble_create(int n, ibl_lb *const *members, void *workspace, size_t b
         lat_start.push_back((int)lat_member.size());
         for (int b = 0; b < (lb->v.nodes + 255) / 256; ++b) lat_member.push_back(k);
         node_start.push_back((int)node_member.size());
-        for (int b = 0; b < (lb->mesh->v.nv * 16 + 127) / 128; ++b) node_member.push_back(k);
+        for (int b = 0; b < (lb->mesh->v.nv + iblb::kFwdNodesPerBlock - 1) / iblb::kFwdNodesPerBlock; ++b)
+            node_member.push_back(k);
     }
     lat_start.push_back((int)lat_member.size());
     node_start.push_back((int)node_member.size());

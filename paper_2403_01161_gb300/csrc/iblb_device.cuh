@@ -102,6 +102,7 @@ __device__ __forceinline__ int wrap_index(int g, int n, bool periodic)
 
 constexpr int kLanesPerNode = 16;  // lane = (b, c) row of the 4x4x4 stencil
 constexpr int kIbThreads = 128;    // threads per block of the node-group kernels
+static_assert(kFwdNodesPerBlock * kFwdLanes == kIbThreads, "forward node-group blocks");
 
 // Per-node stencil of the 16-lane group: lanes 0..2 compute, in FP64, the
 // origin base_a = floor(r_a) - 1 and the exact fraction r_a - floor(r_a) of
@@ -158,6 +159,7 @@ struct NodeStencil {
     double frac[3];
     bool ok;
 };
+template <int LANES = kLanesPerNode>
 __device__ __forceinline__ NodeStencil node_stencil(const LbView &L, const double *r, int lane,
                                                     const L2Keep *keep = nullptr)
 {
@@ -175,7 +177,7 @@ __device__ __forceinline__ NodeStencil node_stencil(const LbView &L, const doubl
         base = A.base;
         fr = ok ? ra - floor(ra) : 0.0;
     }
-    const int w0 = (threadIdx.x & 31) & ~(kLanesPerNode - 1);
+    const int w0 = (threadIdx.x & 31) & ~(LANES - 1);
     NodeStencil S;
     S.ok = true;
     // every lane executes every full-mask shuffle (no short-circuit around

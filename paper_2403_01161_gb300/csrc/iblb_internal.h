@@ -66,7 +66,7 @@ struct MeshView {
     const int *nb_ptr;  // [nv+1]
     const int *nb_idx;  // [3 nt]
     double *s0, *s1, *s2;  // regularisation scratch, [nv][3] each
-    double *tm;            // [nt][3] m_t = -sigma N_t / (2 |N_t|) at the current positions (triangle kernel, read by the force kernel)
+    double *tm;            // [nt][3] m_t = -sigma N_t / (2 |N_t|) at the current positions (ensemble: written by the batched triangle kernel, read by the batched force kernel)
     double *part;          // per-block bounding-box partials of the interpolation kernel, [blocks][6]
     double *cpart;         // re-centring: per-block volume and first moment, [kCentreBlocks][4]
     double *obs_part;      // per-block partial sums of the shape-record kernel, [kObsBlocksMax][11]
@@ -129,6 +129,15 @@ enum { LAUNCH_FULL = 0, LAUNCH_FAR = 1 };
 cudaError_t launch_convert_frames(const LbView &L, int k0, int k1, cudaStream_t s);
 cudaError_t launch_spread(const LbView &L, const MeshView &M, int next_buf, cudaStream_t s, int prio = 0);
 cudaError_t launch_interp(const LbView &L, const MeshView &M, cudaStream_t s, int prio = 0);
+// Lanes per mesh node in the forward force/spread and interpolation kernels
+// (128-thread blocks); each lane takes every kFwdLanes-th incident triangle
+// and 16 / kFwdLanes of the 16 (y, z) rows of the 4x4x4 stencil.
+#ifndef IBLB_FWD_LANES
+#define IBLB_FWD_LANES 8
+#endif
+constexpr int kFwdLanes = IBLB_FWD_LANES;
+static_assert(kFwdLanes == 4 || kFwdLanes == 8 || kFwdLanes == 16, "lanes per mesh node");
+constexpr int kFwdNodesPerBlock = 128 / kFwdLanes;
 // re-centring: the droplet's centre of mass at the current positions into ctl->centre[buf]
 constexpr int kCentreBlocks = 16;
 cudaError_t launch_centre(const LbView &L, const MeshView &M, int buf, cudaStream_t s, int prio = 0);

@@ -550,33 +550,42 @@ __device__ void patch_from_rows(const LbView &L, const MeshView &M, int buf)
 // (Eq. (ibm_force_d)(a)) by atomic adds into the Eulerian force.  Sixteen
 // lanes per node: the lanes split the incident triangles (reduced with
 // shuffles), then each lane adds one x-row of four stencil points.
-template <typename T>
+// STORED: m_t comes from M.tm (written by k_tri_moment_batched just before);
+// otherwise each lane evaluates it for its triangle (three times per
+// triangle in all, but one kernel boundary fewer on the droplet chain of a
+// single droplet, which is latency bound).
+template <typename T, bool STORED>
 __device__ __forceinline__ void spread_body(const LbView &L, const MeshView &M, const int blk, const int next_buf)
 {
     if (blk == 0 && threadIdx.x < 32) patch_from_rows(L, M, next_buf);
-    const int gid = blk * (kIbThreads / kLanesPerNode) + threadIdx.x / kLanesPerNode;
-    const int lane = threadIdx.x % kLanesPerNode;
+    const int gid = blk * kFwdNodesPerBlock + threadIdx.x / kFwdLanes;
+    const int lane = threadIdx.x % kFwdLanes;
     const bool valid = gid < M.nv;
     const int i = valid ? gid : M.nv - 1;
     const L2Keep K;
     double F[3] = {0.0, 0.0, 0.0};
     const int k0 = K.ld(M.n2t_ptr + i), k1 = K.ld(M.n2t_ptr + i + 1);
-    for (int k = k0 + lane; k < k1; k += kLanesPerNode) {
+    for (int k = k0 + lane; k < k1; k += kFwdLanes) {
         const int e = K.ld(M.n2t + k);
         const int t = e / 3;
-        const double m[3] = {K.ld(M.tm + 3 * t), K.ld(M.tm + 3 * t + 1), K.ld(M.tm + 3 * t + 2)};
+        double m[3];
+        if constexpr (STORED) {
+            for (int a = 0; a < 3; ++a) m[a] = K.ld(M.tm + 3 * t + a);
+        } else {
+            tri_moment(M, t, m, K);
+        }
         double g[3];
         tri_force_m(M, t, e - 3 * t, m, g, K);
         for (int a = 0; a < 3; ++a) F[a] += g[a];
     }
-    for (int o = kLanesPerNode / 2; o > 0; o >>= 1)
-        for (int a = 0; a < 3; ++a) F[a] += __shfl_xor_sync(0xffffffffu, F[a], o, kLanesPerNode);
+    for (int o = kFwdLanes / 2; o > 0; o >>= 1)
+        for (int a = 0; a < 3; ++a) F[a] += __shfl_xor_sync(0xffffffffu, F[a], o, kFwdLanes);
     if (valid && lane == 0) {
         M.fn[3 * i] = F[0];
         M.fn[3 * i + 1] = F[1];
         M.fn[3 * i + 2] = F[2];
     }
-    const NodeStencil S = node_stencil(L, M.r + 3 * i, lane, &K);
+    const NodeStencil S = node_stencil<kFwdLanes>(L, M.r + 3 * i, lane, &K);
     if (!valid) return;
     if (!S.ok) {
         if (lane == 0) atomicOr(&L.ctl->err, IBL_ERRBIT_WALL);
@@ -584,36 +593,31 @@ __device__ __forceinline__ void spread_body(const LbView &L, const MeshView &M, 
     }
     const bool perx = L.bc[0] == IBL_BC_PERIODIC, pery = L.bc[1] == IBL_BC_PERIODIC,
                perz = L.bc[2] == IBL_BC_PERIODIC;
-    const int b = lane & 3, c = lane >> 2;
-    T w[4], wy, wz;
-    stencil_weights<T>(S, b, c, w, wy, wz);
     const int nx = L.n[0], nxy = L.n[0] * L.n[1], nodes = L.nodes;
-    const int row = wrap_index(S.base[1] + b, L.n[1], pery) * nx + wrap_index(S.base[2] + c, L.n[2], perz) * nxy;
     T *force = static_cast<T *>(L.force);
     const T Fx = T(F[0]), Fy = T(F[1]), Fz = T(F[2]);
+    // the lane's (y, z) rows r = lane, lane + kFwdLanes, ...: (b, c) = (r & 3, r >> 2)
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        const T dl = w[a] * wy * wz;
-        const int id = row + wrap_index(S.base[0] + a, nx, perx);
-        K.red_add(force + id, Fx * dl);
-        K.red_add(force + nodes + id, Fy * dl);
-        K.red_add(force + 2 * nodes + id, Fz * dl);
+    for (int q = 0; q < 16 / kFwdLanes; ++q) {
+        const int r = lane + kFwdLanes * q, b = r & 3, c = r >> 2;
+        T w[4], wy, wz;
+        stencil_weights<T>(S, b, c, w, wy, wz);
+        const int row =
+            wrap_index(S.base[1] + b, L.n[1], pery) * nx + wrap_index(S.base[2] + c, L.n[2], perz) * nxy;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const T dl = w[a] * wy * wz;
+            const int id = row + wrap_index(S.base[0] + a, nx, perx);
+            K.red_add(force + id, Fx * dl);
+            K.red_add(force + nodes + id, Fy * dl);
+            K.red_add(force + 2 * nodes + id, Fz * dl);
+        }
     }
 }
 
-// m_t of every triangle at the current positions (Eq. (pi_drop)), once per
-// step, for the force kernel that follows on the same stream.
-__global__ void __launch_bounds__(128) k_tri_moment(MeshView M)
-{
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= M.nt) return;
-    const L2Keep K;
-    double m[3];
-    tri_moment(M, t, m, K);
-    for (int a = 0; a < 3; ++a) K.st(M.tm + 3 * t + a, m[a]);
-}
-
-// Ensemble version: blockIdx.y is the member within the group.
+// Ensemble: m_t of every triangle of every member at the current positions
+// (Eq. (pi_drop)), once per step, for the batched force kernel that follows
+// on the same stream; blockIdx.y is the member within the group.
 __global__ void __launch_bounds__(128) k_tri_moment_batched(const __grid_constant__ MeshGroup MG)
 {
     const MeshView &M = MG.v[blockIdx.y];
@@ -628,7 +632,7 @@ __global__ void __launch_bounds__(128) k_tri_moment_batched(const __grid_constan
 template <typename T>
 __global__ void __launch_bounds__(128) k_spread(LbView L, MeshView M, int next_buf)
 {
-    spread_body<T>(L, M, blockIdx.x, next_buf);
+    spread_body<T, false>(L, M, blockIdx.x, next_buf);
 }
 
 // Re-centring (Sec. 3.2: the linearisation is centred on the droplet's
@@ -694,34 +698,38 @@ __global__ void __launch_bounds__(kCentreThreads)
 template <typename T>
 __device__ __forceinline__ void interp_body(const LbView &L, const MeshView &M, const int blk, const int nblk)
 {
-    const int gid = blk * (kIbThreads / kLanesPerNode) + threadIdx.x / kLanesPerNode;
-    const int lane = threadIdx.x % kLanesPerNode;
+    const int gid = blk * kFwdNodesPerBlock + threadIdx.x / kFwdLanes;
+    const int lane = threadIdx.x % kFwdLanes;
     const bool valid = gid < M.nv;
     const int i = valid ? gid : M.nv - 1;
     const L2Keep K;
-    const NodeStencil S = node_stencil(L, M.r + 3 * i, lane, &K);
+    const NodeStencil S = node_stencil<kFwdLanes>(L, M.r + 3 * i, lane, &K);
     T v[3] = {T(0), T(0), T(0)};
     if (S.ok) {
         const bool perx = L.bc[0] == IBL_BC_PERIODIC, pery = L.bc[1] == IBL_BC_PERIODIC,
                    perz = L.bc[2] == IBL_BC_PERIODIC;
-        const int b = lane & 3, c = lane >> 2;
-        T w[4], wy, wz;
-        stencil_weights<T>(S, b, c, w, wy, wz);
         const int nx = L.n[0], nxy = L.n[0] * L.n[1], nodes = L.nodes;
-        const int row =
-            wrap_index(S.base[1] + b, L.n[1], pery) * nx + wrap_index(S.base[2] + c, L.n[2], perz) * nxy;
         const T *vel = static_cast<const T *>(L.vel);
+        // the lane's (y, z) rows r = lane, lane + kFwdLanes, ...: (b, c) = (r & 3, r >> 2)
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            const T dl = w[a] * wy * wz;
-            const int id = row + wrap_index(S.base[0] + a, nx, perx);
-            v[0] += K.ld(vel + id) * dl;
-            v[1] += K.ld(vel + nodes + id) * dl;
-            v[2] += K.ld(vel + 2 * nodes + id) * dl;
+        for (int q = 0; q < 16 / kFwdLanes; ++q) {
+            const int r = lane + kFwdLanes * q, b = r & 3, c = r >> 2;
+            T w[4], wy, wz;
+            stencil_weights<T>(S, b, c, w, wy, wz);
+            const int row =
+                wrap_index(S.base[1] + b, L.n[1], pery) * nx + wrap_index(S.base[2] + c, L.n[2], perz) * nxy;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const T dl = w[a] * wy * wz;
+                const int id = row + wrap_index(S.base[0] + a, nx, perx);
+                v[0] += K.ld(vel + id) * dl;
+                v[1] += K.ld(vel + nodes + id) * dl;
+                v[2] += K.ld(vel + 2 * nodes + id) * dl;
+            }
         }
     }
-    for (int o = kLanesPerNode / 2; o > 0; o >>= 1)
-        for (int a = 0; a < 3; ++a) v[a] += __shfl_xor_sync(0xffffffffu, v[a], o, kLanesPerNode);
+    for (int o = kFwdLanes / 2; o > 0; o >>= 1)
+        for (int a = 0; a < 3; ++a) v[a] += __shfl_xor_sync(0xffffffffu, v[a], o, kFwdLanes);
     const bool have = valid && lane == 0;
     double r[3] = {0.0, 0.0, 0.0};
     if (have) {
@@ -744,10 +752,12 @@ __device__ __forceinline__ void interp_body(const LbView &L, const MeshView &M, 
     __shared__ double smn[3][4], smx[3][4];
     const int wlane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int a = 0; a < 3; ++a) {
-        // lanes 0 and 16 hold the warp's two nodes
+        // lanes 0, kFwdLanes, 2 kFwdLanes, ... hold the warp's nodes
         double mn = have ? r[a] : 1e300, mx = have ? r[a] : -1e300;
-        mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, 16));
-        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
+        for (int o = kFwdLanes; o < 32; o <<= 1) {
+            mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+            mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        }
         if (wlane == 0) {
             smn[a][warp] = mn;
             smx[a][warp] = mx;
@@ -791,7 +801,7 @@ __global__ void __launch_bounds__(128)
                      const int next_buf)
 {
     const int mi = blk_member[b0 + blockIdx.x];
-    spread_body<T>(LG.v[mi - m0], MG.v[mi - m0], b0 + (int)blockIdx.x - blk_start[mi], next_buf);
+    spread_body<T, true>(LG.v[mi - m0], MG.v[mi - m0], b0 + (int)blockIdx.x - blk_start[mi], next_buf);
 }
 
 template <typename T>
@@ -1338,9 +1348,7 @@ cudaError_t launch_convert_frames(const LbView &L, int k0, int k1, cudaStream_t 
 
 cudaError_t launch_spread(const LbView &L, const MeshView &M, int next_buf, cudaStream_t s, int prio)
 {
-    cudaError_t e = launch_p(k_tri_moment, dim3(blocks_for(M.nt, 128)), dim3(128), s, prio, M);
-    if (e != cudaSuccess) return e;
-    const dim3 g(blocks_for((long long)M.nv * kLanesPerNode, kIbThreads)), b(kIbThreads);
+    const dim3 g(blocks_for((long long)M.nv * kFwdLanes, kIbThreads)), b(kIbThreads);
     if (L.precision == IBL_FP64) return launch_p(k_spread<double>, g, b, s, prio, L, M, next_buf);
     return launch_p(k_spread<float>, g, b, s, prio, L, M, next_buf);
 }
@@ -1352,7 +1360,7 @@ cudaError_t launch_centre(const LbView &L, const MeshView &M, int buf, cudaStrea
 
 cudaError_t launch_interp(const LbView &L, const MeshView &M, cudaStream_t s, int prio)
 {
-    const dim3 g(blocks_for((long long)M.nv * kLanesPerNode, kIbThreads)), b(kIbThreads);
+    const dim3 g(blocks_for((long long)M.nv * kFwdLanes, kIbThreads)), b(kIbThreads);
     if (L.precision == IBL_FP64) return launch_p(k_interp<double>, g, b, s, prio, L, M);
     return launch_p(k_interp<float>, g, b, s, prio, L, M);
 }
