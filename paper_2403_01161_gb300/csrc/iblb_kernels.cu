@@ -388,12 +388,23 @@ __device__ __forceinline__ void close_step(const LbView &L)
 }
 
 template <typename T, bool ODD, bool REC, int MODE>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 4) k_lattice(LbView L, int pbuf)
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 4) k_lattice(LbView L, int pbuf, int ahead)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
     if ((blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x | threadIdx.y) == 0) close_step(L);
+    // L2 prefetch of this thread's node `ahead` z-planes on, which a block of
+    // about one resident wave later updates: its loads then find the lines in
+    // L2 instead of waiting on DRAM behind the stream
+    const int za = z + ahead;
+    if (ahead > 0 && za < L.n[2] && x < L.n[0] && y < L.n[1]) {
+        const T *f = static_cast<const T *>(L.f);
+        const int na = x + L.n[0] * (y + L.n[1] * za);
+        const int qs = (int)L.qs;
+#pragma unroll
+        for (int i = 0; i < 19; ++i) asm volatile("prefetch.global.L2 [%0];" ::"l"(f + i * qs + na));
+    }
     bool bad = false;
     if (x < L.n[0] && y < L.n[1]) bad = lattice_node<T, ODD, REC, MODE>(L, x, y, z, pbuf);
     // sticky instability flag, one atomic per warp at most
@@ -1284,8 +1295,13 @@ static void lattice_grid(const LbView &L, dim3 &grid, dim3 &block)
 template <typename T, bool ODD, bool REC>
 static void lattice_launch_t(const LbView &L, int mode, int pbuf, dim3 g, dim3 b, cudaStream_t s)
 {
-    if (mode == LAT_FAR) k_lattice<T, ODD, REC, LAT_FAR><<<g, b, 0, s>>>(L, pbuf);
-    else k_lattice<T, ODD, REC, LAT_FULL><<<g, b, 0, s>>>(L, pbuf);
+    // prefetch distance: the z-planes one wave of resident blocks covers
+    static int sms = 0;
+    if (sms == 0 && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess) sms = 1;
+    const long long wave = (long long)sms * (sizeof(T) == 4 ? 8 : 4), plane = (long long)g.x * g.y;
+    const int ahead = (int)((wave + plane - 1) / plane);
+    if (mode == LAT_FAR) k_lattice<T, ODD, REC, LAT_FAR><<<g, b, 0, s>>>(L, pbuf, ahead);
+    else k_lattice<T, ODD, REC, LAT_FULL><<<g, b, 0, s>>>(L, pbuf, ahead);
 }
 
 cudaError_t launch_lattice(const LbView &L, bool odd, bool record, int mode, int pbuf, cudaStream_t s)
