@@ -548,7 +548,9 @@ def run_ours(args):
     t_launch = lb_ms / lb_n * 1e-3 if lb_n else None
     achieved = BYTES_PER_NODE * far_nodes / t_launch / 1e9 if t_launch else None
     peak, peak_kind = measured_peaks()
-    launches = 3 * args.steps + (sim.steps_done // 100 - (sim.steps_done - args.steps) // 100)
+    # per step: force/spread, patch update, outside update, interpolation;
+    # plus one shape-record kernel every 100 steps
+    launches = 4 * args.steps + (sim.steps_done // 100 - (sim.steps_done - args.steps) // 100)
     sim.close()
 
     # end to end through the C-ABI with host buffers: the Sec. 3.2 loop, per

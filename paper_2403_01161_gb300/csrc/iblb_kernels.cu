@@ -446,12 +446,22 @@ __global__ void __launch_bounds__(256) k_lattice_near(LbView L, int buf)
 template <typename T, bool ODD>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
     k_lattice_batched(const __grid_constant__ LbGroup G, const int m0, const int b0,
-                      const int *__restrict__ blk_member, const int *__restrict__ blk_start, const int pbuf)
+                      const int *__restrict__ blk_member, const int *__restrict__ blk_start, const int pbuf,
+                      const int ahead)
 {
     const int mi = blk_member[b0 + blockIdx.x];
     const LbView &L = G.v[mi - m0];
     const int nx = L.n[0], ny = L.n[1];
     const int lin0 = (b0 + (int)blockIdx.x - blk_start[mi]) * 256;
+    // L2 prefetch of the node `ahead` positions further in the same member
+    // (about one resident wave of blocks later), as in k_lattice
+    const int la = lin0 + (int)threadIdx.x + ahead;
+    if (la < L.nodes) {
+        const T *f = static_cast<const T *>(L.f);
+        const int qs = (int)L.qs;
+#pragma unroll
+        for (int i = 0; i < 19; ++i) asm volatile("prefetch.global.L2 [%0];" ::"l"(f + i * qs + la));
+    }
     const int nxy = nx * ny;
     const int z0 = lin0 / nxy;
     const int rem = lin0 - z0 * nxy;
@@ -1463,6 +1473,10 @@ cudaError_t launch_ensemble_step(const EnsembleView &E, long long step, cudaStre
         const int nxt = (int)((step + 1) % 3);  // patch buffer of the next step
         bool recentre = false;
         for (int k = m0; k < m1; ++k) recentre = recentre || E.lv[k].recentre != 0;
+        // prefetch distance of the batched lattice kernel: one wave of resident blocks
+        static int sms = 0;
+        if (sms == 0 && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess) sms = 1;
+        const int ahead = sms * (E.precision == IBL_FP64 ? 2 : 4) * 256;
         if (recentre)
             k_centre_batched<<<dim3(kCentreBlocks, m1 - m0), kCentreThreads, 0, s>>>(lg, mg, pbuf);
         int nt_max = 0;
@@ -1471,13 +1485,13 @@ cudaError_t launch_ensemble_step(const EnsembleView &E, long long step, cudaStre
         if (E.precision == IBL_FP64) {
             k_spread_batched<double>
                 <<<nb, kIbThreads, 0, s>>>(lg, mg, m0, nb0, E.node_member, E.node_start_d, nxt);
-            if (odd) k_lattice_batched<double, true><<<lbn, 256, 0, s>>>(lg, m0, lb0, E.lat_member, E.lat_start_d, pbuf);
-            else k_lattice_batched<double, false><<<lbn, 256, 0, s>>>(lg, m0, lb0, E.lat_member, E.lat_start_d, pbuf);
+            if (odd) k_lattice_batched<double, true><<<lbn, 256, 0, s>>>(lg, m0, lb0, E.lat_member, E.lat_start_d, pbuf, ahead);
+            else k_lattice_batched<double, false><<<lbn, 256, 0, s>>>(lg, m0, lb0, E.lat_member, E.lat_start_d, pbuf, ahead);
             k_interp_batched<double><<<nb, kIbThreads, 0, s>>>(lg, mg, m0, nb0, E.node_member, E.node_start_d);
         } else {
             k_spread_batched<float><<<nb, kIbThreads, 0, s>>>(lg, mg, m0, nb0, E.node_member, E.node_start_d, nxt);
-            if (odd) k_lattice_batched<float, true><<<lbn, 256, 0, s>>>(lg, m0, lb0, E.lat_member, E.lat_start_d, pbuf);
-            else k_lattice_batched<float, false><<<lbn, 256, 0, s>>>(lg, m0, lb0, E.lat_member, E.lat_start_d, pbuf);
+            if (odd) k_lattice_batched<float, true><<<lbn, 256, 0, s>>>(lg, m0, lb0, E.lat_member, E.lat_start_d, pbuf, ahead);
+            else k_lattice_batched<float, false><<<lbn, 256, 0, s>>>(lg, m0, lb0, E.lat_member, E.lat_start_d, pbuf, ahead);
             k_interp_batched<float><<<nb, kIbThreads, 0, s>>>(lg, mg, m0, nb0, E.node_member, E.node_start_d);
         }
         k_advance_batched<<<1, kGroup, 0, s>>>(lg, m1 - m0);
