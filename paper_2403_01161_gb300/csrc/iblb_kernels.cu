@@ -575,18 +575,18 @@ __device__ void patch_from_rows(const LbView &L, const MeshView &M, int buf)
 // otherwise each lane evaluates it for its triangle (three times per
 // triangle in all, but one kernel boundary fewer on the droplet chain of a
 // single droplet, which is latency bound).
-template <typename T, bool STORED>
+template <typename T, bool STORED, int LANES>
 __device__ __forceinline__ void spread_body(const LbView &L, const MeshView &M, const int blk, const int next_buf)
 {
     if (blk == 0 && threadIdx.x < 32) patch_from_rows(L, M, next_buf);
-    const int gid = blk * kFwdNodesPerBlock + threadIdx.x / kFwdLanes;
-    const int lane = threadIdx.x % kFwdLanes;
+    const int gid = blk * (kIbThreads / LANES) + threadIdx.x / LANES;
+    const int lane = threadIdx.x % LANES;
     const bool valid = gid < M.nv;
     const int i = valid ? gid : M.nv - 1;
     const L2Keep K;
     double F[3] = {0.0, 0.0, 0.0};
     const int k0 = K.ld(M.n2t_ptr + i), k1 = K.ld(M.n2t_ptr + i + 1);
-    for (int k = k0 + lane; k < k1; k += kFwdLanes) {
+    for (int k = k0 + lane; k < k1; k += LANES) {
         const int e = K.ld(M.n2t + k);
         const int t = e / 3;
         double m[3];
@@ -599,14 +599,14 @@ __device__ __forceinline__ void spread_body(const LbView &L, const MeshView &M, 
         tri_force_m(M, t, e - 3 * t, m, g, K);
         for (int a = 0; a < 3; ++a) F[a] += g[a];
     }
-    for (int o = kFwdLanes / 2; o > 0; o >>= 1)
-        for (int a = 0; a < 3; ++a) F[a] += __shfl_xor_sync(0xffffffffu, F[a], o, kFwdLanes);
+    for (int o = LANES / 2; o > 0; o >>= 1)
+        for (int a = 0; a < 3; ++a) F[a] += __shfl_xor_sync(0xffffffffu, F[a], o, LANES);
     if (valid && lane == 0) {
         M.fn[3 * i] = F[0];
         M.fn[3 * i + 1] = F[1];
         M.fn[3 * i + 2] = F[2];
     }
-    const NodeStencil S = node_stencil<kFwdLanes>(L, M.r + 3 * i, lane, &K);
+    const NodeStencil S = node_stencil<LANES>(L, M.r + 3 * i, lane, &K);
     if (!valid) return;
     if (!S.ok) {
         if (lane == 0) atomicOr(&L.ctl->err, IBL_ERRBIT_WALL);
@@ -617,10 +617,10 @@ __device__ __forceinline__ void spread_body(const LbView &L, const MeshView &M, 
     const int nx = L.n[0], nxy = L.n[0] * L.n[1], nodes = L.nodes;
     T *force = static_cast<T *>(L.force);
     const T Fx = T(F[0]), Fy = T(F[1]), Fz = T(F[2]);
-    // the lane's (y, z) rows r = lane, lane + kFwdLanes, ...: (b, c) = (r & 3, r >> 2)
+    // the lane's (y, z) rows r = lane, lane + LANES, ...: (b, c) = (r & 3, r >> 2)
 #pragma unroll
-    for (int q = 0; q < 16 / kFwdLanes; ++q) {
-        const int r = lane + kFwdLanes * q, b = r & 3, c = r >> 2;
+    for (int q = 0; q < 16 / LANES; ++q) {
+        const int r = lane + LANES * q, b = r & 3, c = r >> 2;
         T w[4], wy, wz;
         stencil_weights<T>(S, b, c, w, wy, wz);
         const int row =
@@ -650,10 +650,10 @@ __global__ void __launch_bounds__(128) k_tri_moment_batched(const __grid_constan
     for (int a = 0; a < 3; ++a) K.st(M.tm + 3 * t + a, m[a]);
 }
 
-template <typename T>
+template <typename T, int LANES>
 __global__ void __launch_bounds__(128) k_spread(LbView L, MeshView M, int next_buf)
 {
-    spread_body<T, false>(L, M, blockIdx.x, next_buf);
+    spread_body<T, false, LANES>(L, M, blockIdx.x, next_buf);
 }
 
 // Re-centring (Sec. 3.2: the linearisation is centred on the droplet's
@@ -716,25 +716,25 @@ __global__ void __launch_bounds__(kCentreThreads)
     centre_of_mass(LG.v[blockIdx.y], MG.v[blockIdx.y], blockIdx.x, buf);
 }
 
-template <typename T>
+template <typename T, int LANES>
 __device__ __forceinline__ void interp_body(const LbView &L, const MeshView &M, const int blk, const int nblk)
 {
-    const int gid = blk * kFwdNodesPerBlock + threadIdx.x / kFwdLanes;
-    const int lane = threadIdx.x % kFwdLanes;
+    const int gid = blk * (kIbThreads / LANES) + threadIdx.x / LANES;
+    const int lane = threadIdx.x % LANES;
     const bool valid = gid < M.nv;
     const int i = valid ? gid : M.nv - 1;
     const L2Keep K;
-    const NodeStencil S = node_stencil<kFwdLanes>(L, M.r + 3 * i, lane, &K);
+    const NodeStencil S = node_stencil<LANES>(L, M.r + 3 * i, lane, &K);
     T v[3] = {T(0), T(0), T(0)};
     if (S.ok) {
         const bool perx = L.bc[0] == IBL_BC_PERIODIC, pery = L.bc[1] == IBL_BC_PERIODIC,
                    perz = L.bc[2] == IBL_BC_PERIODIC;
         const int nx = L.n[0], nxy = L.n[0] * L.n[1], nodes = L.nodes;
         const T *vel = static_cast<const T *>(L.vel);
-        // the lane's (y, z) rows r = lane, lane + kFwdLanes, ...: (b, c) = (r & 3, r >> 2)
+        // the lane's (y, z) rows r = lane, lane + LANES, ...: (b, c) = (r & 3, r >> 2)
 #pragma unroll
-        for (int q = 0; q < 16 / kFwdLanes; ++q) {
-            const int r = lane + kFwdLanes * q, b = r & 3, c = r >> 2;
+        for (int q = 0; q < 16 / LANES; ++q) {
+            const int r = lane + LANES * q, b = r & 3, c = r >> 2;
             T w[4], wy, wz;
             stencil_weights<T>(S, b, c, w, wy, wz);
             const int row =
@@ -749,8 +749,8 @@ __device__ __forceinline__ void interp_body(const LbView &L, const MeshView &M, 
             }
         }
     }
-    for (int o = kFwdLanes / 2; o > 0; o >>= 1)
-        for (int a = 0; a < 3; ++a) v[a] += __shfl_xor_sync(0xffffffffu, v[a], o, kFwdLanes);
+    for (int o = LANES / 2; o > 0; o >>= 1)
+        for (int a = 0; a < 3; ++a) v[a] += __shfl_xor_sync(0xffffffffu, v[a], o, LANES);
     const bool have = valid && lane == 0;
     double r[3] = {0.0, 0.0, 0.0};
     if (have) {
@@ -773,9 +773,9 @@ __device__ __forceinline__ void interp_body(const LbView &L, const MeshView &M, 
     __shared__ double smn[3][4], smx[3][4];
     const int wlane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int a = 0; a < 3; ++a) {
-        // lanes 0, kFwdLanes, 2 kFwdLanes, ... hold the warp's nodes
+        // lanes 0, LANES, 2 LANES, ... hold the warp's nodes
         double mn = have ? r[a] : 1e300, mx = have ? r[a] : -1e300;
-        for (int o = kFwdLanes; o < 32; o <<= 1) {
+        for (int o = LANES; o < 32; o <<= 1) {
             mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
             mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         }
@@ -799,10 +799,10 @@ __device__ __forceinline__ void interp_body(const LbView &L, const MeshView &M, 
     }
 }
 
-template <typename T>
+template <typename T, int LANES>
 __global__ void __launch_bounds__(128) k_interp(LbView L, MeshView M)
 {
-    interp_body<T>(L, M, blockIdx.x, gridDim.x);
+    interp_body<T, LANES>(L, M, blockIdx.x, gridDim.x);
 }
 
 // Closes the step of every member of a group (one thread per member).
@@ -822,7 +822,7 @@ __global__ void __launch_bounds__(128)
                      const int next_buf)
 {
     const int mi = blk_member[b0 + blockIdx.x];
-    spread_body<T, true>(LG.v[mi - m0], MG.v[mi - m0], b0 + (int)blockIdx.x - blk_start[mi], next_buf);
+    spread_body<T, true, kFwdLanes>(LG.v[mi - m0], MG.v[mi - m0], b0 + (int)blockIdx.x - blk_start[mi], next_buf);
 }
 
 template <typename T>
@@ -831,7 +831,7 @@ __global__ void __launch_bounds__(128)
                      const int b0, const int *__restrict__ blk_member, const int *__restrict__ blk_start)
 {
     const int mi = blk_member[b0 + blockIdx.x];
-    interp_body<T>(LG.v[mi - m0], MG.v[mi - m0], b0 + (int)blockIdx.x - blk_start[mi],
+    interp_body<T, kFwdLanes>(LG.v[mi - m0], MG.v[mi - m0], b0 + (int)blockIdx.x - blk_start[mi],
                    blk_start[mi + 1] - blk_start[mi]);
 }
 
@@ -1372,11 +1372,28 @@ cudaError_t launch_convert_frames(const LbView &L, int k0, int k1, cudaStream_t 
     return cudaGetLastError();
 }
 
+// Lanes per mesh node of a single droplet's force/spread and interpolation
+// kernels.  A small mesh (one 16-lane block per SM or fewer) takes 16 lanes:
+// its step is the droplet chain's latency, and more, shorter threads shorten
+// it.  A larger mesh takes kFwdLanes: there the lattice update sets the step,
+// and half the threads hold half the SM slots the chain takes from it.
+static int fwd_lanes(const MeshView &M)
+{
+    static int sms = 0;
+    if (sms == 0 && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess) sms = 1;
+    return (long long)M.nv * 16 <= (long long)sms * kIbThreads ? 16 : kFwdLanes;
+}
+
 cudaError_t launch_spread(const LbView &L, const MeshView &M, int next_buf, cudaStream_t s, int prio)
 {
-    const dim3 g(blocks_for((long long)M.nv * kFwdLanes, kIbThreads)), b(kIbThreads);
-    if (L.precision == IBL_FP64) return launch_p(k_spread<double>, g, b, s, prio, L, M, next_buf);
-    return launch_p(k_spread<float>, g, b, s, prio, L, M, next_buf);
+    const int lanes = fwd_lanes(M);
+    const dim3 g(blocks_for((long long)M.nv * lanes, kIbThreads)), b(kIbThreads);
+    if (lanes == 16) {
+        if (L.precision == IBL_FP64) return launch_p(k_spread<double, 16>, g, b, s, prio, L, M, next_buf);
+        return launch_p(k_spread<float, 16>, g, b, s, prio, L, M, next_buf);
+    }
+    if (L.precision == IBL_FP64) return launch_p(k_spread<double, kFwdLanes>, g, b, s, prio, L, M, next_buf);
+    return launch_p(k_spread<float, kFwdLanes>, g, b, s, prio, L, M, next_buf);
 }
 
 cudaError_t launch_centre(const LbView &L, const MeshView &M, int buf, cudaStream_t s, int prio)
@@ -1386,9 +1403,14 @@ cudaError_t launch_centre(const LbView &L, const MeshView &M, int buf, cudaStrea
 
 cudaError_t launch_interp(const LbView &L, const MeshView &M, cudaStream_t s, int prio)
 {
-    const dim3 g(blocks_for((long long)M.nv * kFwdLanes, kIbThreads)), b(kIbThreads);
-    if (L.precision == IBL_FP64) return launch_p(k_interp<double>, g, b, s, prio, L, M);
-    return launch_p(k_interp<float>, g, b, s, prio, L, M);
+    const int lanes = fwd_lanes(M);
+    const dim3 g(blocks_for((long long)M.nv * lanes, kIbThreads)), b(kIbThreads);
+    if (lanes == 16) {
+        if (L.precision == IBL_FP64) return launch_p(k_interp<double, 16>, g, b, s, prio, L, M);
+        return launch_p(k_interp<float, 16>, g, b, s, prio, L, M);
+    }
+    if (L.precision == IBL_FP64) return launch_p(k_interp<double, kFwdLanes>, g, b, s, prio, L, M);
+    return launch_p(k_interp<float, kFwdLanes>, g, b, s, prio, L, M);
 }
 
 cudaError_t launch_regularize(const LbView &L, const MeshView &M, const RegParams &p, int buf, cudaStream_t s,
