@@ -1283,6 +1283,15 @@ __global__ void __launch_bounds__(256) k_observables(LbView L, MeshView M)
 // launchers
 static inline unsigned blocks_for(long long n, int b) { return (unsigned)((n + b - 1) / b); }
 
+// Multiprocessors of the current device (read once; launch shapes and
+// prefetch distances are sized by it).
+static int sm_count()
+{
+    static int sms = 0;
+    if (sms == 0 && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess) sms = 1;
+    return sms;
+}
+
 cudaError_t launch_init(const LbView &L, cudaStream_t s)
 {
     const unsigned g = blocks_for(L.nodes, 256);
@@ -1306,9 +1315,7 @@ template <typename T, bool ODD, bool REC>
 static void lattice_launch_t(const LbView &L, int mode, int pbuf, dim3 g, dim3 b, cudaStream_t s)
 {
     // prefetch distance: the z-planes one wave of resident blocks covers
-    static int sms = 0;
-    if (sms == 0 && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess) sms = 1;
-    const long long wave = (long long)sms * (sizeof(T) == 4 ? 8 : 4), plane = (long long)g.x * g.y;
+    const long long wave = (long long)sm_count() * (sizeof(T) == 4 ? 8 : 4), plane = (long long)g.x * g.y;
     const int ahead = (int)((wave + plane - 1) / plane);
     if (mode == LAT_FAR) k_lattice<T, ODD, REC, LAT_FAR><<<g, b, 0, s>>>(L, pbuf, ahead);
     else k_lattice<T, ODD, REC, LAT_FULL><<<g, b, 0, s>>>(L, pbuf, ahead);
@@ -1379,9 +1386,7 @@ cudaError_t launch_convert_frames(const LbView &L, int k0, int k1, cudaStream_t 
 // and half the threads hold half the SM slots the chain takes from it.
 static int fwd_lanes(const MeshView &M)
 {
-    static int sms = 0;
-    if (sms == 0 && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess) sms = 1;
-    return (long long)M.nv * 16 <= (long long)sms * kIbThreads ? 16 : kFwdLanes;
+    return (long long)M.nv * 16 <= (long long)sm_count() * kIbThreads ? 16 : kFwdLanes;
 }
 
 cudaError_t launch_spread(const LbView &L, const MeshView &M, int next_buf, cudaStream_t s, int prio)
@@ -1496,9 +1501,7 @@ cudaError_t launch_ensemble_step(const EnsembleView &E, long long step, cudaStre
         bool recentre = false;
         for (int k = m0; k < m1; ++k) recentre = recentre || E.lv[k].recentre != 0;
         // prefetch distance of the batched lattice kernel: one wave of resident blocks
-        static int sms = 0;
-        if (sms == 0 && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess) sms = 1;
-        const int ahead = sms * (E.precision == IBL_FP64 ? 2 : 4) * 256;
+        const int ahead = sm_count() * (E.precision == IBL_FP64 ? 2 : 4) * 256;
         if (recentre)
             k_centre_batched<<<dim3(kCentreBlocks, m1 - m0), kCentreThreads, 0, s>>>(lg, mg, pbuf);
         int nt_max = 0;

@@ -86,6 +86,7 @@ def test_argument_validation(lib):
     assert lib.ibl_icosphere_size(5, ctypes.byref(nv), ctypes.byref(nt)) == L.IBL_OK
     assert (nv.value, nt.value) == (10242, 20480)
     assert lib.ibl_icosphere_size(-1, ctypes.byref(nv), ctypes.byref(nt)) == L.IBL_EINVAL
+    assert lib.ibl_set_recentring(None, 1) == L.IBL_EINVAL  # no mesh handle
     msz = ctypes.c_size_t()
     assert lib.ibl_mesh_workspace_size(2562, 5120, ctypes.byref(msz)) == L.IBL_OK
     assert msz.value > 2562 * 3 * 8 * 5
