@@ -568,9 +568,9 @@ __device__ void patch_from_rows(const LbView &L, const MeshView &M, int buf)
 
 // Nodal force F_i = -sigma dA/dx_i (Eq. (pi_drop)) gathered over the
 // triangles around node i, then spread with the 4-point delta
-// (Eq. (ibm_force_d)(a)) by atomic adds into the Eulerian force.  Sixteen
+// (Eq. (ibm_force_d)(a)) by atomic adds into the Eulerian force.  LANES
 // lanes per node: the lanes split the incident triangles (reduced with
-// shuffles), then each lane adds one x-row of four stencil points.
+// shuffles), then each lane adds 16 / LANES x-rows of four stencil points.
 // STORED: m_t comes from M.tm (written by k_tri_moment_batched just before);
 // otherwise each lane evaluates it for its triangle (three times per
 // triangle in all, but one kernel boundary fewer on the droplet chain of a
