@@ -27,6 +27,7 @@ from .oracle import (  # noqa: F401
     mesh_quality,
     enclosed_volume,
     restore_volume,
+    indicator,
     OracleSim,
     BC_ZOU_HE,
     BC_PERIODIC,

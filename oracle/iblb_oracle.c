@@ -30,6 +30,8 @@
  *   regularisation ........... Sec. 3.3, Eqs. (extended laplacian smoothing),
  *                              (HC_algo_full), (distanceregularization)
  *   frame schedule ........... Sec. 3.2, the four-step trajectory loop
+ *   viscosity ratio chi ...... Sec. 2 (droplet viscosity chi mu): tau inside the
+ *                              droplet from an even-odd ray count over the mesh
  *
  * Parity status: every function is pinned by tests/test_oracle_*.py against
  * closed forms, invariants or brute force, except the edge and corner rules
@@ -415,6 +417,10 @@ typedef struct {
      * centre of mass at the start of each step instead of the box centre */
     int recentre;
     double centre[3];
+    /* viscosity ratio: tau_in inside the droplet (chi != 1 only) */
+    int visc;
+    double tau_in;
+    unsigned char *ind; /* [nn] 1 inside the droplet at the current step */
 } orc_sim;
 
 static size_t nid(const orc_sim *s, int x, int y, int z)
@@ -486,6 +492,7 @@ void orc_sim_destroy(orc_sim *s)
     if (!s) return;
     free(s->f); free(s->fn); free(s->F); free(s->rho); free(s->u); free(s->frames);
     free(s->r); free(s->Fn); free(s->tri); free(s->nb_ptr); free(s->nb_idx);
+    free(s->ind);
     free(s);
 }
 
@@ -519,6 +526,70 @@ void orc_sim_set_regularization_volume(orc_sim *s, int keep) { s->reg_keep_volum
 
 /* Re-centring on (1) or off (0); needs a droplet mesh to take effect. */
 void orc_sim_set_recentring(orc_sim *s, int on) { s->recentre = on; }
+
+/* ---------------------------------------------------------------------------
+ * Viscosity ratio (Sec. 2: the droplet phase has viscosity chi mu, the carrier
+ * mu).  With equal densities the relaxation time inside the droplet is
+ * tau_in = 1/2 + chi (tau - 1/2).  Inside is decided per lattice node by the
+ * even-odd rule on a vertical ray: node (x, y, z) is inside when the number
+ * of triangles crossed strictly above it is odd.  Triangle (a, b, c) is
+ * crossed above the node when q = (x + RAY_DX, y + RAY_DY) lies strictly
+ * inside its projection on the xy plane (all three edge functions of one
+ * sign) and its height over q, interpolated with the barycentric weights,
+ * exceeds z.  The fixed sub-lattice offsets keep the rays off the mesh's
+ * vertices and edges.  Every product and sum is a separate IEEE operation
+ * (this file is compiled without contraction), in the order written.
+ */
+static const double RAY_DX = 1.4142135623730951e-7, RAY_DY = 1.7320508075688772e-7;
+
+void orc_indicator(const int n[3], int nv, const double *r, int nt, const int *tri, unsigned char *ind)
+{
+    (void)nv;
+    const size_t nn = (size_t)n[0] * n[1] * n[2];
+    memset(ind, 0, nn);
+    for (int t = 0; t < nt; ++t) {
+        const double *a = r + 3 * tri[3 * t], *b = r + 3 * tri[3 * t + 1], *c = r + 3 * tri[3 * t + 2];
+        const double xmin = fmin(a[0], fmin(b[0], c[0])), xmax = fmax(a[0], fmax(b[0], c[0]));
+        const double ymin = fmin(a[1], fmin(b[1], c[1])), ymax = fmax(a[1], fmax(b[1], c[1]));
+        int x0 = (int)ceil(xmin - RAY_DX), x1 = (int)floor(xmax - RAY_DX);
+        int y0 = (int)ceil(ymin - RAY_DY), y1 = (int)floor(ymax - RAY_DY);
+        if (x0 < 0) x0 = 0;
+        if (y0 < 0) y0 = 0;
+        if (x1 > n[0] - 1) x1 = n[0] - 1;
+        if (y1 > n[1] - 1) y1 = n[1] - 1;
+        for (int y = y0; y <= y1; ++y)
+            for (int x = x0; x <= x1; ++x) {
+                const double qx = (double)x + RAY_DX, qy = (double)y + RAY_DY;
+                const double e0 = (b[0] - a[0]) * (qy - a[1]) - (b[1] - a[1]) * (qx - a[0]);
+                const double e1 = (c[0] - b[0]) * (qy - b[1]) - (c[1] - b[1]) * (qx - b[0]);
+                const double e2 = (a[0] - c[0]) * (qy - c[1]) - (a[1] - c[1]) * (qx - c[0]);
+                const int inside = (e0 > 0.0 && e1 > 0.0 && e2 > 0.0) || (e0 < 0.0 && e1 < 0.0 && e2 < 0.0);
+                if (!inside) continue;
+                const double zc = ((e1 * a[2] + e2 * b[2]) + e0 * c[2]) / ((e0 + e1) + e2);
+                for (int z = 0; z < n[2]; ++z)
+                    if ((double)z < zc) ind[(size_t)x + (size_t)n[0] * ((size_t)y + (size_t)n[1] * z)] ^= 1;
+            }
+    }
+}
+
+/* chi = 1 switches the viscosity ratio off.  Needs a mesh and Zou-He walls on
+ * every axis (a vertical ray must not wrap); returns 0 otherwise. */
+int orc_sim_set_viscosity_ratio(orc_sim *s, double chi)
+{
+    if (!(chi > 0.0) || s->nv <= 0) return 0;
+    for (int a = 0; a < 3; ++a)
+        if (s->bc[a] != BC_ZOU_HE) return 0;
+    s->visc = chi != 1.0;
+    s->tau_in = 0.5 + chi * (s->tau - 0.5);
+    if (!s->ind) s->ind = (unsigned char *)calloc(s->nn, 1);
+    return 1;
+}
+
+void orc_sim_get_indicator(const orc_sim *s, unsigned char *out)
+{
+    if (s->ind) memcpy(out, s->ind, s->nn);
+    else memset(out, 0, s->nn);
+}
 
 /* Centre of the linear boundary field used by the last step. */
 void orc_sim_get_centre(const orc_sim *s, double c[3])
@@ -619,6 +690,7 @@ static void lattice_update(orc_sim *s)
                     wall_velocity(s, A, x, y, z, uw);
                     orc_bc_node(f, side, uw, s->rule);
                 }
+                const double tau_x = (s->visc && s->ind[id]) ? s->tau_in : tau;
                 double Fx[3] = {s->F[id], s->F[s->nn + id], s->F[2 * s->nn + id]};
                 double rho = 0.0, j[3] = {0, 0, 0};
                 for (int i = 0; i < Q; ++i) {
@@ -632,9 +704,9 @@ static void lattice_update(orc_sim *s)
                 for (int a = 0; a < 3; ++a) s->u[a * s->nn + id] = u[a];
                 double feq[Q], S[Q];
                 orc_equilibrium(rho, u, feq);
-                orc_guo_source(tau, u, Fx, S);
+                orc_guo_source(tau_x, u, Fx, S);
                 for (int i = 0; i < Q; ++i) {
-                    double fs = f[i] - (f[i] - feq[i]) / tau + S[i];
+                    double fs = f[i] - (f[i] - feq[i]) / tau_x + S[i];
                     int d[3];
                     int inside = 1;
                     for (int a = 0; a < 3; ++a) {
@@ -675,6 +747,7 @@ int orc_sim_step(orc_sim *s, long nsteps)
 {
     for (long k = 0; k < nsteps; ++k) {
         step_centre(s);
+        if (s->visc) orc_indicator(s->n, s->nv, s->r, s->nt, s->tri, s->ind);
         if (s->nv > 0) spread(s);
         else memset(s->F, 0, sizeof(double) * 3 * s->nn);
         lattice_update(s);

@@ -70,6 +70,10 @@ def lib():
             L.orc_restore_volume.argtypes = [ctypes.c_int, _D, ctypes.c_int, _I, ctypes.c_double]
             L.orc_sim_set_regularization_volume.argtypes = [ctypes.c_void_p, ctypes.c_int]
             L.orc_sim_set_recentring.argtypes = [ctypes.c_void_p, ctypes.c_int]
+            L.orc_sim_set_viscosity_ratio.argtypes = [ctypes.c_void_p, ctypes.c_double]
+            L.orc_sim_set_viscosity_ratio.restype = ctypes.c_int
+            L.orc_sim_get_indicator.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+            L.orc_indicator.argtypes = [_I, ctypes.c_int, _D, ctypes.c_int, _I, ctypes.c_void_p]
             L.orc_sim_get_centre.argtypes = [ctypes.c_void_p, _D]
             L.orc_sim_create.argtypes = [_I, _I, ctypes.c_double, ctypes.c_int, _D, ctypes.c_int,
                                          ctypes.c_int]
@@ -163,6 +167,18 @@ def enclosed_volume(r, tris):
     c = np.zeros(3)
     lib().orc_enclosed_volume(x.shape[0], _dp(x), t.shape[0], _ip(t), _dp(V), _dp(c))
     return float(V[0]), c
+
+
+def indicator(n, r, tris):
+    """1 at the lattice nodes of an (nx, ny, nz) box that lie inside the
+    closed mesh by the even-odd rule on vertical rays (see the C oracle's
+    orc_indicator), as an (nz, ny, nx) uint8 array."""
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    t = np.ascontiguousarray(tris, dtype=np.int32)
+    nn = np.array(n, dtype=np.int32)
+    out = np.zeros(int(np.prod(n)), dtype=np.uint8)
+    lib().orc_indicator(_ip(nn), r.shape[0], _dp(r), t.shape[0], _ip(t), out.ctypes.data)
+    return out.reshape(n[2], n[1], n[0])
 
 
 def restore_volume(r, tris, V_target):
@@ -379,6 +395,21 @@ class OracleSim:
         centre of mass (volume centroid at the start of the step) instead of
         the box centre (Sec. 3.2)."""
         self.L.orc_sim_set_recentring(self.h, 1 if on else 0)
+
+    def set_viscosity_ratio(self, chi):
+        """Droplet viscosity chi times the carrier's (Sec. 2): tau inside the
+        droplet = 1/2 + chi (tau - 1/2), inside decided per node by the
+        even-odd ray rule of `indicator`.  Needs the mesh and Zou-He walls on
+        every axis."""
+        if not self.L.orc_sim_set_viscosity_ratio(self.h, float(chi)):
+            raise ValueError("viscosity ratio needs chi > 0, a mesh and Zou-He walls on every axis")
+
+    def indicator(self):
+        """Inside-the-droplet flags used by the last step, (nz, ny, nx) uint8."""
+        out = np.zeros(self.nn, dtype=np.uint8)
+        self.L.orc_sim_get_indicator(self.h, out.ctypes.data)
+        nx, ny, nz = self.n
+        return out.reshape(nz, ny, nx)
 
     def centre(self):
         """Centre of the boundary field used by the last step."""
