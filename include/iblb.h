@@ -192,6 +192,20 @@ int ibl_set_regularization_keep_volume(ibl_mesh *m, int keep);
  * is not attached.  Synchronises the lattice's stream. */
 int ibl_set_recentring(ibl_mesh *m, int on);
 
+/* Viscosity ratio (Sec. 2: the droplet phase has viscosity chi mu, the
+ * carrier mu; the paper's runs have chi = 1).  Each step, the nodes inside
+ * the droplet relax with tau_in = 1/2 + chi (tau - 1/2), the others with
+ * tau.  Inside is decided per lattice node by the even-odd rule on a
+ * vertical ray: a node is inside when an odd number of mesh triangles lie
+ * above it, a triangle counting when the point (x + 1.4142135623730951e-7,
+ * y + 1.7320508075688772e-7) falls strictly inside its projection on the xy
+ * plane and its height there exceeds z (IEEE operations, no contraction).
+ * chi = 1 switches it off.  IBL_EINVAL if chi is not finite and positive,
+ * the mesh is not attached, or an axis is periodic.  The adjoint and the
+ * ensemble refuse a lattice with chi != 1.  Synchronises the lattice's
+ * stream. */
+int ibl_set_viscosity_ratio(ibl_mesh *m, double chi);
+
 /* Synchronising: *count = regularisations performed so far (triggered
  * scheduled ones and ibl_regularize_now calls), *mesh_quality = q measured
  * at the latest regularisation check (0 before the first).  Either pointer

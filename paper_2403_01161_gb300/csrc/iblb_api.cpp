@@ -37,7 +37,7 @@ int cuda_fail(cudaError_t e, const char *what)
 inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
 struct Layout {
-    size_t ctl = 0, frames = 0, frames_t = 0, f = 0, force = 0, vel = 0, rec = 0, total = 0;
+    size_t ctl = 0, frames = 0, frames_t = 0, f = 0, force = 0, vel = 0, rec = 0, ind = 0, total = 0;
 };
 
 long long pop_stride(long long nodes) { return (nodes + 63) / 64 * 64; }
@@ -65,6 +65,7 @@ bool lb_layout(const ibl_lb_params *p, int n_frames, Layout &L)
     L.force = take(es * 3 * (size_t)nodes);
     L.vel = take(es * 3 * (size_t)nodes);
     L.rec = p->record_fields ? take(es * 7 * (size_t)nodes) : 0;
+    L.ind = take(((size_t)nodes + 3) / 4 * 4);  // inside flags, one byte per node
     L.total = off;
     return true;
 }
@@ -272,6 +273,9 @@ int one_step(ibl_lb *lb, bool record, cudaStream_t sL, cudaStream_t sH)
         e = iblb::launch_centre(lb->v, m->v, pbuf, sH, lb->hi_prio);
         if (e == cudaSuccess) e = cudaEventRecord(evCentre, sH);
     }
+    // with a viscosity ratio, the inside flags of this step's patch nodes
+    // (read and cleared by the patch update below)
+    if (e == cudaSuccess && lb->v.visc) e = iblb::launch_indicator(lb->v, m->v, pbuf, sH, lb->hi_prio);
     const int ps = prof_begin(lb, PROF_SPREAD, sH);
     if (e == cudaSuccess) e = iblb::launch_spread(lb->v, m->v, pnext, sH, lb->hi_prio);
     prof_end(lb, ps, sH);
@@ -913,6 +917,10 @@ int ibl_lb_create(const ibl_lb_params *p, const double *A_frames, int n_frames, 
     v.force = lb->ws + L.force;
     v.vel = lb->ws + L.vel;
     v.rec = p->record_fields ? lb->ws + L.rec : nullptr;
+    v.visc = 0;
+    v.omega_in = v.omega;
+    v.omega_in_f = v.omega_f;
+    v.ind = reinterpret_cast<unsigned int *>(lb->ws + L.ind);
     v.frames = reinterpret_cast<const double *>(lb->ws + L.frames);
     v.frames_t = lb->ws + L.frames_t;
     v.n_frames = n_frames;
@@ -933,6 +941,7 @@ int ibl_lb_create(const ibl_lb_params *p, const double *A_frames, int n_frames, 
     if (e == cudaSuccess) e = iblb::launch_convert_frames(v, 0, n_frames, lb->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(v.force, 0, es * 3 * nodes, lb->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(v.vel, 0, es * 3 * nodes, lb->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v.ind, 0, ((size_t)nodes + 3) / 4 * 4, lb->stream);
     if (e == cudaSuccess && v.rec) e = cudaMemsetAsync(v.rec, 0, es * 7 * nodes, lb->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(v.f, 0, es * 19 * v.qs, lb->stream);
     if (e == cudaSuccess) e = iblb::launch_init(v, lb->stream);
@@ -1028,8 +1037,25 @@ void ibl_mesh_destroy(ibl_mesh *m)
         drop_graph(m->lb);
         m->lb->mesh = nullptr;
         m->lb->v.recentre = 0;  // the centre came from this droplet
+        m->lb->v.visc = 0;      // and the inside flags
     }
     delete m;
+}
+
+int ibl_set_viscosity_ratio(ibl_mesh *m, double chi)
+{
+    if (!m || !m->lb) return fail(IBL_EINVAL, "the mesh is not attached to a lattice");
+    if (!(chi > 0.0) || !std::isfinite(chi)) return fail(IBL_EINVAL, "chi must be finite and > 0");
+    ibl_lb *lb = m->lb;
+    for (int a = 0; a < 3; ++a)
+        if (lb->v.bc[a] != IBL_BC_ZOU_HE) return fail(IBL_EINVAL, "a viscosity ratio needs Zou-He walls on every axis");
+    cudaStreamSynchronize(lb->stream);
+    const double tau = 1.0 / lb->v.omega, tau_in = 0.5 + chi * (tau - 0.5);
+    lb->v.visc = chi != 1.0 ? 1 : 0;
+    lb->v.omega_in = 1.0 / tau_in;
+    lb->v.omega_in_f = (float)(1.0 / tau_in);
+    drop_graph(lb);  // captured chunks hold the lattice view by value
+    return IBL_OK;
 }
 
 int ibl_set_recentring(ibl_mesh *m, int on)
@@ -1387,6 +1413,7 @@ int ibl_ensemble_create(int n, ibl_lb *const *members, void *workspace, size_t b
         if (lb->p.precision != m0->p.precision) return fail(IBL_EINVAL, "members differ in precision");
         if (lb->stream != m0->stream) return fail(IBL_EINVAL, "members are bound to different streams");
         if (lb->host_step != m0->host_step) return fail(IBL_EINVAL, "members are at different step counts");
+        if (lb->v.visc) return fail(IBL_EINVAL, "ensemble members need chi = 1");
         for (int j = 0; j < k; ++j)
             if (members[j] == lb) return fail(IBL_EINVAL, "a lattice appears twice");
         lv.push_back(lb->v);
@@ -1533,6 +1560,7 @@ int ibl_adjoint(ibl_lb *lb, long long n_steps, int K, void *workspace, size_t by
     if (lb->host_step != 0) return fail(IBL_EINVAL, "the adjoint starts from step 0");
     if (m->reg_every != 0) return fail(IBL_EINVAL, "the adjoint needs the regularisation switched off");
     if (lb->v.recentre) return fail(IBL_EINVAL, "the adjoint does not differentiate the re-centring");
+    if (lb->v.visc) return fail(IBL_EINVAL, "the adjoint needs chi = 1");
     if (!workspace || bytes < A.total) return fail(IBL_ENOMEM, "adjoint workspace too small");
     if (((uintptr_t)workspace & 255) != 0) return fail(IBL_EINVAL, "workspace must be 256-byte aligned");
     int st = ensure_streams(lb);

@@ -52,6 +52,10 @@ struct LbView {
     int n_frames;
     int n_hold;
     int recentre;       // 1: the boundary field is centred on the droplet's centre of mass (ctl->centre)
+    int visc;           // 1: viscosity ratio chi != 1, relaxation omega_in at nodes inside the droplet
+    double omega_in;    // 1 / tau_in, tau_in = 1/2 + chi (tau - 1/2)
+    float omega_in_f;
+    unsigned int *ind;  // [ceil(nodes / 4)] inside flags, one byte per node (set by the indicator kernel, cleared by the patch update)
     Ctl *ctl;
 };
 
@@ -139,6 +143,8 @@ constexpr int kFwdNodesPerBlock = 128 / kFwdLanes;
 // re-centring: the droplet's centre of mass at the current positions into ctl->centre[buf]
 constexpr int kCentreBlocks = 16;
 cudaError_t launch_centre(const LbView &L, const MeshView &M, int buf, cudaStream_t s, int prio = 0);
+// viscosity ratio: the inside flags of the patch nodes of step `buf` from the current positions
+cudaError_t launch_indicator(const LbView &L, const MeshView &M, int buf, cudaStream_t s, int prio = 0);
 cudaError_t launch_regularize(const LbView &L, const MeshView &M, const RegParams &p, int buf, cudaStream_t s,
                               int prio = 0);
 cudaError_t launch_observables(const LbView &L, const MeshView &M, cudaStream_t s, int prio = 0);

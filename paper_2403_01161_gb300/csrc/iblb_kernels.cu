@@ -285,7 +285,15 @@ __device__ __forceinline__ bool lattice_node(const LbView &L, const int x, const
         const T ux = (jx + T(0.5) * Fx) * ir, uy = (jy + T(0.5) * Fy) * ir, uz = (jz + T(0.5) * Fz) * ir;
         const T uu = ux * ux + uy * uy + uz * uz;
         bad = !(uu <= T(0.09)) || !(drho == drho);
-        const T om = sizeof(T) == 4 ? T(L.omega_f) : T(L.omega);
+        T om = sizeof(T) == 4 ? T(L.omega_f) : T(L.omega);
+        if constexpr (MODE == LAT_NEAR) {
+            // viscosity ratio: relaxation of the inside nodes (flags read and cleared)
+            if (L.visc) {
+                unsigned char *flag = reinterpret_cast<unsigned char *>(L.ind) + node;
+                if (*flag) om = sizeof(T) == 4 ? T(L.omega_in_f) : T(L.omega_in);
+                *flag = 0;
+            }
+        }
         const T fpre = T(1) - T(0.5) * om;
         const T uF = ux * Fx + uy * Fy + uz * Fz;
         const T base = T(1.5) * uu;
@@ -414,7 +422,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 4) k_lattice(LbView 
 
 // The patch nodes of the step (grid-stride over the patch box, x fastest).
 template <typename T, bool ODD, bool REC>
-__global__ void __launch_bounds__(256) k_lattice_near(LbView L, int buf)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_lattice_near(LbView L, int buf)
 {
     const Ctl *c = L.ctl;
     const int ex = c->patch_ext[buf][0] + 1, ey = c->patch_ext[buf][1] + 1, ez = c->patch_ext[buf][2] + 1;
@@ -707,6 +715,64 @@ __device__ __forceinline__ void centre_of_mass(const LbView &L, const MeshView &
 __global__ void __launch_bounds__(kCentreThreads) k_centre(LbView L, MeshView M, int buf)
 {
     centre_of_mass(L, M, blockIdx.x, buf);
+}
+
+// Viscosity ratio (Sec. 2: droplet viscosity chi mu): the inside flags of the
+// patch nodes of step `buf` by the even-odd rule on vertical rays.  One
+// thread per triangle (a, b, c): for every lattice column (x, y) of the patch
+// whose point q = (x + kRayDx, y + kRayDy) lies strictly inside the
+// triangle's xy projection (three edge functions of one sign), the height
+// z_c of the triangle over q comes from the barycentric weights, and the
+// flags of the patch nodes with z < z_c flip.  A node is inside when an odd
+// number of triangles lie above it.  The sub-lattice offsets keep the rays
+// off mesh vertices and edges; every operation is a separately rounded IEEE
+// one (no contraction), so the flags do not depend on the compiler.  The
+// patch covers the droplet, so every inside node is a patch node; the patch
+// update reads and clears the flags.
+constexpr double kRayDx = 1.4142135623730951e-7, kRayDy = 1.7320508075688772e-7;
+
+__device__ __forceinline__ double edge_fn(double ax, double ay, double bx, double by, double qx, double qy)
+{
+    return __dsub_rn(__dmul_rn(__dsub_rn(bx, ax), __dsub_rn(qy, ay)), __dmul_rn(__dsub_rn(by, ay), __dsub_rn(qx, ax)));
+}
+
+__global__ void __launch_bounds__(128) k_indicator(LbView L, MeshView M, int buf)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= M.nt) return;
+    const Ctl *c = L.ctl;
+    if (c->patch_ext[buf][0] < 0 || c->patch_ext[buf][1] < 0 || c->patch_ext[buf][2] < 0) return;
+    const int lo[3] = {c->patch_lo[buf][0], c->patch_lo[buf][1], c->patch_lo[buf][2]};
+    const int hi[3] = {lo[0] + c->patch_ext[buf][0], lo[1] + c->patch_ext[buf][1], lo[2] + c->patch_ext[buf][2]};
+    double p[3][3];
+    for (int k = 0; k < 3; ++k) {
+        const int v = M.tris[3 * t + k];
+        for (int a = 0; a < 3; ++a) p[k][a] = M.r[3 * v + a];
+    }
+    const double xmin = fmin(p[0][0], fmin(p[1][0], p[2][0])), xmax = fmax(p[0][0], fmax(p[1][0], p[2][0]));
+    const double ymin = fmin(p[0][1], fmin(p[1][1], p[2][1])), ymax = fmax(p[0][1], fmax(p[1][1], p[2][1]));
+    int x0 = (int)ceil(__dsub_rn(xmin, kRayDx)), x1 = (int)floor(__dsub_rn(xmax, kRayDx));
+    int y0 = (int)ceil(__dsub_rn(ymin, kRayDy)), y1 = (int)floor(__dsub_rn(ymax, kRayDy));
+    x0 = max(x0, max(lo[0], 0));
+    y0 = max(y0, max(lo[1], 0));
+    x1 = min(x1, min(hi[0], L.n[0] - 1));
+    y1 = min(y1, min(hi[1], L.n[1] - 1));
+    const int z_lo = max(lo[2], 0), z_hi = min(hi[2], L.n[2] - 1);
+    for (int y = y0; y <= y1; ++y)
+        for (int x = x0; x <= x1; ++x) {
+            const double qx = __dadd_rn((double)x, kRayDx), qy = __dadd_rn((double)y, kRayDy);
+            const double e0 = edge_fn(p[0][0], p[0][1], p[1][0], p[1][1], qx, qy);
+            const double e1 = edge_fn(p[1][0], p[1][1], p[2][0], p[2][1], qx, qy);
+            const double e2 = edge_fn(p[2][0], p[2][1], p[0][0], p[0][1], qx, qy);
+            const bool inside = (e0 > 0.0 && e1 > 0.0 && e2 > 0.0) || (e0 < 0.0 && e1 < 0.0 && e2 < 0.0);
+            if (!inside) continue;
+            const double num = __dadd_rn(__dadd_rn(__dmul_rn(e1, p[0][2]), __dmul_rn(e2, p[1][2])), __dmul_rn(e0, p[2][2]));
+            const double zc = __ddiv_rn(num, __dadd_rn(__dadd_rn(e0, e1), e2));
+            for (int z = z_lo; z <= z_hi && (double)z < zc; ++z) {
+                const int node = x + L.n[0] * (y + L.n[1] * z);
+                atomicXor(L.ind + (node >> 2), 1u << (8 * (node & 3)));
+            }
+        }
 }
 
 // Ensemble version: blockIdx.y is the member within the group.
@@ -1404,6 +1470,11 @@ cudaError_t launch_spread(const LbView &L, const MeshView &M, int next_buf, cuda
 cudaError_t launch_centre(const LbView &L, const MeshView &M, int buf, cudaStream_t s, int prio)
 {
     return launch_p(k_centre, dim3(kCentreBlocks), dim3(kCentreThreads), s, prio, L, M, buf);
+}
+
+cudaError_t launch_indicator(const LbView &L, const MeshView &M, int buf, cudaStream_t s, int prio)
+{
+    return launch_p(k_indicator, dim3(blocks_for(M.nt, 128)), dim3(128), s, prio, L, M, buf);
 }
 
 cudaError_t launch_interp(const LbView &L, const MeshView &M, cudaStream_t s, int prio)

@@ -160,6 +160,12 @@ class Sim:
         the box centre (Sec. 3.2)."""
         L.check(self.lib.ibl_set_recentring(self.mesh_h, 1 if on else 0))
 
+    def set_viscosity_ratio(self, chi: float):
+        """Droplet viscosity chi times the carrier's (Sec. 2): nodes inside the
+        droplet relax with tau_in = 1/2 + chi (tau - 1/2).  Needs Zou-He walls
+        on every axis; 1 switches it off."""
+        L.check(self.lib.ibl_set_viscosity_ratio(self.mesh_h, float(chi)))
+
     def regularization_stats(self):
         """(regularisations performed, mesh quality at the latest check)."""
         n = ctypes.c_int()
