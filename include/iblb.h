@@ -236,6 +236,24 @@ int ibl_set_graphs(ibl_lb *lb, int enable);
 /* Waits for the stream and reports the sticky device error bits as a status. */
 int ibl_sync(ibl_lb *lb);
 
+/* Checkpoint and resume (the paper's trajectories run for thousands of
+ * frames, Sec. 3.2).  ibl_save synchronises the lattice's stream and writes
+ * the whole dynamic state between steps to the file `path`: populations,
+ * control block (step count, frame slots, patch buffers, sticky error bits),
+ * frames, and, with a mesh, positions, nodal forces, bounding-box rows and
+ * the shape-record ring.  ibl_load restores such a file into a lattice (and
+ * its attached mesh) created with the same box, boundaries, precision, edge
+ * rule, record_fields, tau, frame count, steps per frame and mesh size; the
+ * step count comes from the file.  Settings made through the ibl_set_*
+ * calls (regularisation, readout period, re-centring, viscosity ratio,
+ * graphs) are not in the file: apply them to the resumed lattice as before.
+ * Load before putting the lattice into an ensemble.  IBL_EINVAL for a null
+ * argument, a file that cannot be opened, written or read in full, or a
+ * mismatch; IBL_ECUDA for a failed copy.  The file layout is this library
+ * version's own (a header, then the raw workspaces). */
+int ibl_save(ibl_lb *lb, const char *path);
+int ibl_load(ibl_lb *lb, const char *path);
+
 /* Number of steps enqueued so far. */
 long long ibl_steps_done(const ibl_lb *lb);
 

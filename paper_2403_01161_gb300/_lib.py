@@ -72,6 +72,8 @@ SIGNATURES = [
     ("ibl_set_regularization_keep_volume", ctypes.c_int, [_P, ctypes.c_int]),
     ("ibl_set_recentring", ctypes.c_int, [_P, ctypes.c_int]),
     ("ibl_set_viscosity_ratio", ctypes.c_int, [_P, ctypes.c_double]),
+    ("ibl_save", ctypes.c_int, [_P, ctypes.c_char_p]),
+    ("ibl_load", ctypes.c_int, [_P, ctypes.c_char_p]),
     ("ibl_step", ctypes.c_int, [_P, ctypes.c_longlong]),
     ("ibl_step_record", ctypes.c_int, [_P]),
     ("ibl_set_graphs", ctypes.c_int, [_P, ctypes.c_int]),

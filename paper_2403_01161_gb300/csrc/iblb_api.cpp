@@ -1208,6 +1208,113 @@ int ibl_sync(ibl_lb *lb)
 
 long long ibl_steps_done(const ibl_lb *lb) { return lb ? lb->host_step : -1; }
 
+namespace {
+
+// Checkpoint file: this header, the lattice workspace, then the mesh
+// workspace.  Between steps the workspaces hold the whole dynamic state (the
+// populations, the control block with its step counter, frame slots, patch
+// buffers and error bits, the frames, the mesh positions, forces, bounding-box
+// rows and shape-record ring); the Eulerian force, the velocity scratch and
+// the inside flags are zero or unused there.
+struct CkptHeader {
+    char magic[8];
+    int abi_version;
+    int n[3], bc[3];
+    int precision, edge_rule, record_fields;
+    int n_frames, steps_per_frame;
+    int mesh_nv, mesh_nt;  // -1 without a mesh
+    double tau;
+    long long host_step;
+    unsigned long long lb_bytes, mesh_bytes;
+};
+const char kCkptMagic[8] = {'I', 'B', 'L', 'B', 'C', 'K', 'P', '1'};
+
+CkptHeader ckpt_header(const ibl_lb *lb)
+{
+    CkptHeader h;
+    std::memset(&h, 0, sizeof h);
+    std::memcpy(h.magic, kCkptMagic, sizeof h.magic);
+    h.abi_version = IBL_ABI_VERSION;
+    for (int a = 0; a < 3; ++a) {
+        h.n[a] = lb->v.n[a];
+        h.bc[a] = lb->v.bc[a];
+    }
+    h.precision = lb->p.precision;
+    h.edge_rule = lb->p.edge_rule;
+    h.record_fields = lb->p.record_fields ? 1 : 0;
+    h.n_frames = lb->v.n_frames;
+    h.steps_per_frame = lb->v.n_hold;
+    h.mesh_nv = lb->mesh ? lb->mesh->v.nv : -1;
+    h.mesh_nt = lb->mesh ? lb->mesh->v.nt : -1;
+    h.tau = lb->p.tau;
+    h.host_step = lb->host_step;
+    h.lb_bytes = lb->lay.total;
+    h.mesh_bytes = lb->mesh ? lb->mesh->lay.total : 0;
+    return h;
+}
+
+char *mesh_ws(const ibl_mesh *m) { return reinterpret_cast<char *>(m->v.r) - m->lay.r; }
+
+}  // namespace
+
+int ibl_save(ibl_lb *lb, const char *path)
+{
+    if (!lb || !path) return fail(IBL_EINVAL, "null argument");
+    cudaError_t e = cudaStreamSynchronize(lb->stream);
+    if (e == cudaSuccess && lb->helper) e = cudaStreamSynchronize(lb->helper);
+    if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    const CkptHeader h = ckpt_header(lb);
+    std::vector<char> buf(h.lb_bytes + h.mesh_bytes);
+    e = cudaMemcpy(buf.data(), lb->ws, h.lb_bytes, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && lb->mesh)
+        e = cudaMemcpy(buf.data() + h.lb_bytes, mesh_ws(lb->mesh), h.mesh_bytes, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "checkpoint copy");
+    std::FILE *fp = std::fopen(path, "wb");
+    if (!fp) return fail(IBL_EINVAL, std::string("cannot open for writing: ") + path);
+    const bool ok = std::fwrite(&h, sizeof h, 1, fp) == 1 && std::fwrite(buf.data(), 1, buf.size(), fp) == buf.size();
+    const bool closed = std::fclose(fp) == 0;
+    if (!ok || !closed) return fail(IBL_EINVAL, std::string("cannot write: ") + path);
+    return IBL_OK;
+}
+
+int ibl_load(ibl_lb *lb, const char *path)
+{
+    if (!lb || !path) return fail(IBL_EINVAL, "null argument");
+    std::FILE *fp = std::fopen(path, "rb");
+    if (!fp) return fail(IBL_EINVAL, std::string("cannot open: ") + path);
+    CkptHeader h;
+    if (std::fread(&h, sizeof h, 1, fp) != 1) {
+        std::fclose(fp);
+        return fail(IBL_EINVAL, "not a checkpoint (short header)");
+    }
+    const CkptHeader mine = ckpt_header(lb);
+    const bool same = std::memcmp(h.magic, kCkptMagic, sizeof h.magic) == 0 && h.abi_version == mine.abi_version &&
+                      std::memcmp(h.n, mine.n, sizeof h.n) == 0 && std::memcmp(h.bc, mine.bc, sizeof h.bc) == 0 &&
+                      h.precision == mine.precision && h.edge_rule == mine.edge_rule &&
+                      h.record_fields == mine.record_fields && h.n_frames == mine.n_frames &&
+                      h.steps_per_frame == mine.steps_per_frame && h.mesh_nv == mine.mesh_nv &&
+                      h.mesh_nt == mine.mesh_nt && h.tau == mine.tau && h.lb_bytes == mine.lb_bytes &&
+                      h.mesh_bytes == mine.mesh_bytes && h.host_step >= 0;
+    if (!same) {
+        std::fclose(fp);
+        return fail(IBL_EINVAL, "checkpoint does not match this lattice and mesh (box, boundaries, precision, "
+                                "edge rule, tau, frames or mesh size)");
+    }
+    std::vector<char> buf(h.lb_bytes + h.mesh_bytes);
+    const bool ok = std::fread(buf.data(), 1, buf.size(), fp) == buf.size();
+    std::fclose(fp);
+    if (!ok) return fail(IBL_EINVAL, "truncated checkpoint");
+    cudaError_t e = cudaStreamSynchronize(lb->stream);
+    if (e == cudaSuccess && lb->helper) e = cudaStreamSynchronize(lb->helper);
+    if (e == cudaSuccess) e = cudaMemcpy(lb->ws, buf.data(), h.lb_bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && lb->mesh)
+        e = cudaMemcpy(mesh_ws(lb->mesh), buf.data() + h.lb_bytes, h.mesh_bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "checkpoint upload");
+    lb->host_step = h.host_step;
+    drop_graph(lb);  // chunks are captured for a phase of the step sequence
+    return IBL_OK;
+}
+
 int ibl_readout(ibl_mesh *m, ibl_observables *out)
 {
     if (!m || !m->lb || !out) return fail(IBL_EINVAL, "null argument");

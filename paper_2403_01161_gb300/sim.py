@@ -5,6 +5,7 @@ only marshals arguments and owns the torch buffers."""
 from __future__ import annotations
 
 import ctypes
+import os
 from typing import Optional, Sequence
 
 import numpy as np
@@ -189,6 +190,16 @@ class Sim:
 
     def sync(self):
         L.check(self.lib.ibl_sync(self.h))
+
+    def save(self, path: str):
+        """Write the dynamic state between steps to `path` (ibl_save)."""
+        L.check(self.lib.ibl_save(self.h, os.fsencode(path)))
+
+    def load(self, path: str):
+        """Resume from a file written by `save` for a Sim built the same way
+        (box, boundaries, precision, tau, frames, mesh size); settings such as
+        the regularisation schedule are applied to this Sim as before."""
+        L.check(self.lib.ibl_load(self.h, os.fsencode(path)))
 
     def status(self) -> int:
         """Synchronise and return the status code instead of raising."""

@@ -87,6 +87,8 @@ def test_argument_validation(lib):
     assert (nv.value, nt.value) == (10242, 20480)
     assert lib.ibl_icosphere_size(-1, ctypes.byref(nv), ctypes.byref(nt)) == L.IBL_EINVAL
     assert lib.ibl_set_recentring(None, 1) == L.IBL_EINVAL  # no mesh handle
+    assert lib.ibl_set_viscosity_ratio(None, 2.0) == L.IBL_EINVAL
+    assert lib.ibl_save(None, b"x") == L.IBL_EINVAL and lib.ibl_load(None, b"x") == L.IBL_EINVAL
     msz = ctypes.c_size_t()
     assert lib.ibl_mesh_workspace_size(2562, 5120, ctypes.byref(msz)) == L.IBL_OK
     assert msz.value > 2562 * 3 * 8 * 5
