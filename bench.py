@@ -627,6 +627,8 @@ def main():
     ap.add_argument("--adjoint-seeds", type=int, default=16)
     ap.add_argument("--adjoint-steps", type=int, default=2000)
     args = ap.parse_args()
+    if args.steps < 1:
+        ap.error("--steps must be >= 1")
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.ensemble_steps < 1:
