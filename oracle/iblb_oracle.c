@@ -34,9 +34,11 @@
  *                              droplet from an even-odd ray count over the mesh
  *
  * Parity status: every function is pinned by tests/test_oracle_*.py against
- * closed forms, invariants or brute force, except the edge and corner rules
- * with a moving wall (EDGE_PAPER_PLUS_WALL), whose agreement with the paper
- * is "parity unpinned" (only the rest state is pinned).
+ * closed forms, invariants or brute force (the re-centred face velocity
+ * against the pinned volume centroid, the ray indicator against the
+ * half-space test and the solid-angle winding number), except the edge and
+ * corner rules with a moving wall (EDGE_PAPER_PLUS_WALL), whose agreement
+ * with the paper is "parity unpinned" (only the rest state is pinned).
  */
 #include <math.h>
 #include <stdlib.h>
