@@ -36,7 +36,10 @@
  * Parity status: every function is pinned by tests/test_oracle_*.py against
  * closed forms, invariants or brute force (the re-centred face velocity
  * against the pinned volume centroid, the ray indicator against the
- * half-space test and the solid-angle winding number), except the edge and
+ * half-space test and the solid-angle winding number; interpolation and
+ * advection by exact transport in a uniform flow, exact reproduction of a
+ * linear velocity field and the (k - 1/2) g velocity of a fluid under a
+ * uniform force), except the edge and
  * corner rules with a moving wall (EDGE_PAPER_PLUS_WALL), whose agreement
  * with the paper is "parity unpinned" (only the rest state is pinned).
  */

@@ -154,3 +154,106 @@ def test_recentring_follows_the_droplet_each_step():
     assert np.abs(a.fields()[1] - b.fields()[1]).max() < 1e-13
     a.close()
     b.close()
+
+
+# ---------------------------------------------------------------------------
+# Interpolation and advection, Eq. (ibm_force_d)(b) and Eq. (fwd_euler),
+# pinned by what the 4-point kernel and the Guo scheme fix exactly: the
+# kernel is a partition of unity with zero first moment, so it reproduces
+# constant and linear velocity fields at any node position, and the Guo
+# source changes the momentum of a uniform fluid by exactly F per step while
+# the velocity of a step carries half of that step's force.
+
+def _periodic_with_mesh(N, tau, pops, level=2, R=3.2, centre=None):
+    """Periodic box in the state `pops` (19, z, y, x in the oracle's order) and
+    a force-free droplet mesh (sigma = 0), slightly off the lattice planes."""
+    s = O.OracleSim((N, N, N), tau, np.zeros((1, 3, 3)), 10 ** 9, bc=(O.BC_PERIODIC,) * 3)
+    s.set_populations(pops, 0)
+    c = centre if centre is not None else (0.5 * (N - 1) + 0.23, 0.5 * (N - 1) - 0.31, 0.5 * (N - 1) + 0.17)
+    r, t = O.icosphere(level, R, c)
+    s.set_mesh(r, t, 0.0)
+    return s, r
+
+
+def _equilibrium_field(N, u_of_node):
+    """f = f_eq(1, u(x)) at every node, u_of_node(x, y, z) -> 3-vector."""
+    f = np.zeros((19, N, N, N))
+    for z in range(N):
+        for y in range(N):
+            for x in range(N):
+                f[:, z, y, x] = O.equilibrium(1.0, u_of_node(x, y, z))
+    return f
+
+
+@pytest.mark.parametrize("tau", [1.0, 0.8])
+def test_uniform_flow_carries_every_node_by_U(tau):
+    """A fluid at uniform velocity U with no force is a fixed point of the
+    step (its equilibrium streams onto itself), and a partition-of-unity
+    kernel interpolates exactly U: every node moves by exactly U per step."""
+    N = 14
+    U = np.array([3.1e-3, -1.7e-3, 2.3e-3])
+    s, r0 = _periodic_with_mesh(N, tau, _equilibrium_field(N, lambda x, y, z: U))
+    for k in range(1, 4):
+        assert s.step(1) == 0
+        r, _ = s.mesh()
+        assert np.abs(r - (r0 + k * U)).max() < 1e-14
+    s.close()
+
+
+def test_linear_field_interpolates_exactly():
+    """u(x) = B (x - c) set as the state: the moments of the step return it at
+    every node, and the 4-point kernel (zero first moment) gives exactly
+    B (r_i - c) at every node position, so one step moves each node by
+    that.  A stencil shifted by one node would move it by B (r_i - c +- e_a),
+    off by |B e_a| ~ 1e-3."""
+    N = 16
+    c = np.array([7.5, 7.5, 7.5])
+    B = np.array([[1.3e-3, -2.1e-3, 0.7e-3], [0.4e-3, -0.9e-3, 1.8e-3], [-1.1e-3, 0.6e-3, 0.5e-3]])
+    s, r0 = _periodic_with_mesh(N, 1.0, _equilibrium_field(N, lambda x, y, z: B @ (np.array([x, y, z]) - c)))
+    assert s.step(1) == 0
+    rho, u, _ = s.fields()
+    X = np.stack(np.meshgrid(np.arange(N), np.arange(N), np.arange(N), indexing="ij")[::-1])  # (3, z, y, x)
+    want_u = np.einsum("ab,bzyx->azyx", B, X - c[:, None, None, None])
+    assert np.abs(u - want_u).max() < 1e-15
+    r, _ = s.mesh()
+    v = (r0 - c) @ B.T
+    assert np.abs(r - (r0 + v)).max() < 1e-15 * np.abs(r0).max()
+    assert np.abs(v).max() > 5e-3
+    s.close()
+
+
+def test_interpolated_velocity_carries_half_the_force():
+    """Uniform body force g on a fluid at rest: the half-force momentum of
+    Eq. (density_velocity_LB) gives u = (k - 1/2) g in step k (the Guo
+    source adds exactly g per step), so after n steps a node has moved by
+    sum_k (k - 1/2) g = (n^2 / 2) g -- not n (n - 1) / 2 g, which
+    interpolating u without the F/2 term would give."""
+    N = 12
+    g = np.array([2.0e-5, -3.0e-5, 1.0e-5])
+    rest = np.stack([np.full((N, N, N), w) for w in O.weights()])
+    s, r0 = _periodic_with_mesh(N, 0.9, rest)
+    for n in range(1, 5):
+        assert s.step(1, body_force=g) == 0
+        rho, u, F = s.fields()
+        assert np.abs(rho - 1.0).max() < 1e-14
+        assert np.abs(u - ((n - 0.5) * g)[:, None, None, None]).max() < 1e-15
+        r, _ = s.mesh()
+        assert np.abs(r - (r0 + 0.5 * n * n * g)).max() < 1e-15 * np.abs(r0).max()
+    s.close()
+
+
+def test_first_step_velocity_is_half_the_spread_force():
+    """A droplet with surface tension at rest in a fluid at rest: in the first
+    step the streamed fluid carries no momentum, so the velocity the step
+    interpolates is exactly F_ext / 2 at every node, F_ext the spread force."""
+    N = 16
+    rest = np.stack([np.full((N, N, N), w) for w in O.weights()])
+    s = O.OracleSim((N, N, N), 1.0, np.zeros((1, 3, 3)), 10 ** 9, bc=(O.BC_PERIODIC,) * 3)
+    s.set_populations(rest, 0)
+    r, t = O.icosphere(2, 3.4, (7.6, 7.3, 7.45))
+    s.set_mesh(r, t, 0.02)
+    assert s.step(1) == 0
+    rho, u, F = s.fields()
+    assert np.abs(F).max() > 1e-4
+    assert np.abs(u - 0.5 * F / rho[None]).max() < 1e-15
+    s.close()
