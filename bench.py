@@ -60,16 +60,9 @@ def config_dict(w, extra=None):
     return d
 
 
-def traffic_from_profiles():
-    """Per-launch DRAM bytes of the lattice kernel from the committed ncu
-    record, if it was taken on the current lattice source (the part of the
-    kernel file up to the end of the lattice kernel, plus the shared device
-    header it includes)."""
-    p = os.path.join(ROOT, "profiles", "lattice_traffic.json")
-    if not os.path.exists(p):
-        return None
-    with open(p) as fh:
-        d = json.load(fh)
+def lattice_source_hash():
+    """Hash of the lattice kernel's source: the kernel file up to the end of
+    the lattice kernels, plus the shared device header it includes."""
     import hashlib
 
     src = open(os.path.join(ROOT, "paper_2403_01161_gb300", "csrc", "iblb_kernels.cu")).read()
@@ -77,10 +70,36 @@ def traffic_from_profiles():
     if marker not in src:
         return None
     hdr = open(os.path.join(ROOT, "paper_2403_01161_gb300", "csrc", "iblb_device.cuh")).read()
-    h = hashlib.sha256((src[: src.index(marker)] + hdr).encode()).hexdigest()
-    if d.get("lattice_source_sha256") != h:
+    return hashlib.sha256((src[: src.index(marker)] + hdr).encode()).hexdigest()
+
+
+def traffic_from_profiles(name):
+    """Per-launch DRAM bytes (read + write) of the far lattice kernel of the
+    workload `name` from the committed ncu record, if that record was taken
+    on the current lattice source; None otherwise."""
+    p = os.path.join(ROOT, "profiles", "lattice_traffic.json")
+    if not os.path.exists(p):
         return None
-    return float(d["bytes_per_launch_full_size"])
+    with open(p) as fh:
+        d = json.load(fh)
+    if d.get("lattice_source_sha256") != lattice_source_hash():
+        return None
+    rec = d.get("workloads", {}).get(name)
+    return float(rec["bytes_per_launch_full_size"]) if rec else None
+
+
+CHUNK_128 = 300  # graph chunk of the single-droplet workload: lcm(6, readout period 100)
+
+
+def warm_up_aligned(sim, warmup, chunk, steps):
+    """W warm-up steps; when the timed region holds whole graph chunks, then
+    enough more that it starts at a chunk boundary with the chunk graph
+    already captured and replayed once.  Returns the steps run."""
+    sim.step(warmup)
+    if steps >= chunk:
+        sim.step((-sim.steps_done) % chunk)
+        sim.step(chunk)
+    return sim.steps_done
 
 
 class ClockSampler:
@@ -159,27 +178,53 @@ def job_throughput(nodes_per_rank: int, steps: int, world: int, seconds: float) 
     return world * nodes_per_rank * steps / seconds / 1e6
 
 
-def cpu_baseline(w, budget_s=15.0, max_steps=400):
+def _omp_threads(n):
+    """Sets the OpenMP thread count of the calling thread's next parallel
+    regions (the oracle's lattice loop) through the OpenMP runtime the
+    oracle library is linked against."""
+    import ctypes
+
+    try:
+        ctypes.CDLL("libgomp.so.1").omp_set_num_threads(int(n))
+        return True
+    except (OSError, AttributeError):
+        return False
+
+
+def cpu_baseline(w, budget_s=15.0, max_steps=400, one_core_budget_s=8.0):
     """The FP64 oracle, as it stands, on this host's cores: a bounded number
-    of steps of the same workload (same box, mesh and gradients)."""
+    of steps of the same workload (same box, mesh and gradients), once with
+    every core and once with one core."""
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     os.environ["OMP_NUM_THREADS"] = str(cores)
     import oracle as O
     from paper_2403_01161_gb300 import config
 
-    o = O.OracleSim(w.n, w.tau, w.frames, w.n_hold)
-    r, t = O.icosphere(w.level, w.R, config.box_center(w.n))
-    o.set_mesh(r, t, w.sigma)
-    t0 = time.perf_counter()
-    o.step(1)
-    first = time.perf_counter() - t0
-    n = max(1, min(max_steps, int(budget_s / max(first, 1e-3))))
-    t0 = time.perf_counter()
-    o.step(n)
-    dt = time.perf_counter() - t0
-    o.close()
-    return {"value": w.nodes * n / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "%d FP64 oracle steps of %s (steps 1..%d of the trajectory), %.1f s" % (n, w.name, n, dt)}
+    def run(budget, cap):
+        o = O.OracleSim(w.n, w.tau, w.frames, w.n_hold)
+        r, t = O.icosphere(w.level, w.R, config.box_center(w.n))
+        o.set_mesh(r, t, w.sigma)
+        t0 = time.perf_counter()
+        o.step(1)
+        first = time.perf_counter() - t0
+        n = max(1, min(cap, int(budget / max(first, 1e-3))))
+        t0 = time.perf_counter()
+        o.step(n)
+        dt = time.perf_counter() - t0
+        o.close()
+        return n, dt
+
+    O.lib()
+    _omp_threads(cores)
+    n, dt = run(budget_s, max_steps)
+    out = {"value": w.nodes * n / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": "%d FP64 oracle steps of %s (steps 1..%d of the trajectory), %.1f s" % (n, w.name, n, dt)}
+    if one_core_budget_s > 0 and _omp_threads(1):
+        n1, dt1 = run(one_core_budget_s, max_steps)
+        _omp_threads(cores)
+        out["one_core"] = {"value": w.nodes * n1 / dt1 / 1e6, "unit": UNIT, "cores": 1,
+                           "sample": "%d FP64 oracle steps of %s, %.1f s" % (n1, w.name, dt1)}
+    return out
 
 
 def ensemble_partition(sizes, world):
@@ -193,6 +238,30 @@ def ensemble_partition(sizes, world):
     return owner
 
 
+def gather_member_records(records, world):
+    """The union over ranks of each rank's {member id: record} (every rank
+    gets it); with one rank, the rank's own records."""
+    if world <= 1:
+        return dict(records)
+    import torch.distributed as dist
+
+    out = [None] * world
+    dist.all_gather_object(out, dict(records))
+    merged = {}
+    for d in out:
+        merged.update(d)
+    return merged
+
+
+def run_member_share(workloads, rank, world, runner):
+    """Runs this rank's share of the members (longest-processing-time by node
+    count) through runner(workload) -> record and gathers every rank's
+    records: {member index: record}."""
+    owner = ensemble_partition([w.nodes for w in workloads], world)
+    mine = {k: runner(w) for k, w in enumerate(workloads) if owner[k] == rank}
+    return gather_member_records(mine, world)
+
+
 def measure_ensemble(dev, steps, warmup, rank, world):
     """Batched ensemble of the 64 uneven droplets (boxes 48^3..96^3, R 6..10,
     own OU trajectories) against the same droplets stepped one at a time.
@@ -202,7 +271,7 @@ def measure_ensemble(dev, steps, warmup, rank, world):
     from paper_2403_01161_gb300 import config
     from paper_2403_01161_gb300.sim import Ensemble, Sim
 
-    ws = config.ensemble_workloads(64, steps=warmup + 2 * steps + 8)
+    ws = config.ensemble_workloads(64, steps=warmup + 2 * steps + 80)
     owner = ensemble_partition([w.nodes for w in ws], world)
     mine = [w for k, w in enumerate(ws) if owner[k] == rank]
     sims = []
@@ -226,12 +295,21 @@ def measure_ensemble(dev, steps, warmup, rank, world):
         return max_over_ranks(e0.elapsed_time(e1) * 1e-3, world, dev)
 
     E = Ensemble(sims) if sims else None
+    tuned = None
     if E:
+        k, tms = E.tune(6)  # the autotuner's steps are steps of the members' trajectories
+        tuned = {"shape": E.shape(), "ms_per_step_by_shape": [float(v) for v in tms]}
         E.step(warmup)
     t_ens = timed(lambda: E.step(steps) if E else None)
+    final = {}
     if E:
         E.sync()
         E.close()
+        mine_idx = [k for k in range(len(ws)) if owner[k] == rank]
+        for k, g in zip(mine_idx, sims):
+            ob = g.readout()
+            final[k] = {"seed": ws[k].name, "step": ob["step"], "D": ob["D"], "V": ob["V"]}
+    final = gather_member_records(final, world)
     for g in sims:
         g.step(warmup)
     t_seq = timed(lambda: [g.step(steps) for g in sims])
@@ -243,6 +321,8 @@ def measure_ensemble(dev, steps, warmup, rank, world):
             "total_nodes": sum(w.nodes for w in ws), "steps": steps, "warmup": warmup,
             "ms_per_step": t_ens / steps * 1e3,
             "mlups": sum(w.nodes for w in ws) * steps / t_ens / 1e6,
+            "members_final_D": [final[k]["D"] for k in sorted(final)] if len(final) == len(ws) else None,
+            "autotuner": tuned,
             "config": "64 droplets, boxes 48^3-96^3 (seeds 1000-1063), R 6-10, icosphere level 3 or 4, "
                       "own OU gradients, FP32; baseline: the same droplets stepped one after another with "
                       "the single-droplet kernels (graph replay each)"}
@@ -313,6 +393,69 @@ def measure_adjoint(dev, rank, world, seeds=range(500, 516), steps=2000, K=100):
                       "2000 steps; adjoint = one ibl_adjoint call (forward pass with checkpoints every K "
                       "steps, recomputation per segment, reverse steps); resident = every step's moments "
                       "kept in HBM (K = 2000)"}
+
+
+def measure_stress_256(dev, steps, warmup=300):
+    """The 256^3 precision-stress workload (R 24, icosphere level 5, OU
+    gradients at R/eta 1 and rms Ca 0.5, regularisation every 50 steps, a
+    shape record every 100): step time and MLUPS by CUDA events over `steps`
+    graph-replayed steps after a chunk of warm-up, and the far lattice
+    kernel's achieved bandwidth from event pairs on one launch in 20."""
+    import numpy as np
+    import torch
+
+    from paper_2403_01161_gb300 import config
+    from paper_2403_01161_gb300.sim import Sim
+
+    w = config.precision_stress_256(steps=warmup + steps + 8)
+    s = Sim(w.n, w.tau, w.frames, w.n_hold, precision=w.precision, device=dev)
+    s.add_icosphere(w.level, w.R, w.sigma)
+    s.set_regularization(every=w.reg_every)
+    s.set_readout(100)
+    every = 21  # odd: both step parities
+    s.profile(True, mask=1, every=every)
+    s.step(warmup)
+    s.sync()
+    s.profile(True, mask=1, every=every)
+    paths0 = s.step_paths()
+    stream = torch.cuda.current_stream(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    s.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    prof = s.profile_read()
+    paths1 = s.step_paths()
+    s.profile(False)
+    st = s.status()
+    _, pext = s.patch()
+    patch_nodes = int(np.prod(pext + 1)) if (pext >= 0).all() else 0
+    ob = s.readout()
+    s.close()
+    if st != 0:
+        raise RuntimeError("device error status %d in the 256^3 run" % st)
+    lb_ms, lb_n = prof["lattice"]
+    if lb_n == 0:
+        raise RuntimeError("no lattice launch was bracketed in the 256^3 run")
+    t_launch = lb_ms / lb_n * 1e-3
+    far = w.nodes - patch_nodes
+    achieved = BYTES_PER_NODE * far / t_launch / 1e9
+    peak, peak_kind = measured_peaks()
+    return {"metric": "MLUPS", "value": w.nodes * steps / (ms * 1e-3) / 1e6, "unit": "MLUPS",
+            "us_per_step": 1e3 * ms / steps, "steps": steps, "warmup": warmup,
+            "graph_replayed_steps": paths1[1] - paths0[1], "eager_steps": paths1[0] - paths0[0],
+            "final_D": ob["D"],
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_kind": peak_kind, "traffic": traffic_from_profiles(w.name),
+                         "kernel": "lattice stream-collide, nodes outside the droplet patch",
+                         "kernel_us": t_launch * 1e6, "launches_timed": lb_n, "bytes_per_launch": BYTES_PER_NODE * far,
+                         "patch_nodes": patch_nodes},
+            "config": "256^3, R 24, icosphere level 5 (10242 nodes, 20480 triangles), tau 1, R/eta 1, rms Ca 0.5, "
+                      "OU gradients (seed 4), regularisation (alpha 0.1, gamma 0.51, tol 0.01) every 50 steps, "
+                      "shape record every 100, FP32 populations; population array 1.27 GB > L2"}
 
 
 PAPER_TRAJECTORY_HOURS = 3.0   # Sec. 3.2: about 3 h per trajectory on one A100
@@ -416,6 +559,37 @@ def measure_linear_theory(dev, n_traj=1000, n_frames=2000, Ca_values=(0.05, 0.2)
     return out
 
 
+def measure_iblb_statistics(dev, n_members=64, n_frames=200, Ca_values=(0.05, 0.2), skip=20):
+    """The synthetic analogue of the paper's ensemble statistics (Sec. 4):
+    n_members IBLB droplets (48^3, R 6, icosphere level 3, R/eta 0.472, own
+    OU gradients, 95 steps per frame) stepped as one ensemble for n_frames
+    frames, and the linear theory (Eq. (LT)) along the same frames; the
+    quantiles of lambda_max/R^2 and beta of both after `skip` frames, per
+    capillary number."""
+    import torch
+
+    from paper_2403_01161_gb300 import statistics
+
+    out = {"metric": "droplet-frames/s", "members": n_members, "frames": n_frames, "skip": skip, "by_Ca": {},
+           "config": "48^3 box, R 6, icosphere level 3 (642 nodes), tau 1, R/eta 0.472 (tau_eta 969 steps, 95 "
+                     "steps per frame), OU gradients (rms 1/tau_eta, correlation 20 tau_eta, seed 900), FP32; "
+                     "quantiles 5/25/50/75/95 % over members and frames"}
+    for Ca in Ca_values:
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        res = statistics.trajectories(n_members, n_frames, Ca, device=dev)
+        dt = time.perf_counter() - t0
+        qs = statistics.quantiles(res, skip)
+        lam_i, lam_t = qs["iblb_lam"][2] - 1.0, qs["lt_lam"][2] - 1.0
+        out["by_Ca"]["%g" % Ca] = {"seconds": dt, "lam_max_R2_quantiles_iblb": qs["iblb_lam"],
+                                   "lam_max_R2_quantiles_theory": qs["lt_lam"],
+                                   "beta_quantiles_iblb": qs["iblb_beta"], "beta_quantiles_theory": qs["lt_beta"],
+                                   "median_excess_ratio": lam_i / lam_t if lam_t > 0 else None,
+                                   "steps_per_frame": res["hold"]}
+    out["value"] = n_members * n_frames * len(Ca_values) / sum(v["seconds"] for v in out["by_Ca"].values())
+    return out
+
+
 def regularization_study(dev, steps=50000, sample=2000):
     """Sec. 3.3 in practice: one sub-critical droplet trajectory (96^3, R 10,
     level 4, rms Ca 0.2, OU gradients changing direction every 2 tau_eta)
@@ -480,11 +654,11 @@ def run_reference(args):
     w = workload()
     # a step of the reference arm is a bounded sample of oracle steps
     budget = max(2.0, min(20.0, 60.0 / max(1, args.steps + args.warmup)))
-    cb = cpu_baseline(w, budget_s=budget)
+    cb = cpu_baseline(w, budget_s=budget, one_core_budget_s=0.0)
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": w.nodes / (cb["value"] * 1e6) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_dict(w), "cpu_baseline": cb,
+            "config": config_dict(w, {"parallelism": "replicas" if world > 1 else "single"}), "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -507,23 +681,26 @@ def run_ours(args):
     sim = Sim(w.n, w.tau, w.frames, w.n_hold, precision=w.precision, device=dev)
     sim.add_icosphere(w.level, w.R, w.sigma)
     sim.set_readout(100)
-    sim.step(args.warmup)
-    sim.sync()
 
     def barrier():
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize(dev)
 
+    # event pairs around one launch in `every` of the lattice kernel (nodes
+    # outside the droplet patch), eager or inside a replayed graph: an event
+    # pair costs its step a little of the two streams' overlap, so sampling
+    # stays sparse (at least 4 launches of the timed region when it has 16
+    # steps or more); an odd stride samples both step parities (the AA
+    # pattern's even and odd kernels differ)
+    every = max(1, min(99, args.steps // 5)) | 1
+    sim.profile(True, mask=1, every=every)
+    warm = warm_up_aligned(sim, args.warmup, CHUNK_128, args.steps)
+    sim.sync()
+    paths0 = sim.step_paths()
     clocks = ClockSampler(local)
     clocks.start()
-    # event pairs around every 100th launch of the lattice kernel (nodes
-    # outside the droplet patch) inside the replayed graph chunks: an event
-    # node in the two-stream graph costs the overlap of its step, so sampling
-    # stays sparse; the last replay in the timed region is read back
-    sim.profile(True, mask=1 | 8, every=100)
-    sim.step(args.warmup)  # re-captures the chunk with its event nodes
-    sim.sync()
+    sim.profile(True, mask=1, every=every)  # clears the marks of the warm-up, keeps the captures
     stream = torch.cuda.current_stream(dev)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -534,6 +711,7 @@ def run_ours(args):
     barrier()
     ms = e0.elapsed_time(e1)
     prof = sim.profile_read()
+    paths1 = sim.step_paths()
     sim.profile(False)
     _, pext = sim.patch()
     patch_nodes = int(np.prod(pext + 1)) if (pext >= 0).all() else 0
@@ -545,21 +723,26 @@ def run_ours(args):
     ms = max_over_ranks(ms, world, dev)
     value = job_throughput(w.nodes, args.steps, world, ms * 1e-3)
     lb_ms, lb_n = prof["lattice"]
-    t_launch = lb_ms / lb_n * 1e-3 if lb_n else None
-    achieved = BYTES_PER_NODE * far_nodes / t_launch / 1e9 if t_launch else None
+    if lb_n == 0:
+        raise RuntimeError("no lattice launch was bracketed in the timed region")
+    t_launch = lb_ms / lb_n * 1e-3
+    achieved = BYTES_PER_NODE * far_nodes / t_launch / 1e9
     peak, peak_kind = measured_peaks()
     # per step: force/spread, patch update, outside update, interpolation;
     # plus one shape-record kernel every 100 steps
     launches = 4 * args.steps + (sim.steps_done // 100 - (sim.steps_done - args.steps) // 100)
+    timed_path = {"graph_replayed_steps": paths1[1] - paths0[1], "eager_steps": paths1[0] - paths0[0],
+                  "warmup_steps_run": warm}
     sim.close()
 
     # end to end through the C-ABI with host buffers: the Sec. 3.2 loop, per
     # frame one pinned H2D gradient copy and one D2H shape record
     n_fr = max(1, (args.steps + w.n_hold - 1) // w.n_hold)
     pinned = torch.empty((n_fr, 9), dtype=torch.float64, pin_memory=True)
-    pinned.copy_(torch.from_numpy(np.ascontiguousarray(w.frames[:n_fr].reshape(n_fr, 9))))
-    sim2 = Sim(w.n, w.tau, w.frames[:n_fr], w.n_hold, precision=w.precision, device=dev)
+    pinned.copy_(torch.from_numpy(np.ascontiguousarray(w.frames[1:n_fr + 1].reshape(n_fr, 9))))
+    sim2 = Sim(w.n, w.tau, w.frames[:n_fr + 1], w.n_hold, precision=w.precision, device=dev)
     sim2.add_icosphere(w.level, w.R, w.sigma)
+    sim2.run_frames(w.frames[:1], w.n_hold)  # warm-up frame: the graph captures happen here
     sim2.sync()
     barrier()
     t0 = time.perf_counter()
@@ -579,10 +762,12 @@ def run_ours(args):
            "h2d_bytes_per_step": 72.0 / w.n_hold, "d2h_bytes_per_step": rec_bytes / w.n_hold,
            "steps": e2e_steps, "api": "ibl_run_frames (host gradients in, host shape records out)"}
 
+    stress = measure_stress_256(dev, args.stress_steps) if args.stress_steps > 0 else None
     ens = measure_ensemble(dev, args.ensemble_steps, 20, rank, world)
     adj = measure_adjoint(dev, rank, world) if args.adjoint else None
     prod = measure_production(dev, 2 * 1488, 1488) if args.production else None
     lt = measure_linear_theory(dev) if args.theory and rank == 0 else None
+    lstat = measure_iblb_statistics(dev) if args.theory and rank == 0 else None
 
     if rank == 0:
         cb = cpu_baseline(w) if world == 1 else None
@@ -591,13 +776,15 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": config_dict(w, {"parallelism": "replicas" if world > 1 else "single"}),
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                             "frac": achieved / peak if achieved else None, "traffic": traffic_from_profiles(),
+                             "frac": achieved / peak, "traffic": traffic_from_profiles(w.name),
                              "kernel": "lattice stream-collide, nodes outside the droplet patch",
                              "peak_kind": peak_kind,
-                             "kernel_us": t_launch * 1e6 if t_launch else None, "launches_timed": lb_n,
+                             "kernel_us": t_launch * 1e6, "launches_timed": lb_n, "sampling_every": every,
                              "bytes_per_launch": BYTES_PER_NODE * far_nodes, "patch_nodes": patch_nodes},
+                "timed_path": timed_path, "precision_stress_256": stress,
                 "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches * world, "clocks": clk,
                 "ensemble": ens, "adjoint": adj, "production": prod, "linear_theory": lt,
+                "iblb_statistics": lstat,
                 "droplet_steps_per_s": world * args.steps / (ms * 1e-3),
                 "lagrangian_updates_per_s": world * (10 * 4 ** w.level + 2) * args.steps / (ms * 1e-3)}
         print(json.dumps(line))
@@ -614,6 +801,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ensemble-steps", type=int, default=200,
                     help="timed steps of the 64-droplet ensemble measurement")
+    ap.add_argument("--stress-steps", type=int, default=600,
+                    help="timed steps of the 256^3 precision-stress measurement (0 skips it)")
     ap.add_argument("--no-adjoint", dest="adjoint", action="store_false",
                     help="skip the adjoint/forward measurement (16 seeds of the 64^3 droplet)")
     ap.add_argument("--no-production", dest="production", action="store_false",

@@ -226,12 +226,16 @@ int ibl_step(ibl_lb *lb, long long n);
 int ibl_step_record(ibl_lb *lb);
 
 /* Graph replay (default on): ibl_step runs whole chunks of steps -- a
- * multiple of 2 and of the regularisation and readout periods, at least 32
+ * multiple of 6 and of the regularisation and readout periods, at least 32
  * -- as one captured CUDA graph launched on the bound stream, and the steps
  * before the first chunk boundary and after the last one eagerly.  The
  * chunk is captured on a private stream at the first use and again after
  * any schedule change.  enable = 0 launches every kernel eagerly. */
 int ibl_set_graphs(ibl_lb *lb, int enable);
+
+/* Steps ibl_step has run eagerly and by graph replay since the lattice was
+ * created (ibl_step_record and the adjoint's recomputations not counted). */
+int ibl_step_paths(const ibl_lb *lb, long long *eager, long long *replayed);
 
 /* Waits for the stream and reports the sticky device error bits as a status. */
 int ibl_sync(ibl_lb *lb);
@@ -303,7 +307,11 @@ int ibl_regularize_now(ibl_mesh *m, int *iters);
  * exits; n_nodes above 16384 is rejected with IBL_EINVAL.  The first call
  * on a device looks up that array's device address (with the caller's
  * current device), so make the first call on each device before any stream
- * capture.  Every call uses the same array and leaves its contents behind;
+ * capture.  The address is looked up again whenever the calling thread's
+ * current context is not the one it was looked up in (a driver-API context
+ * made current, or the primary context created anew after
+ * cudaDeviceReset): make the first call after such a change outside a
+ * stream capture too.  Every call uses the same array and leaves its contents behind;
  * each call writes every element it reads first, so nothing needs
  * clearing, but calls whose executions overlap on the GPU (other streams,
  * other threads) race on it.  Calls no allocating routine. */
@@ -336,7 +344,36 @@ int ibl_ensemble_workspace_size(int n_members, ibl_lb *const *members, size_t *b
 int ibl_ensemble_create(int n_members, ibl_lb *const *members, void *workspace, size_t bytes, ibl_ensemble **out);
 /* Enqueues n steps of every member (asynchronous). */
 int ibl_ensemble_step(ibl_ensemble *e, long long n);
-/* Waits and returns the first member's error status, if any. */
+/* Launch shape of an ensemble step: IBL_ENSEMBLE_SHAPES candidates, shape
+ * k = 4 p + 2 t + w.  The batched lattice update of the nodes outside each
+ * droplet patch (almost all of a step's bytes) takes 128 (t = 0) or 256
+ * (t = 1) threads per block, each block updating that many consecutive
+ * nodes of one z plane of one member, and prefetches the populations into
+ * L2 w resident waves of blocks ahead (w = 0 or 1).  p = 0 keeps the
+ * droplet-side data (mesh, patch populations, force and velocity) in L2
+ * with an evict_last policy, as a single droplet's step does; p = 1 uses the
+ * default policy.  The shape changes only launch geometry and cache
+ * policy: every shape computes the same populations.  Default: shape 5.
+ *
+ * ibl_ensemble_tune is the autotuner: it runs 2 untimed and
+ * steps_per_candidate timed ensemble steps with each shape in turn (eager
+ * launches, CUDA events on the bound stream), keeps the shape with the
+ * least time per step and writes its index to *chosen and the measured ms
+ * per step of every shape to ms (IBL_ENSEMBLE_SHAPES doubles; either may be
+ * NULL).  These are steps of the members' trajectories: afterwards every
+ * member has advanced by IBL_ENSEMBLE_SHAPES * (steps_per_candidate + 2)
+ * steps.  Synchronising; returns the members' error status as
+ * ibl_ensemble_sync.  ibl_ensemble_set_shape sets a shape directly (for
+ * instance one stored from an earlier tuning of the same member sizes);
+ * ibl_ensemble_shape reports the current one (any pointer may be NULL). */
+#define IBL_ENSEMBLE_SHAPES 8
+int ibl_ensemble_tune(ibl_ensemble *e, int steps_per_candidate, double *ms, int *chosen);
+int ibl_ensemble_set_shape(ibl_ensemble *e, int shape);
+int ibl_ensemble_shape(const ibl_ensemble *e, int *shape, int *threads, int *prefetch_waves);
+
+/* Waits and returns the error status of the first member (in the order
+ * given at creation) whose sticky device bits are set, with ibl_last_error()
+ * naming that member's index ("ensemble member k: ..."); IBL_OK if none. */
 int ibl_ensemble_sync(ibl_ensemble *e);
 void ibl_ensemble_destroy(ibl_ensemble *e);
 

@@ -16,6 +16,7 @@ IBL_OK, IBL_EINVAL, IBL_ENOMEM, IBL_ECUDA, IBL_EUNSTABLE, IBL_ENOCONV, IBL_EWALL
 BC_ZOU_HE, BC_PERIODIC = 0, 1
 EDGE_PAPER_PLUS_WALL, EDGE_PAPER_LITERAL = 0, 1
 FP32_DEV, FP64 = 0, 1
+ENSEMBLE_SHAPES = 8
 ERRBIT_UNSTABLE, ERRBIT_NOCONV, ERRBIT_WALL = 1, 2, 4
 
 
@@ -77,6 +78,7 @@ SIGNATURES = [
     ("ibl_step", ctypes.c_int, [_P, ctypes.c_longlong]),
     ("ibl_step_record", ctypes.c_int, [_P]),
     ("ibl_set_graphs", ctypes.c_int, [_P, ctypes.c_int]),
+    ("ibl_step_paths", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
     ("ibl_sync", ctypes.c_int, [_P]),
     ("ibl_steps_done", ctypes.c_longlong, [_P]),
     ("ibl_readout", ctypes.c_int, [_P, ctypes.POINTER(Observables)]),
@@ -97,6 +99,10 @@ SIGNATURES = [
                                            ctypes.POINTER(_P)]),
     ("ibl_ensemble_step", ctypes.c_int, [_P, ctypes.c_longlong]),
     ("ibl_ensemble_sync", ctypes.c_int, [_P]),
+    ("ibl_ensemble_tune", ctypes.c_int, [_P, ctypes.c_int, _D, ctypes.POINTER(ctypes.c_int)]),
+    ("ibl_ensemble_set_shape", ctypes.c_int, [_P, ctypes.c_int]),
+    ("ibl_ensemble_shape", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(ctypes.c_int)]),
     ("ibl_ensemble_destroy", None, [_P]),
     ("ibl_patch", ctypes.c_int, [_P, _I32, _I32]),
     ("ibl_velocity_set", ctypes.c_int, [_I32, _D]),

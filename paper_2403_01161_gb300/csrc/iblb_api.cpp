@@ -153,6 +153,7 @@ struct ibl_lb {
     bool graphs = true;
     int chunk = 0;                       // steps per captured chunk (0 = none captured)
     cudaGraphExec_t gexec = nullptr;
+    long long steps_eager = 0, steps_replayed = 0;  // counts of ibl_step's two paths
     cudaStream_t cap_stream = nullptr;   // private streams used only for capture
     cudaStream_t cap_helper = nullptr;
     bool capturing = false;
@@ -636,23 +637,46 @@ int capture_chunk(ibl_lb *lb, int chunk)
 struct ibl_ensemble {
     std::vector<ibl_lb *> m;
     iblb::EnsembleView v{};
-    cudaStream_t stream = nullptr;
-    cudaStream_t cap_stream = nullptr;
-    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t stream = nullptr;       // the members' bound stream
+    cudaStream_t helper = nullptr;       // high-priority helper stream (droplet kernels, patch nodes)
+    int hi_prio = 0;
+    cudaStream_t cap_stream = nullptr, cap_helper = nullptr;  // capture twins
+    cudaGraphExec_t gexec = nullptr;     // whole chunk
     int chunk = 0;
+    bool capturing = false;
+    // step events as in ibl_lb: evNear[p] the end of the patch update (and
+    // regularisations, shape records) of the last step of parity p, evFar[p]
+    // the end of its outside update; a second set for use inside captures
+    cudaEvent_t evNear[2] = {nullptr, nullptr}, evFar[2] = {nullptr, nullptr};
+    cudaEvent_t cNear[2] = {nullptr, nullptr}, cFar[2] = {nullptr, nullptr};
+    cudaEvent_t evFork = nullptr, evJoin = nullptr, evCentre = nullptr;
+    cudaEvent_t cFork = nullptr, cJoin = nullptr, cCentre = nullptr;
     ~ibl_ensemble()
     {
         if (gexec) cudaGraphExecDestroy(gexec);
         if (cap_stream) cudaStreamDestroy(cap_stream);
+        if (cap_helper) cudaStreamDestroy(cap_helper);
+        if (helper) cudaStreamDestroy(helper);
+        for (cudaEvent_t ev : {evNear[0], evNear[1], evFar[0], evFar[1], cNear[0], cNear[1], cFar[0], cFar[1], evFork,
+                               evJoin, evCentre, cFork, cJoin, cCentre})
+            if (ev) cudaEventDestroy(ev);
     }
 };
 
 namespace {
 
 struct EnsembleLayout {
-    size_t lv = 0, mv = 0, lat_member = 0, lat_start = 0, node_member = 0, node_start = 0, total = 0;
-    int lat_blocks = 0, node_blocks = 0;
+    size_t lat_member[2] = {0, 0}, lat_start[2] = {0, 0}, node_member = 0, node_start = 0, total = 0;
+    int lat_blocks[2] = {0, 0}, node_blocks = 0;
 };
+
+// Blocks of the batched lattice update of one member with nt threads per
+// block: whole blocks per z plane.
+long long lattice_blocks(const ibl_lb *lb, int nt)
+{
+    const long long nxy = (long long)lb->v.n[0] * lb->v.n[1];
+    return (nxy + nt - 1) / nt * lb->v.n[2];
+}
 
 int ensemble_layout(int n, ibl_lb *const *members, EnsembleLayout &L, std::string &why)
 {
@@ -660,17 +684,22 @@ int ensemble_layout(int n, ibl_lb *const *members, EnsembleLayout &L, std::strin
         why = "need at least one member";
         return IBL_EINVAL;
     }
-    long long lat = 0, node = 0;
+    long long lat[2] = {0, 0}, node = 0;
     for (int k = 0; k < n; ++k) {
         const ibl_lb *lb = members[k];
         if (!lb || !lb->mesh) {
             why = "every member needs a lattice with a droplet mesh";
             return IBL_EINVAL;
         }
-        lat += (lb->v.nodes + 255) / 256;
+        if ((long long)lb->v.n[0] * lb->v.n[1] >= (1LL << 22)) {
+            why = "an ensemble member's z plane exceeds 2^22 nodes";
+            return IBL_EINVAL;
+        }
+        lat[0] += lattice_blocks(lb, 128);
+        lat[1] += lattice_blocks(lb, 256);
         node += ((long long)lb->mesh->v.nv + iblb::kFwdNodesPerBlock - 1) / iblb::kFwdNodesPerBlock;
     }
-    if (lat > 0x7fffffffLL) {
+    if (lat[0] > 0x7fffffffLL) {
         why = "ensemble too large";
         return IBL_EINVAL;
     }
@@ -680,12 +709,14 @@ int ensemble_layout(int n, ibl_lb *const *members, EnsembleLayout &L, std::strin
         off = align256(off + b);
         return o;
     };
-    L.lat_member = take(sizeof(int) * lat);
-    L.lat_start = take(sizeof(int) * (n + 1));
+    for (int t = 0; t < 2; ++t) {
+        L.lat_member[t] = take(sizeof(int) * lat[t]);
+        L.lat_start[t] = take(sizeof(int) * (n + 1));
+        L.lat_blocks[t] = (int)lat[t];
+    }
     L.node_member = take(sizeof(int) * node);
     L.node_start = take(sizeof(int) * (n + 1));
     L.total = off;
-    L.lat_blocks = (int)lat;
     L.node_blocks = (int)node;
     return IBL_OK;
 }
@@ -703,54 +734,126 @@ int ensemble_chunk(const ibl_ensemble *e)
     return (int)c;
 }
 
-// One ensemble step on `s`: the four batched kernels, then each member's
-// scheduled regularisation and shape record; advances every member's count.
-int ensemble_one_step(ibl_ensemble *e, cudaStream_t s)
+int ensemble_streams(ibl_ensemble *en)
 {
-    const long long step = e->m[0]->host_step;
-    cudaError_t err = iblb::launch_ensemble_step(e->v, step, s);
-    if (err != cudaSuccess) return cuda_fail(err, "ensemble step launch");
-    const long long next = step + 1;
-    for (ibl_lb *lb : e->m) {
-        ibl_mesh *mm = lb->mesh;
-        if (mm->reg_every > 0 && next % mm->reg_every == 0) {
-            err = iblb::launch_regularize(lb->v, mm->v, mm->reg, (int)(next % 3), s);
-            if (err != cudaSuccess) return cuda_fail(err, "ensemble regularisation launch");
-        }
-        if (mm->readout_every > 0 && next % mm->readout_every == 0) {
-            err = iblb::launch_observables(lb->v, mm->v, s);
-            if (err != cudaSuccess) return cuda_fail(err, "ensemble observables launch");
-        }
-        lb->host_step = next;
-    }
+    if (en->helper) return IBL_OK;
+    int lo = 0, hi = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    en->hi_prio = hi;
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&en->helper, cudaStreamNonBlocking, hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&en->cap_stream, cudaStreamNonBlocking, lo);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&en->cap_helper, cudaStreamNonBlocking, hi);
+    cudaEvent_t *evs[] = {&en->evNear[0], &en->evNear[1], &en->evFar[0], &en->evFar[1], &en->cNear[0], &en->cNear[1],
+                          &en->cFar[0], &en->cFar[1], &en->evFork, &en->evJoin, &en->evCentre, &en->cFork,
+                          &en->cJoin, &en->cCentre};
+    for (cudaEvent_t *ev : evs)
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(e, "ensemble stream/event creation");
     return IBL_OK;
 }
 
-int ensemble_capture(ibl_ensemble *e, int chunk)
+// One ensemble step on two streams, as one_step for a single droplet: on
+// the helper stream sH the droplet kernels of every member (re-centring,
+// triangle moments, forces + spread), the patch nodes once the previous
+// outside update has finished, the interpolation, then each member's
+// scheduled regularisation and shape record; on the bound stream sL the
+// nodes outside every member's patch once the previous patch update has
+// finished (its first block per member closes that member's step).
+int ensemble_one_step(ibl_ensemble *e, cudaStream_t sL, cudaStream_t sH)
 {
-    cudaError_t err = cudaSuccess;
-    if (!e->cap_stream) err = cudaStreamCreateWithFlags(&e->cap_stream, cudaStreamNonBlocking);
-    if (err != cudaSuccess) return cuda_fail(err, "ensemble capture stream");
+    const long long step = e->m[0]->host_step;
+    const int par = (int)(step & 1);
+    const long long next = step + 1;
+    cudaEvent_t *evNear = e->capturing ? e->cNear : e->evNear;
+    cudaEvent_t *evFar = e->capturing ? e->cFar : e->evFar;
+    cudaEvent_t evCentre = e->capturing ? e->cCentre : e->evCentre;
+    bool recentre = false;
+    for (ibl_lb *lb : e->m) recentre = recentre || lb->v.recentre != 0;
+    cudaError_t err = iblb::launch_ensemble_pre(e->v, step, sH, e->hi_prio);
+    if (err == cudaSuccess && recentre) err = cudaEventRecord(evCentre, sH);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(sH, evFar[par ^ 1], 0);
+    if (err == cudaSuccess) err = iblb::launch_ensemble_near(e->v, step, sH, e->hi_prio);
+    if (err == cudaSuccess) err = cudaEventRecord(evNear[par], sH);
+    if (err != cudaSuccess) return cuda_fail(err, "ensemble droplet-side launch");
+    err = cudaStreamWaitEvent(sL, evNear[par ^ 1], 0);
+    if (err == cudaSuccess && recentre) err = cudaStreamWaitEvent(sL, evCentre, 0);
+    if (err == cudaSuccess) err = iblb::launch_ensemble_far(e->v, step, sL);
+    if (err == cudaSuccess) err = cudaEventRecord(evFar[par], sL);
+    if (err != cudaSuccess) return cuda_fail(err, "ensemble lattice launch");
+    err = iblb::launch_ensemble_interp(e->v, sH, e->hi_prio);
+    if (err != cudaSuccess) return cuda_fail(err, "ensemble interpolation launch");
+    bool reg = false, obs = false;
+    for (ibl_lb *lb : e->m) {
+        ibl_mesh *mm = lb->mesh;
+        if (mm->reg_every > 0 && next % mm->reg_every == 0) {
+            // rewrites the member's patch of the next step: the next outside update waits for it
+            err = iblb::launch_regularize(lb->v, mm->v, mm->reg, (int)(next % 3), sH, e->hi_prio);
+            if (err != cudaSuccess) return cuda_fail(err, "ensemble regularisation launch");
+            reg = true;
+        }
+    }
+    if (reg) {
+        err = cudaEventRecord(evNear[par], sH);
+        if (err != cudaSuccess) return cuda_fail(err, "ensemble event");
+    }
+    for (ibl_lb *lb : e->m) {
+        ibl_mesh *mm = lb->mesh;
+        if (mm->readout_every > 0 && next % mm->readout_every == 0) {
+            // the record reads the member's step counter, closed by the outside update
+            if (!obs) err = cudaStreamWaitEvent(sH, evFar[par], 0);
+            if (err == cudaSuccess) err = iblb::launch_observables(lb->v, mm->v, sH, e->hi_prio);
+            if (err != cudaSuccess) return cuda_fail(err, "ensemble observables launch");
+            obs = true;
+        }
+    }
+    if (obs) {
+        err = cudaEventRecord(evNear[par], sH);
+        if (err != cudaSuccess) return cuda_fail(err, "ensemble event");
+    }
+    for (ibl_lb *lb : e->m) lb->host_step = next;
+    return IBL_OK;
+}
+
+// Captures n ensemble steps (from the members' current step) into *out.
+int ensemble_capture(ibl_ensemble *e, int n, cudaGraphExec_t *out)
+{
+    int st = ensemble_streams(e);
+    if (st != IBL_OK) return st;
     std::vector<long long> saved;
     for (ibl_lb *lb : e->m) saved.push_back(lb->host_step);
-    err = cudaStreamBeginCapture(e->cap_stream, cudaStreamCaptureModeThreadLocal);
-    int st = IBL_OK;
-    if (err == cudaSuccess) {
-        for (int k = 0; k < chunk && st == IBL_OK; ++k) st = ensemble_one_step(e, e->cap_stream);
-        cudaGraph_t g = nullptr;
-        const cudaError_t e2 = cudaStreamEndCapture(e->cap_stream, &g);
-        if (e2 != cudaSuccess && st == IBL_OK) st = cuda_fail(e2, "end capture");
-        if (st == IBL_OK) {
-            const cudaError_t e3 = cudaGraphInstantiateWithFlags(&e->gexec, g, cudaGraphInstantiateFlagUseNodePriority);
-            if (e3 != cudaSuccess) st = cuda_fail(e3, "graph instantiate");
-        }
-        if (g) cudaGraphDestroy(g);
-    } else {
-        st = cuda_fail(err, "begin capture");
+    cudaStream_t cL = e->cap_stream, cH = e->cap_helper;
+    cudaError_t err = cudaStreamBeginCapture(cL, cudaStreamCaptureModeThreadLocal);
+    if (err != cudaSuccess) return cuda_fail(err, "begin capture");
+    e->capturing = true;
+    err = join(cL, cH, e->cFork);
+    for (int k = 0; k < 2 && err == cudaSuccess; ++k) {
+        err = cudaEventRecord(e->cNear[k], cH);
+        if (err == cudaSuccess) err = cudaEventRecord(e->cFar[k], cL);
     }
+    if (err != cudaSuccess) st = cuda_fail(err, "capture fork");
+    for (int k = 0; k < n && st == IBL_OK; ++k) st = ensemble_one_step(e, cL, cH);
+    if (st == IBL_OK) {
+        err = join(cH, cL, e->cJoin);
+        if (err != cudaSuccess) st = cuda_fail(err, "capture join");
+    }
+    e->capturing = false;
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(cL, &g);
+    if (e2 != cudaSuccess && st == IBL_OK) st = cuda_fail(e2, "end capture");
+    if (st == IBL_OK) {
+        const cudaError_t e3 = cudaGraphInstantiateWithFlags(out, g, cudaGraphInstantiateFlagUseNodePriority);
+        if (e3 != cudaSuccess) st = cuda_fail(e3, "graph instantiate");
+    }
+    if (g) cudaGraphDestroy(g);
     for (size_t k = 0; k < e->m.size(); ++k) e->m[k]->host_step = saved[k];
-    if (st == IBL_OK) e->chunk = chunk;
     return st;
+}
+
+void ensemble_drop_graphs(ibl_ensemble *e)
+{
+    if (e->gexec) cudaGraphExecDestroy(e->gexec);
+    e->gexec = nullptr;
+    e->chunk = 0;
 }
 
 
@@ -913,6 +1016,7 @@ int ibl_lb_create(const ibl_lb_params *p, const double *A_frames, int n_frames, 
     v.rule = p->edge_rule;
     v.omega = 1.0 / p->tau;
     v.omega_f = (float)(1.0 / p->tau);
+    v.inv_nx = 1.0f / (float)p->n[0];
     v.f = lb->ws + L.f;
     v.force = lb->ws + L.force;
     v.vel = lb->ws + L.vel;
@@ -1138,40 +1242,59 @@ int ibl_step(ibl_lb *lb, long long n)
     // the helper stream starts after everything already on the bound stream
     cudaError_t e = join(sL, sH, lb->evFork);
     if (e != cudaSuccess) return cuda_fail(e, "stream fork");
+    bool forked = true;  // eager steps may use the helper stream
     const int chunk = lb->graphs ? chunk_length(lb) : 0;
     long long done = 0;
-    if (chunk > 0) {
-        // eager steps up to the next chunk boundary, then whole chunks by replay
-        while (done < n && lb->host_step % chunk != 0) {
-            st = one_step(lb, false, sL, sH);
-            if (st != IBL_OK) return st;
-            ++done;
+    // whole chunks at chunk boundaries, eager steps elsewhere (consecutive
+    // eager steps pipeline across steps on the two streams, while a graph
+    // boundary drains them); a graph starts after all eager work
+    auto replay = [&](cudaGraphExec_t g, int len) -> int {
+        if (forked) {
+            e = join(sH, sL, lb->evJoin);
+            if (e != cudaSuccess) return cuda_fail(e, "stream join");
+            forked = false;
         }
-        if (n - done >= chunk) {
-            if (lb->chunk != chunk) {
+        e = cudaGraphLaunch(g, sL);
+        if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+        lb->host_step += len;
+        lb->steps_replayed += len;
+        done += len;
+        return IBL_OK;
+    };
+    while (done < n) {
+        if (chunk > 0 && lb->host_step % chunk == 0 && n - done >= chunk) {
+            if (lb->chunk != chunk || !lb->gexec) {
                 drop_graph(lb);
                 st = capture_chunk(lb, chunk);
                 if (st != IBL_OK) return st;
             }
-            e = join(sH, sL, lb->evJoin);  // the graph starts after all eager work
-            if (e != cudaSuccess) return cuda_fail(e, "stream join");
-            while (n - done >= chunk) {
-                e = cudaGraphLaunch(lb->gexec, sL);
-                if (e != cudaSuccess) return cuda_fail(e, "graph launch");
-                lb->host_step += chunk;
-                done += chunk;
-            }
+            st = replay(lb->gexec, chunk);
+            if (st != IBL_OK) return st;
+            continue;
+        }
+        if (!forked) {
             e = join(sL, sH, lb->evFork);
             if (e != cudaSuccess) return cuda_fail(e, "stream fork");
+            forked = true;
         }
-    }
-    for (; done < n; ++done) {
         st = one_step(lb, false, sL, sH);
         if (st != IBL_OK) return st;
+        ++lb->steps_eager;
+        ++done;
     }
     // the bound stream resumes after all helper-stream work
-    e = join(sH, sL, lb->evJoin);
-    if (e != cudaSuccess) return cuda_fail(e, "stream join");
+    if (forked) {
+        e = join(sH, sL, lb->evJoin);
+        if (e != cudaSuccess) return cuda_fail(e, "stream join");
+    }
+    return IBL_OK;
+}
+
+int ibl_step_paths(const ibl_lb *lb, long long *eager, long long *replayed)
+{
+    if (!lb || !eager || !replayed) return fail(IBL_EINVAL, "null argument");
+    *eager = lb->steps_eager;
+    *replayed = lb->steps_replayed;
     return IBL_OK;
 }
 
@@ -1514,7 +1637,7 @@ int ibl_ensemble_create(int n, ibl_lb *const *members, void *workspace, size_t b
     const ibl_lb *m0 = members[0];
     std::vector<LbView> lv;
     std::vector<MeshView> mv;
-    std::vector<int> lat_member, lat_start, node_member, node_start;
+    std::vector<int> lat_member[2], lat_start[2], node_member, node_start;
     for (int k = 0; k < n; ++k) {
         const ibl_lb *lb = members[k];
         if (lb->p.precision != m0->p.precision) return fail(IBL_EINVAL, "members differ in precision");
@@ -1525,13 +1648,15 @@ int ibl_ensemble_create(int n, ibl_lb *const *members, void *workspace, size_t b
             if (members[j] == lb) return fail(IBL_EINVAL, "a lattice appears twice");
         lv.push_back(lb->v);
         mv.push_back(lb->mesh->v);
-        lat_start.push_back((int)lat_member.size());
-        for (int b = 0; b < (lb->v.nodes + 255) / 256; ++b) lat_member.push_back(k);
+        for (int t = 0; t < 2; ++t) {
+            lat_start[t].push_back((int)lat_member[t].size());
+            for (long long b = 0; b < lattice_blocks(lb, t == 0 ? 128 : 256); ++b) lat_member[t].push_back(k);
+        }
         node_start.push_back((int)node_member.size());
         for (int b = 0; b < (lb->mesh->v.nv + iblb::kFwdNodesPerBlock - 1) / iblb::kFwdNodesPerBlock; ++b)
             node_member.push_back(k);
     }
-    lat_start.push_back((int)lat_member.size());
+    for (int t = 0; t < 2; ++t) lat_start[t].push_back((int)lat_member[t].size());
     node_start.push_back((int)node_member.size());
     char *w = static_cast<char *>(workspace);
     cudaStream_t s = m0->stream;
@@ -1539,8 +1664,10 @@ int ibl_ensemble_create(int n, ibl_lb *const *members, void *workspace, size_t b
     auto up = [&](size_t off, const void *src, size_t nbytes) {
         if (e == cudaSuccess) e = cudaMemcpyAsync(w + off, src, nbytes, cudaMemcpyHostToDevice, s);
     };
-    up(L.lat_member, lat_member.data(), sizeof(int) * lat_member.size());
-    up(L.lat_start, lat_start.data(), sizeof(int) * lat_start.size());
+    for (int t = 0; t < 2; ++t) {
+        up(L.lat_member[t], lat_member[t].data(), sizeof(int) * lat_member[t].size());
+        up(L.lat_start[t], lat_start[t].data(), sizeof(int) * lat_start[t].size());
+    }
     up(L.node_member, node_member.data(), sizeof(int) * node_member.size());
     up(L.node_start, node_start.data(), sizeof(int) * node_start.size());
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host tables are temporaries
@@ -1551,13 +1678,16 @@ int ibl_ensemble_create(int n, ibl_lb *const *members, void *workspace, size_t b
     iblb::EnsembleView &v = en->v;
     v.lv = lv;
     v.mv = mv;
-    v.lat_member = reinterpret_cast<const int *>(w + L.lat_member);
-    v.lat_start_d = reinterpret_cast<const int *>(w + L.lat_start);
+    for (int t = 0; t < 2; ++t) {
+        v.lat_member[t] = reinterpret_cast<const int *>(w + L.lat_member[t]);
+        v.lat_start_d[t] = reinterpret_cast<const int *>(w + L.lat_start[t]);
+        v.lat_start[t] = lat_start[t];
+    }
     v.node_member = reinterpret_cast<const int *>(w + L.node_member);
     v.node_start_d = reinterpret_cast<const int *>(w + L.node_start);
-    v.lat_start = lat_start;
     v.node_start = node_start;
     v.precision = m0->p.precision;
+    v.shape = iblb::kEnsDefaultShape;
     *out = en;
     return IBL_OK;
 }
@@ -1565,47 +1695,133 @@ int ibl_ensemble_create(int n, ibl_lb *const *members, void *workspace, size_t b
 int ibl_ensemble_step(ibl_ensemble *en, long long n)
 {
     if (!en || n < 0) return fail(IBL_EINVAL, "bad ensemble step request");
+    if (n == 0) return IBL_OK;
     const long long h0 = en->m[0]->host_step;
     for (ibl_lb *lb : en->m)
         if (lb->host_step != h0 || !lb->mesh) return fail(IBL_EINVAL, "members were stepped apart from the ensemble");
+    int st = ensemble_streams(en);
+    if (st != IBL_OK) return st;
+    cudaStream_t sL = en->stream, sH = en->helper;
+    cudaError_t e = join(sL, sH, en->evFork);
+    if (e != cudaSuccess) return cuda_fail(e, "stream fork");
+    bool forked = true;
     const int chunk = ensemble_chunk(en);
     long long done = 0;
-    if (chunk > 0) {
-        while (done < n && en->m[0]->host_step % chunk != 0) {
-            const int st = ensemble_one_step(en, en->stream);
-            if (st != IBL_OK) return st;
-            ++done;
+    auto replay = [&](cudaGraphExec_t g, int len) -> int {
+        if (forked) {
+            e = join(sH, sL, en->evJoin);
+            if (e != cudaSuccess) return cuda_fail(e, "stream join");
+            forked = false;
         }
-        if (n - done >= chunk) {
-            if (en->chunk != chunk) {
-                if (en->gexec) {
-                    cudaGraphExecDestroy(en->gexec);
-                    en->gexec = nullptr;
+        e = cudaGraphLaunch(g, sL);
+        if (e != cudaSuccess) return cuda_fail(e, "ensemble graph launch");
+        for (ibl_lb *lb : en->m) lb->host_step += len;
+        done += len;
+        return IBL_OK;
+    };
+    while (done < n) {
+        const long long s0 = en->m[0]->host_step;
+        if (chunk > 0 && s0 % chunk == 0 && n - done >= chunk) {
+            if (en->chunk != chunk || !en->gexec) {
+                ensemble_drop_graphs(en);
+                st = ensemble_capture(en, chunk, &en->gexec);
+                if (st != IBL_OK) {
+                    ensemble_drop_graphs(en);
+                    return st;
                 }
-                const int st = ensemble_capture(en, chunk);
-                if (st != IBL_OK) return st;
+                en->chunk = chunk;
             }
-            while (n - done >= chunk) {
-                const cudaError_t e = cudaGraphLaunch(en->gexec, en->stream);
-                if (e != cudaSuccess) return cuda_fail(e, "ensemble graph launch");
-                for (ibl_lb *lb : en->m) lb->host_step += chunk;
-                done += chunk;
-            }
+            st = replay(en->gexec, chunk);
+            if (st != IBL_OK) return st;
+            continue;
         }
-    }
-    for (; done < n; ++done) {
-        const int st = ensemble_one_step(en, en->stream);
+        if (!forked) {
+            e = join(sL, sH, en->evFork);
+            if (e != cudaSuccess) return cuda_fail(e, "stream fork");
+            forked = true;
+        }
+        st = ensemble_one_step(en, sL, sH);
         if (st != IBL_OK) return st;
+        ++done;
+    }
+    if (forked) {
+        e = join(sH, sL, en->evJoin);
+        if (e != cudaSuccess) return cuda_fail(e, "stream join");
     }
     return IBL_OK;
+}
+
+int ibl_ensemble_set_shape(ibl_ensemble *en, int shape)
+{
+    if (!en || shape < 0 || shape >= IBL_ENSEMBLE_SHAPES) return fail(IBL_EINVAL, "bad ensemble launch shape");
+    cudaStreamSynchronize(en->stream);
+    en->v.shape = shape;
+    ensemble_drop_graphs(en);  // captured chunks hold the launch shape
+    return IBL_OK;
+}
+
+int ibl_ensemble_shape(const ibl_ensemble *en, int *shape, int *threads, int *prefetch_waves)
+{
+    if (!en) return fail(IBL_EINVAL, "null ensemble");
+    if (shape) *shape = en->v.shape;
+    if (threads) *threads = iblb::ens_shape_threads(en->v.shape);
+    if (prefetch_waves) *prefetch_waves = iblb::ens_shape_waves(en->v.shape);
+    return IBL_OK;
+}
+
+int ibl_ensemble_tune(ibl_ensemble *en, int steps_per_candidate, double *ms, int *chosen)
+{
+    if (!en || steps_per_candidate < 1) return fail(IBL_EINVAL, "bad tuning request");
+    const long long h0 = en->m[0]->host_step;
+    for (ibl_lb *lb : en->m)
+        if (lb->host_step != h0 || !lb->mesh) return fail(IBL_EINVAL, "members were stepped apart from the ensemble");
+    int st = ensemble_streams(en);
+    if (st != IBL_OK) return st;
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    if (e != cudaSuccess) return cuda_fail(e, "tuning events");
+    cudaStream_t sL = en->stream, sH = en->helper;
+    double best = 1e300;
+    int best_k = en->v.shape;
+    for (int k = 0; k < IBL_ENSEMBLE_SHAPES && st == IBL_OK; ++k) {
+        en->v.shape = k;
+        float t = 0.f;
+        for (int pass = 0; pass < 2 && st == IBL_OK; ++pass) {
+            // pass 0: two untimed steps; pass 1: the timed ones
+            const int n = pass == 0 ? 2 : steps_per_candidate;
+            e = join(sL, sH, en->evFork);
+            if (e == cudaSuccess && pass == 1) e = cudaEventRecord(a, sL);
+            for (int j = 0; j < n && st == IBL_OK && e == cudaSuccess; ++j) st = ensemble_one_step(en, sL, sH);
+            if (st == IBL_OK && e == cudaSuccess) e = join(sH, sL, en->evJoin);
+            if (e == cudaSuccess && pass == 1) e = cudaEventRecord(b, sL);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(sL);
+            if (e == cudaSuccess && pass == 1) e = cudaEventElapsedTime(&t, a, b);
+            if (e != cudaSuccess) st = cuda_fail(e, "tuning run");
+        }
+        if (st != IBL_OK) break;
+        const double per = (double)t / steps_per_candidate;
+        if (ms) ms[k] = per;
+        if (per < best) {
+            best = per;
+            best_k = k;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    en->v.shape = best_k;
+    ensemble_drop_graphs(en);
+    if (chosen) *chosen = best_k;
+    if (st != IBL_OK) return st;
+    return ibl_ensemble_sync(en);
 }
 
 int ibl_ensemble_sync(ibl_ensemble *en)
 {
     if (!en) return fail(IBL_EINVAL, "null ensemble");
-    for (ibl_lb *lb : en->m) {
-        const int st = lb_status_from_device(lb);
-        if (st != IBL_OK) return st;
+    for (size_t k = 0; k < en->m.size(); ++k) {
+        const int st = lb_status_from_device(en->m[k]);
+        if (st != IBL_OK) return fail(st, "ensemble member " + std::to_string(k) + ": " + g_err);
     }
     return IBL_OK;
 }

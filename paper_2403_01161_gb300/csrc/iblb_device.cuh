@@ -154,14 +154,33 @@ struct L2Keep {
     }
 };
 
+// The same interface with the default policy (plain loads, stores and
+// reductions), for the batched ensemble kernels: the droplet-side working
+// set of many members together exceeds L2, where lines kept with evict_last
+// would only displace the lattice update's reuse.
+struct L2Plain {
+    template <class V>
+    __device__ __forceinline__ V ld(const V *a) const
+    {
+        return *a;
+    }
+    template <class V>
+    __device__ __forceinline__ void st(V *a, V v) const
+    {
+        *a = v;
+    }
+    __device__ __forceinline__ void red_add(float *a, float v) const { atomicAdd(a, v); }
+    __device__ __forceinline__ void red_add(double *a, double v) const { atomicAdd(a, v); }
+};
+
 struct NodeStencil {
     int base[3];
     double frac[3];
     bool ok;
 };
-template <int LANES = kLanesPerNode>
+template <int LANES = kLanesPerNode, class P = L2Keep>
 __device__ __forceinline__ NodeStencil node_stencil(const LbView &L, const double *r, int lane,
-                                                    const L2Keep *keep = nullptr)
+                                                    const P *keep = nullptr)
 {
     double ra = 0.0, fr = 0.0;
     int base = 0;
@@ -254,7 +273,8 @@ __device__ __forceinline__ void tri_force(const MeshView &M, const int t, const 
 // evaluated once per step instead of once per corner: tri_moment gives m_t
 // = -sigma N_t / (2 |N_t|) (the m of tri_force<double>, bit for bit), and
 // tri_force_m the force on corner `slot` from a stored m_t.
-__device__ __forceinline__ void tri_moment(const MeshView &M, const int t, double m[3], const L2Keep &K)
+template <class P>
+__device__ __forceinline__ void tri_moment(const MeshView &M, const int t, double m[3], const P &K)
 {
     double x[3][3];
     for (int k = 0; k < 3; ++k) {
@@ -271,8 +291,9 @@ __device__ __forceinline__ void tri_moment(const MeshView &M, const int t, doubl
     for (int a = 0; a < 3; ++a) m[a] = s * N[a];
 }
 
+template <class P>
 __device__ __forceinline__ void tri_force_m(const MeshView &M, const int t, const int slot, const double m[3],
-                                            double g[3], const L2Keep &K)
+                                            double g[3], const P &K)
 {
     const int kp = slot == 2 ? 0 : slot + 1, km = slot == 0 ? 2 : slot - 1;
     const int vp = K.ld(M.tris + 3 * t + kp), vm = K.ld(M.tris + 3 * t + km);

@@ -43,6 +43,7 @@ struct LbView {
     int rule;           // IBL_EDGE_*
     double omega;       // 1 / tau
     float omega_f;
+    float inv_nx;       // 1 / n[0] (rounded): row of a node within its z plane in the batched lattice kernel
     void *f;            // [19][qs]
     void *force;        // [3][nodes]
     void *vel;          // [3][nodes]
@@ -97,15 +98,31 @@ struct MeshGroup {
     MeshView v[kGroup];
 };
 
+// Launch shapes of the ensemble step, the candidates of ibl_ensemble_tune:
+// shape k = 4 p + 2 t + w takes w resident waves of blocks of L2 prefetch
+// distance and 128 (t = 0) or 256 (t = 1) threads per block in the batched
+// lattice update (each block takes that many consecutive nodes of one z
+// plane of one member), and with p = 0 keeps the droplet-side working set
+// in L2 (evict_last, as the single droplet does), with p = 1 the default
+// policy.
+constexpr int kEnsShapes = IBL_ENSEMBLE_SHAPES;
+constexpr int ens_shape_waves(int k) { return k & 1; }
+constexpr int ens_shape_threads(int k) { return (k & 2) ? 256 : 128; }
+constexpr bool ens_shape_keep(int k) { return (k & 4) == 0; }
+constexpr int kEnsDefaultShape = 5;
+
 struct EnsembleView {
     std::vector<LbView> lv;      // host copies of the member views
     std::vector<MeshView> mv;
-    const int *lat_member;       // [lat blocks] member of each lattice block (device)
+    // lattice block tables, one per block size (index 0: 128 threads, 1: 256)
+    const int *lat_member[2];    // [lat blocks] member of each lattice block (device)
+    const int *lat_start_d[2];   // [n+1] first block of each member (device)
+    std::vector<int> lat_start[2];  // host copies
     const int *node_member;      // [node blocks]
-    const int *lat_start_d;      // [n+1] first block of each member (device)
     const int *node_start_d;
-    std::vector<int> lat_start, node_start;  // host copies
+    std::vector<int> node_start;
     int precision;
+    int shape;                   // kEnsShapes index of the batched lattice launch
 };
 
 // Discrete adjoint of one step (device pointers in the adjoint workspace).
@@ -149,7 +166,16 @@ cudaError_t launch_regularize(const LbView &L, const MeshView &M, const RegParam
                               int prio = 0);
 cudaError_t launch_observables(const LbView &L, const MeshView &M, cudaStream_t s, int prio = 0);
 cudaError_t launch_patch_from_mesh(const LbView &L, const MeshView &M, int buf, cudaStream_t s);
-cudaError_t launch_ensemble_step(const EnsembleView &E, long long step, cudaStream_t s);
+// Ensemble step phases (two streams, as the single droplet's step):
+// helper stream: pre (centre, triangle moments, forces + spread of the next
+// patch) then near (patch nodes, after the previous far update) then interp;
+// bound stream: far (nodes outside each member's patch, closes each
+// member's step, after the previous near update).
+constexpr int kEnsNearBlocks = 48;  // blocks per member of the batched patch-node kernel
+cudaError_t launch_ensemble_pre(const EnsembleView &E, long long step, cudaStream_t s, int prio);
+cudaError_t launch_ensemble_near(const EnsembleView &E, long long step, cudaStream_t s, int prio);
+cudaError_t launch_ensemble_far(const EnsembleView &E, long long step, cudaStream_t s);
+cudaError_t launch_ensemble_interp(const EnsembleView &E, cudaStream_t s, int prio);
 
 // adjoint kernels (iblb_adjoint.cu); Mt.r holds the positions r_t of the
 // step, pc the control block recorded before it (its patch)

@@ -16,6 +16,7 @@
 // touched: the spread adds into it, the lattice kernel reads and re-zeroes it
 // and stores the velocity there, the interpolation reads it.
 #include <cooperative_groups.h>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -174,7 +175,10 @@ __device__ __forceinline__ void bc_dispatch(T (&f)[19], const T (&uw)[3], int ru
 // and written by one node only within a step.
 enum { LAT_FULL = 0, LAT_FAR = 1, LAT_NEAR = 2 };
 
-template <typename T, bool ODD, bool REC, int MODE>
+// PER: some axis may be periodic (false: every axis has Zou-He walls, so
+// the neighbour offsets are fixed and only the boundary tests remain).
+// P: L2 policy of the patch nodes' accesses (LAT_NEAR).
+template <typename T, bool ODD, bool REC, int MODE, bool PER, class P = L2Keep>
 __device__ __forceinline__ bool lattice_node(const LbView &L, const int x, const int y, const int z, const int pbuf)
 {
     const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
@@ -189,10 +193,10 @@ __device__ __forceinline__ bool lattice_node(const LbView &L, const int x, const
         T *__restrict__ f = static_cast<T *>(L.f);
         // the patch nodes keep their lines in L2 between steps (see L2Keep)
         struct NoKeep {};
-        [[maybe_unused]] const std::conditional_t<MODE == LAT_NEAR, L2Keep, NoKeep> K;
+        [[maybe_unused]] const std::conditional_t<MODE == LAT_NEAR, P, NoKeep> K;
         const int qs = (int)L.qs;
-        const bool px = L.bc[0] == IBL_BC_PERIODIC, py = L.bc[1] == IBL_BC_PERIODIC,
-                   pz = L.bc[2] == IBL_BC_PERIODIC;
+        const bool px = PER && L.bc[0] == IBL_BC_PERIODIC, py = PER && L.bc[1] == IBL_BC_PERIODIC,
+                   pz = PER && L.bc[2] == IBL_BC_PERIODIC;
         const int sx = px ? 0 : (x == 0 ? -1 : (x == nx - 1 ? 1 : 0));
         const int sy = py ? 0 : (y == 0 ? -1 : (y == ny - 1 ? 1 : 0));
         const int sz = pz ? 0 : (z == 0 ? -1 : (z == nz - 1 ? 1 : 0));
@@ -395,7 +399,7 @@ __device__ __forceinline__ void close_step(const LbView &L)
     L.ctl->frame_par[s & 1] = (int)(k < L.n_frames - 1 ? k : L.n_frames - 1);
 }
 
-template <typename T, bool ODD, bool REC, int MODE>
+template <typename T, bool ODD, bool REC, int MODE, bool PER>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 4) k_lattice(LbView L, int pbuf, int ahead)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -414,14 +418,14 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 4) k_lattice(LbView 
         for (int i = 0; i < 19; ++i) asm volatile("prefetch.global.L2 [%0];" ::"l"(f + i * qs + na));
     }
     bool bad = false;
-    if (x < L.n[0] && y < L.n[1]) bad = lattice_node<T, ODD, REC, MODE>(L, x, y, z, pbuf);
+    if (x < L.n[0] && y < L.n[1]) bad = lattice_node<T, ODD, REC, MODE, PER>(L, x, y, z, pbuf);
     // sticky instability flag, one atomic per warp at most
     const unsigned m = __ballot_sync(0xffffffffu, bad);
     if (m != 0u && (threadIdx.x & 31) == 0) atomicOr(&L.ctl->err, IBL_ERRBIT_UNSTABLE);
 }
 
 // The patch nodes of the step (grid-stride over the patch box, x fastest).
-template <typename T, bool ODD, bool REC>
+template <typename T, bool ODD, bool REC, bool PER>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_lattice_near(LbView L, int buf)
 {
     const Ctl *c = L.ctl;
@@ -440,53 +444,87 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_lattice_near(Lb
             if (x >= L.n[0]) x -= L.n[0];  // a periodic patch may wrap once
             if (y >= L.n[1]) y -= L.n[1];
             if (z >= L.n[2]) z -= L.n[2];
-            bad = lattice_node<T, ODD, REC, LAT_NEAR>(L, x, y, z, buf);
+            bad = lattice_node<T, ODD, REC, LAT_NEAR, PER>(L, x, y, z, buf);
         }
         const unsigned m = __ballot_sync(0xffffffffu, bad);
         if (m != 0u && (threadIdx.x & 31) == 0) atomicOr(&L.ctl->err, IBL_ERRBIT_UNSTABLE);
     }
 }
 
-// Ensemble: one launch over the lattices of a group of members.  Block b
-// works for member blk_member[b0 + b] (view G.v[member - m0], read from the
-// kernel parameters) and covers its 256 consecutive nodes starting at
-// 256 * (b0 + b - blk_start[member]) in x-fastest order.
-template <typename T, bool ODD>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
+// Ensemble: the nodes outside each member's droplet patch, one launch over
+// the lattices of a group of members (the patches are updated concurrently
+// by k_lattice_near_batched on the helper stream).  Block b works for member
+// blk_member[b0 + b] (view G.v[member - m0], read from the kernel
+// parameters) as its local block l = b0 + b - blk_start[member]: NT
+// consecutive nodes of z plane l / bpp (bpp = blocks per plane) in x-fastest
+// order, starting at node (l mod bpp) NT of the plane; the row of a node is
+// p / n_x, taken as floor((p + 1/2) inv_nx), exact while n_x n_y < 2^22 (the
+// fraction of (p + 1/2)/n_x stays 1/(2 n_x) away from an integer, more than
+// the float rounding).  The first thread of a member's first block closes
+// that member's step, as the single-droplet far kernel does.  Each thread
+// prefetches into L2 its (x, y) `ahead` planes further (about `waves`
+// resident waves of blocks later).
+template <typename T, bool ODD, int NT, bool PER>
+__global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 1024 : 512) / NT)
     k_lattice_batched(const __grid_constant__ LbGroup G, const int m0, const int b0,
                       const int *__restrict__ blk_member, const int *__restrict__ blk_start, const int pbuf,
-                      const int ahead)
+                      const int ahead_nodes)
 {
     const int mi = blk_member[b0 + blockIdx.x];
     const LbView &L = G.v[mi - m0];
-    const int nx = L.n[0], ny = L.n[1];
-    const int lin0 = (b0 + (int)blockIdx.x - blk_start[mi]) * 256;
-    // L2 prefetch of the node `ahead` positions further in the same member
-    // (about one resident wave of blocks later), as in k_lattice
-    const int la = lin0 + (int)threadIdx.x + ahead;
-    if (la < L.nodes) {
-        const T *f = static_cast<const T *>(L.f);
-        const int qs = (int)L.qs;
+    const int nx = L.n[0], nxy = L.n[0] * L.n[1];
+    const int bpp = (nxy + NT - 1) / NT;
+    const int lb = b0 + (int)blockIdx.x - blk_start[mi];
+    const int z = lb / bpp;
+    const int p = (lb - z * bpp) * NT + (int)threadIdx.x;
+    if (lb == 0 && threadIdx.x == 0) close_step(L);
+    if (ahead_nodes > 0) {
+        const int za = z + (ahead_nodes + nxy - 1) / nxy;
+        if (za < L.n[2] && p < nxy) {
+            const T *f = static_cast<const T *>(L.f);
+            const int na = p + nxy * za;
+            const int qs = (int)L.qs;
 #pragma unroll
-        for (int i = 0; i < 19; ++i) asm volatile("prefetch.global.L2 [%0];" ::"l"(f + i * qs + la));
-    }
-    const int nxy = nx * ny;
-    const int z0 = lin0 / nxy;
-    const int rem = lin0 - z0 * nxy;
-    const int y0 = rem / nx;
-    int x = rem - y0 * nx + (int)threadIdx.x, y = y0, z = z0;
-    while (x >= nx) {  // at most 256 / nx carries
-        x -= nx;
-        ++y;
-    }
-    while (y >= ny) {
-        y -= ny;
-        ++z;
+            for (int i = 0; i < 19; ++i) asm volatile("prefetch.global.L2 [%0];" ::"l"(f + i * qs + na));
+        }
     }
     bool bad = false;
-    if (lin0 + (int)threadIdx.x < L.nodes) bad = lattice_node<T, ODD, false, LAT_FULL>(L, x, y, z, pbuf);
+    if (p < nxy) {
+        const int y = (int)(((float)p + 0.5f) * L.inv_nx);
+        bad = lattice_node<T, ODD, false, LAT_FAR, PER>(L, p - y * nx, y, z, pbuf);
+    }
     const unsigned m = __ballot_sync(0xffffffffu, bad);
     if (m != 0u && (threadIdx.x & 31) == 0) atomicOr(&L.ctl->err, IBL_ERRBIT_UNSTABLE);
+}
+
+// Ensemble: the patch nodes of every member of a group (blockIdx.y is the
+// member within the group), grid-stride over each member's patch box.
+template <typename T, bool ODD, bool PER, class P>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_lattice_near_batched(const __grid_constant__ LbGroup G,
+                                                                                    const int buf)
+{
+    const LbView &L = G.v[blockIdx.y];
+    const Ctl *c = L.ctl;
+    const int ex = c->patch_ext[buf][0] + 1, ey = c->patch_ext[buf][1] + 1, ez = c->patch_ext[buf][2] + 1;
+    const int lx = c->patch_lo[buf][0], ly = c->patch_lo[buf][1], lz = c->patch_lo[buf][2];
+    const int count = (ex > 0 && ey > 0 && ez > 0) ? ex * ey * ez : 0;
+    for (int base = blockIdx.x * blockDim.x; base < count; base += gridDim.x * blockDim.x) {
+        const int idx = base + threadIdx.x;
+        bool bad = false;
+        if (idx < count) {
+            const int pz = idx / (ex * ey);
+            const int rem = idx - pz * ex * ey;
+            const int py = rem / ex;
+            const int px = rem - py * ex;
+            int x = lx + px, y = ly + py, z = lz + pz;
+            if (x >= L.n[0]) x -= L.n[0];  // a periodic patch may wrap once
+            if (y >= L.n[1]) y -= L.n[1];
+            if (z >= L.n[2]) z -= L.n[2];
+            bad = lattice_node<T, ODD, false, LAT_NEAR, PER, P>(L, x, y, z, buf);
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, bad);
+        if (m != 0u && (threadIdx.x & 31) == 0) atomicOr(&L.ctl->err, IBL_ERRBIT_UNSTABLE);
+    }
 }
 
 
@@ -555,11 +593,12 @@ __device__ void write_patch(const LbView &L, const double mn[3], const double mx
 // bounding-box rows of r_t left by the previous interpolation (or
 // regularisation) into the patch of step t + 1, grown by one node, in
 // buffer `buf` (the parity of step t + 1).
+template <class P>
 __device__ void patch_from_rows(const LbView &L, const MeshView &M, int buf)
 {
     const int lane = threadIdx.x & 31;
     const int rows = L.ctl->n_part;
-    const L2Keep K;
+    const P K;
     double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
     for (int k = lane; k < rows; k += 32)
         for (int a = 0; a < 3; ++a) {
@@ -583,15 +622,15 @@ __device__ void patch_from_rows(const LbView &L, const MeshView &M, int buf)
 // otherwise each lane evaluates it for its triangle (three times per
 // triangle in all, but one kernel boundary fewer on the droplet chain of a
 // single droplet, which is latency bound).
-template <typename T, bool STORED, int LANES>
+template <typename T, bool STORED, int LANES, class P = L2Keep>
 __device__ __forceinline__ void spread_body(const LbView &L, const MeshView &M, const int blk, const int next_buf)
 {
-    if (blk == 0 && threadIdx.x < 32) patch_from_rows(L, M, next_buf);
+    if (blk == 0 && threadIdx.x < 32) patch_from_rows<P>(L, M, next_buf);
     const int gid = blk * (kIbThreads / LANES) + threadIdx.x / LANES;
     const int lane = threadIdx.x % LANES;
     const bool valid = gid < M.nv;
     const int i = valid ? gid : M.nv - 1;
-    const L2Keep K;
+    const P K;
     double F[3] = {0.0, 0.0, 0.0};
     const int k0 = K.ld(M.n2t_ptr + i), k1 = K.ld(M.n2t_ptr + i + 1);
     for (int k = k0 + lane; k < k1; k += LANES) {
@@ -614,7 +653,7 @@ __device__ __forceinline__ void spread_body(const LbView &L, const MeshView &M, 
         M.fn[3 * i + 1] = F[1];
         M.fn[3 * i + 2] = F[2];
     }
-    const NodeStencil S = node_stencil<LANES>(L, M.r + 3 * i, lane, &K);
+    const NodeStencil S = node_stencil<LANES, P>(L, M.r + 3 * i, lane, &K);
     if (!valid) return;
     if (!S.ok) {
         if (lane == 0) atomicOr(&L.ctl->err, IBL_ERRBIT_WALL);
@@ -647,12 +686,13 @@ __device__ __forceinline__ void spread_body(const LbView &L, const MeshView &M, 
 // Ensemble: m_t of every triangle of every member at the current positions
 // (Eq. (pi_drop)), once per step, for the batched force kernel that follows
 // on the same stream; blockIdx.y is the member within the group.
+template <class P>
 __global__ void __launch_bounds__(128) k_tri_moment_batched(const __grid_constant__ MeshGroup MG)
 {
     const MeshView &M = MG.v[blockIdx.y];
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= M.nt) return;
-    const L2Keep K;
+    const P K;
     double m[3];
     tri_moment(M, t, m, K);
     for (int a = 0; a < 3; ++a) K.st(M.tm + 3 * t + a, m[a]);
@@ -782,15 +822,15 @@ __global__ void __launch_bounds__(kCentreThreads)
     centre_of_mass(LG.v[blockIdx.y], MG.v[blockIdx.y], blockIdx.x, buf);
 }
 
-template <typename T, int LANES>
+template <typename T, int LANES, class P = L2Keep>
 __device__ __forceinline__ void interp_body(const LbView &L, const MeshView &M, const int blk, const int nblk)
 {
     const int gid = blk * (kIbThreads / LANES) + threadIdx.x / LANES;
     const int lane = threadIdx.x % LANES;
     const bool valid = gid < M.nv;
     const int i = valid ? gid : M.nv - 1;
-    const L2Keep K;
-    const NodeStencil S = node_stencil<LANES>(L, M.r + 3 * i, lane, &K);
+    const P K;
+    const NodeStencil S = node_stencil<LANES, P>(L, M.r + 3 * i, lane, &K);
     T v[3] = {T(0), T(0), T(0)};
     if (S.ok) {
         const bool perx = L.bc[0] == IBL_BC_PERIODIC, pery = L.bc[1] == IBL_BC_PERIODIC,
@@ -871,33 +911,27 @@ __global__ void __launch_bounds__(128) k_interp(LbView L, MeshView M)
     interp_body<T, LANES>(L, M, blockIdx.x, gridDim.x);
 }
 
-// Closes the step of every member of a group (one thread per member).
-__global__ void k_advance_batched(const __grid_constant__ LbGroup LG, const int count)
-{
-    if ((int)threadIdx.x < count) close_step(LG.v[threadIdx.x]);
-}
-
 // Ensemble versions: block b works for member blk_member[b0 + b] as its
 // local block b0 + b - blk_start[member]; node-group kernels use ceil(nv/8)
 // blocks per member.
 
-template <typename T>
+template <typename T, class P>
 __global__ void __launch_bounds__(128)
     k_spread_batched(const __grid_constant__ LbGroup LG, const __grid_constant__ MeshGroup MG, const int m0,
                      const int b0, const int *__restrict__ blk_member, const int *__restrict__ blk_start,
                      const int next_buf)
 {
     const int mi = blk_member[b0 + blockIdx.x];
-    spread_body<T, true, kFwdLanes>(LG.v[mi - m0], MG.v[mi - m0], b0 + (int)blockIdx.x - blk_start[mi], next_buf);
+    spread_body<T, true, kFwdLanes, P>(LG.v[mi - m0], MG.v[mi - m0], b0 + (int)blockIdx.x - blk_start[mi], next_buf);
 }
 
-template <typename T>
+template <typename T, class P>
 __global__ void __launch_bounds__(128)
     k_interp_batched(const __grid_constant__ LbGroup LG, const __grid_constant__ MeshGroup MG, const int m0,
                      const int b0, const int *__restrict__ blk_member, const int *__restrict__ blk_start)
 {
     const int mi = blk_member[b0 + blockIdx.x];
-    interp_body<T, kFwdLanes>(LG.v[mi - m0], MG.v[mi - m0], b0 + (int)blockIdx.x - blk_start[mi],
+    interp_body<T, kFwdLanes, P>(LG.v[mi - m0], MG.v[mi - m0], b0 + (int)blockIdx.x - blk_start[mi],
                    blk_start[mi + 1] - blk_start[mi]);
 }
 
@@ -1377,14 +1411,24 @@ static void lattice_grid(const LbView &L, dim3 &grid, dim3 &block)
     grid = dim3((L.n[0] + bx - 1) / bx, (L.n[1] + by - 1) / by, L.n[2]);
 }
 
+static bool any_periodic(const LbView &L)
+{
+    return L.bc[0] == IBL_BC_PERIODIC || L.bc[1] == IBL_BC_PERIODIC || L.bc[2] == IBL_BC_PERIODIC;
+}
+
 template <typename T, bool ODD, bool REC>
 static void lattice_launch_t(const LbView &L, int mode, int pbuf, dim3 g, dim3 b, cudaStream_t s)
 {
     // prefetch distance: the z-planes one wave of resident blocks covers
     const long long wave = (long long)sm_count() * (sizeof(T) == 4 ? 8 : 4), plane = (long long)g.x * g.y;
     const int ahead = (int)((wave + plane - 1) / plane);
-    if (mode == LAT_FAR) k_lattice<T, ODD, REC, LAT_FAR><<<g, b, 0, s>>>(L, pbuf, ahead);
-    else k_lattice<T, ODD, REC, LAT_FULL><<<g, b, 0, s>>>(L, pbuf, ahead);
+    if (any_periodic(L)) {
+        if (mode == LAT_FAR) k_lattice<T, ODD, REC, LAT_FAR, true><<<g, b, 0, s>>>(L, pbuf, ahead);
+        else k_lattice<T, ODD, REC, LAT_FULL, true><<<g, b, 0, s>>>(L, pbuf, ahead);
+    } else {
+        if (mode == LAT_FAR) k_lattice<T, ODD, REC, LAT_FAR, false><<<g, b, 0, s>>>(L, pbuf, ahead);
+        else k_lattice<T, ODD, REC, LAT_FULL, false><<<g, b, 0, s>>>(L, pbuf, ahead);
+    }
 }
 
 cudaError_t launch_lattice(const LbView &L, bool odd, bool record, int mode, int pbuf, cudaStream_t s)
@@ -1411,23 +1455,24 @@ cudaError_t launch_lattice(const LbView &L, bool odd, bool record, int mode, int
     return cudaGetLastError();
 }
 
-cudaError_t launch_near(const LbView &L, bool odd, bool record, int pbuf, cudaStream_t s, int prio)
+template <typename T, bool PER>
+static cudaError_t near_t(const LbView &L, bool odd, bool record, int pbuf, cudaStream_t s, int prio)
 {
     const dim3 g(2 * 152), b(256);  // grid-stride over the patch box
-    if (L.precision == IBL_FP64) {
-        if (odd) {
-            if (record) return launch_p(k_lattice_near<double, true, true>, g, b, s, prio, L, pbuf);
-            return launch_p(k_lattice_near<double, true, false>, g, b, s, prio, L, pbuf);
-        }
-        if (record) return launch_p(k_lattice_near<double, false, true>, g, b, s, prio, L, pbuf);
-        return launch_p(k_lattice_near<double, false, false>, g, b, s, prio, L, pbuf);
-    }
     if (odd) {
-        if (record) return launch_p(k_lattice_near<float, true, true>, g, b, s, prio, L, pbuf);
-        return launch_p(k_lattice_near<float, true, false>, g, b, s, prio, L, pbuf);
+        if (record) return launch_p(k_lattice_near<T, true, true, PER>, g, b, s, prio, L, pbuf);
+        return launch_p(k_lattice_near<T, true, false, PER>, g, b, s, prio, L, pbuf);
     }
-    if (record) return launch_p(k_lattice_near<float, false, true>, g, b, s, prio, L, pbuf);
-    return launch_p(k_lattice_near<float, false, false>, g, b, s, prio, L, pbuf);
+    if (record) return launch_p(k_lattice_near<T, false, true, PER>, g, b, s, prio, L, pbuf);
+    return launch_p(k_lattice_near<T, false, false, PER>, g, b, s, prio, L, pbuf);
+}
+
+cudaError_t launch_near(const LbView &L, bool odd, bool record, int pbuf, cudaStream_t s, int prio)
+{
+    const bool per = any_periodic(L);
+    if (L.precision == IBL_FP64)
+        return per ? near_t<double, true>(L, odd, record, pbuf, s, prio) : near_t<double, false>(L, odd, record, pbuf, s, prio);
+    return per ? near_t<float, true>(L, odd, record, pbuf, s, prio) : near_t<float, false>(L, odd, record, pbuf, s, prio);
 }
 
 template <typename T>
@@ -1552,46 +1597,182 @@ cudaError_t launch_patch_from_mesh(const LbView &L, const MeshView &M, int buf, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_ensemble_step(const EnsembleView &E, long long step, cudaStream_t s)
+// Ensemble phases.  Each launches one kernel per group of up to kGroup
+// members; the group's views travel in the kernel parameters.
+namespace {
+struct Groups {
+    // parameter blocks are large: kept off the stack
+    LbGroup lg;
+    MeshGroup mg;
+};
+Groups &groups()
+{
+    static thread_local Groups g;
+    return g;
+}
+void fill_group(const EnsembleView &E, int m0, int m1)
+{
+    Groups &G = groups();
+    for (int k = m0; k < m1; ++k) {
+        G.lg.v[k - m0] = E.lv[k];
+        G.mg.v[k - m0] = E.mv[k];
+    }
+}
+}  // namespace
+
+static int ens_shape(const EnsembleView &E) { return E.shape >= 0 && E.shape < kEnsShapes ? E.shape : kEnsDefaultShape; }
+
+template <class P>
+static cudaError_t ensemble_pre_t(const EnsembleView &E, int m0, int m1, int pbuf, int nxt, cudaStream_t s, int prio)
+{
+    Groups &G = groups();
+    bool recentre = false;
+    int nt_max = 0;
+    for (int k = m0; k < m1; ++k) {
+        recentre = recentre || E.lv[k].recentre != 0;
+        nt_max = E.mv[k].nt > nt_max ? E.mv[k].nt : nt_max;
+    }
+    cudaError_t e = cudaSuccess;
+    if (recentre)
+        e = launch_p(k_centre_batched, dim3(kCentreBlocks, m1 - m0), dim3(kCentreThreads), s, prio, G.lg, G.mg, pbuf);
+    if (e == cudaSuccess)
+        e = launch_p(k_tri_moment_batched<P>, dim3((nt_max + 127) / 128, m1 - m0), dim3(128), s, prio, G.mg);
+    const int nb0 = E.node_start[m0], nb = E.node_start[m1] - nb0;
+    if (e == cudaSuccess) {
+        if (E.precision == IBL_FP64)
+            e = launch_p(k_spread_batched<double, P>, dim3(nb), dim3(kIbThreads), s, prio, G.lg, G.mg, m0, nb0,
+                         E.node_member, E.node_start_d, nxt);
+        else
+            e = launch_p(k_spread_batched<float, P>, dim3(nb), dim3(kIbThreads), s, prio, G.lg, G.mg, m0, nb0,
+                         E.node_member, E.node_start_d, nxt);
+    }
+    return e;
+}
+
+cudaError_t launch_ensemble_pre(const EnsembleView &E, long long step, cudaStream_t s, int prio)
+{
+    const int pbuf = (int)(step % 3), nxt = (int)((step + 1) % 3);
+    const int n = (int)E.lv.size();
+    const bool keep = ens_shape_keep(ens_shape(E));
+    for (int m0 = 0; m0 < n; m0 += kGroup) {
+        const int m1 = m0 + kGroup < n ? m0 + kGroup : n;
+        fill_group(E, m0, m1);
+        const cudaError_t e = keep ? ensemble_pre_t<L2Keep>(E, m0, m1, pbuf, nxt, s, prio)
+                                   : ensemble_pre_t<L2Plain>(E, m0, m1, pbuf, nxt, s, prio);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+template <typename T, bool PER, class P>
+static cudaError_t ensemble_near_t(const EnsembleView &E, bool odd, int m0, int m1, int pbuf, cudaStream_t s, int prio)
+{
+    Groups &G = groups();
+    const dim3 g(kEnsNearBlocks, m1 - m0), b(256);
+    return odd ? launch_p(k_lattice_near_batched<T, true, PER, P>, g, b, s, prio, G.lg, pbuf)
+               : launch_p(k_lattice_near_batched<T, false, PER, P>, g, b, s, prio, G.lg, pbuf);
+}
+
+template <class P>
+static cudaError_t ensemble_near_p(const EnsembleView &E, bool odd, int m0, int m1, int pbuf, cudaStream_t s,
+                                   int prio)
+{
+    bool per = false;
+    for (int k = m0; k < m1; ++k) per = per || any_periodic(E.lv[k]);
+    if (E.precision == IBL_FP64)
+        return per ? ensemble_near_t<double, true, P>(E, odd, m0, m1, pbuf, s, prio)
+                   : ensemble_near_t<double, false, P>(E, odd, m0, m1, pbuf, s, prio);
+    return per ? ensemble_near_t<float, true, P>(E, odd, m0, m1, pbuf, s, prio)
+               : ensemble_near_t<float, false, P>(E, odd, m0, m1, pbuf, s, prio);
+}
+
+cudaError_t launch_ensemble_near(const EnsembleView &E, long long step, cudaStream_t s, int prio)
 {
     const bool odd = (step & 1) != 0;
     const int pbuf = (int)(step % 3);
     const int n = (int)E.lv.size();
-    // parameter blocks are large: keep them off the stack
-    static thread_local LbGroup lg;
-    static thread_local MeshGroup mg;
+    const bool keep = ens_shape_keep(ens_shape(E));
     for (int m0 = 0; m0 < n; m0 += kGroup) {
         const int m1 = m0 + kGroup < n ? m0 + kGroup : n;
-        for (int k = m0; k < m1; ++k) {
-            lg.v[k - m0] = E.lv[k];
-            mg.v[k - m0] = E.mv[k];
-        }
-        const int nb0 = E.node_start[m0], nb = E.node_start[m1] - nb0;
-        const int lb0 = E.lat_start[m0], lbn = E.lat_start[m1] - lb0;
-        const int nxt = (int)((step + 1) % 3);  // patch buffer of the next step
-        bool recentre = false;
-        for (int k = m0; k < m1; ++k) recentre = recentre || E.lv[k].recentre != 0;
-        // prefetch distance of the batched lattice kernel: one wave of resident blocks
-        const int ahead = sm_count() * (E.precision == IBL_FP64 ? 2 : 4) * 256;
-        if (recentre)
-            k_centre_batched<<<dim3(kCentreBlocks, m1 - m0), kCentreThreads, 0, s>>>(lg, mg, pbuf);
-        int nt_max = 0;
-        for (int k = m0; k < m1; ++k) nt_max = E.mv[k].nt > nt_max ? E.mv[k].nt : nt_max;
-        k_tri_moment_batched<<<dim3((nt_max + 127) / 128, m1 - m0), 128, 0, s>>>(mg);
+        fill_group(E, m0, m1);
+        const cudaError_t e = keep ? ensemble_near_p<L2Keep>(E, odd, m0, m1, pbuf, s, prio)
+                                   : ensemble_near_p<L2Plain>(E, odd, m0, m1, pbuf, s, prio);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+template <typename T, bool ODD, bool PER>
+static void far_batched_t(const EnsembleView &E, int m0, int pbuf, int waves, int ti, cudaStream_t s)
+{
+    const int m1 = m0 + kGroup < (int)E.lv.size() ? m0 + kGroup : (int)E.lv.size();
+    const int lb0 = E.lat_start[ti][m0], lbn = E.lat_start[ti][m1] - lb0;
+    const int nt = ti == 0 ? 128 : 256;
+    const int per_sm = (sizeof(T) == 4 ? 1024 : 512) / nt;
+    const int ahead = waves * sm_count() * per_sm * nt;
+    Groups &G = groups();
+    if (nt == 128)
+        k_lattice_batched<T, ODD, 128, PER><<<lbn, 128, 0, s>>>(G.lg, m0, lb0, E.lat_member[ti], E.lat_start_d[ti], pbuf, ahead);
+    else
+        k_lattice_batched<T, ODD, 256, PER><<<lbn, 256, 0, s>>>(G.lg, m0, lb0, E.lat_member[ti], E.lat_start_d[ti], pbuf, ahead);
+}
+
+cudaError_t launch_ensemble_far(const EnsembleView &E, long long step, cudaStream_t s)
+{
+    const bool odd = (step & 1) != 0;
+    const int pbuf = (int)(step % 3);
+    const int n = (int)E.lv.size();
+    const int shape = ens_shape(E);
+    const int ti = ens_shape_threads(shape) == 128 ? 0 : 1, waves = ens_shape_waves(shape);
+    for (int m0 = 0; m0 < n; m0 += kGroup) {
+        const int m1 = m0 + kGroup < n ? m0 + kGroup : n;
+        fill_group(E, m0, m1);
+        bool per = false;
+        for (int k = m0; k < m1; ++k) per = per || any_periodic(E.lv[k]);
         if (E.precision == IBL_FP64) {
-            k_spread_batched<double>
-                <<<nb, kIbThreads, 0, s>>>(lg, mg, m0, nb0, E.node_member, E.node_start_d, nxt);
-            if (odd) k_lattice_batched<double, true><<<lbn, 256, 0, s>>>(lg, m0, lb0, E.lat_member, E.lat_start_d, pbuf, ahead);
-            else k_lattice_batched<double, false><<<lbn, 256, 0, s>>>(lg, m0, lb0, E.lat_member, E.lat_start_d, pbuf, ahead);
-            k_interp_batched<double><<<nb, kIbThreads, 0, s>>>(lg, mg, m0, nb0, E.node_member, E.node_start_d);
+            if (per) {
+                if (odd) far_batched_t<double, true, true>(E, m0, pbuf, waves, ti, s);
+                else far_batched_t<double, false, true>(E, m0, pbuf, waves, ti, s);
+            } else {
+                if (odd) far_batched_t<double, true, false>(E, m0, pbuf, waves, ti, s);
+                else far_batched_t<double, false, false>(E, m0, pbuf, waves, ti, s);
+            }
         } else {
-            k_spread_batched<float><<<nb, kIbThreads, 0, s>>>(lg, mg, m0, nb0, E.node_member, E.node_start_d, nxt);
-            if (odd) k_lattice_batched<float, true><<<lbn, 256, 0, s>>>(lg, m0, lb0, E.lat_member, E.lat_start_d, pbuf, ahead);
-            else k_lattice_batched<float, false><<<lbn, 256, 0, s>>>(lg, m0, lb0, E.lat_member, E.lat_start_d, pbuf, ahead);
-            k_interp_batched<float><<<nb, kIbThreads, 0, s>>>(lg, mg, m0, nb0, E.node_member, E.node_start_d);
+            if (per) {
+                if (odd) far_batched_t<float, true, true>(E, m0, pbuf, waves, ti, s);
+                else far_batched_t<float, false, true>(E, m0, pbuf, waves, ti, s);
+            } else {
+                if (odd) far_batched_t<float, true, false>(E, m0, pbuf, waves, ti, s);
+                else far_batched_t<float, false, false>(E, m0, pbuf, waves, ti, s);
+            }
         }
-        k_advance_batched<<<1, kGroup, 0, s>>>(lg, m1 - m0);
         const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_ensemble_interp(const EnsembleView &E, cudaStream_t s, int prio)
+{
+    const int n = (int)E.lv.size();
+    const bool keep = ens_shape_keep(ens_shape(E));
+    Groups &G = groups();
+    for (int m0 = 0; m0 < n; m0 += kGroup) {
+        const int m1 = m0 + kGroup < n ? m0 + kGroup : n;
+        fill_group(E, m0, m1);
+        const int nb0 = E.node_start[m0], nb = E.node_start[m1] - nb0;
+        const dim3 g(nb), b(kIbThreads);
+        cudaError_t e;
+        if (E.precision == IBL_FP64)
+            e = keep ? launch_p(k_interp_batched<double, L2Keep>, g, b, s, prio, G.lg, G.mg, m0, nb0, E.node_member,
+                                E.node_start_d)
+                     : launch_p(k_interp_batched<double, L2Plain>, g, b, s, prio, G.lg, G.mg, m0, nb0, E.node_member,
+                                E.node_start_d);
+        else
+            e = keep ? launch_p(k_interp_batched<float, L2Keep>, g, b, s, prio, G.lg, G.mg, m0, nb0, E.node_member,
+                                E.node_start_d)
+                     : launch_p(k_interp_batched<float, L2Plain>, g, b, s, prio, G.lg, G.mg, m0, nb0, E.node_member,
+                                E.node_start_d);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -1691,8 +1872,44 @@ __global__ void __launch_bounds__(1024)
     }
 }
 
+// Device address of the array per device ordinal, with the id of the
+// context it was looked up in: the array is part of the module loaded into
+// that context, so another context (a driver-API context made current, or the
+// primary context created anew after cudaDeviceReset) holds it elsewhere.
+struct NoAllocSlot {
+    unsigned long long ctx_id;
+    double *ptr;
+};
 std::mutex g_noalloc_mu;
-double *g_noalloc_ptr[256] = {};  // device address of the array, per device ordinal
+NoAllocSlot g_noalloc_slot[256] = {};
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long *);
+
+// Id of the calling thread's current context (0 if there is none yet).
+// Called with g_noalloc_mu held.
+cudaError_t current_context_id(unsigned long long *id)
+{
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    *id = 0;
+    if (!get_current || !get_id) {
+        void *a = nullptr, *b = nullptr;
+        cudaDriverEntryPointQueryResult qa, qb;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa);
+        if (e == cudaSuccess)
+            e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb);
+        if (e != cudaSuccess) return e;
+        if (qa != cudaDriverEntryPointSuccess || qb != cudaDriverEntryPointSuccess || !a || !b)
+            return cudaErrorNotSupported;
+        get_current = reinterpret_cast<CtxGetCurrentFn>(a);
+        get_id = reinterpret_cast<CtxGetIdFn>(b);
+    }
+    CUcontext c = nullptr;
+    if (get_current(&c) != CUDA_SUCCESS) return cudaErrorUnknown;
+    if (!c) return cudaSuccess;
+    return get_id(c, id) == CUDA_SUCCESS ? cudaSuccess : cudaErrorUnknown;
+}
 
 }  // namespace
 }  // namespace iblb
@@ -1714,16 +1931,24 @@ extern "C" int ibl_regularize_noalloc(double *r, const int32_t *nb_ptr, const in
     if (dev < 0 || dev >= 256) return iblb_set_error(IBL_EINVAL, "device ordinal out of range");
     double *scratch = nullptr;
     {
-        // first call on this device: look up the array's device address with
-        // the device current (the name alone is a host-side stand-in)
+        // first call on this device, or first call in another context of
+        // it: look up the array's device address with the device current
+        // (the name alone is a host-side stand-in, not a device address)
         std::lock_guard<std::mutex> lock(g_noalloc_mu);
-        if (!g_noalloc_ptr[dev]) {
+        unsigned long long ctx = 0;
+        e = current_context_id(&ctx);
+        if (e != cudaSuccess) return iblb_set_error(IBL_ECUDA, cudaGetErrorString(e));
+        NoAllocSlot &slot = g_noalloc_slot[dev];
+        if (ctx == 0 || !slot.ptr || slot.ctx_id != ctx) {
             void *p = nullptr;
-            e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            e = cudaGetSymbolAddress(&p, g_noalloc_scratch);  // also creates the context if there is none yet
             if (e != cudaSuccess) return iblb_set_error(IBL_ECUDA, cudaGetErrorString(e));
-            g_noalloc_ptr[dev] = static_cast<double *>(p);
+            e = current_context_id(&ctx);
+            if (e != cudaSuccess) return iblb_set_error(IBL_ECUDA, cudaGetErrorString(e));
+            slot.ptr = static_cast<double *>(p);
+            slot.ctx_id = ctx;
         }
-        scratch = g_noalloc_ptr[dev];
+        scratch = slot.ptr;
     }
     RegParams p{alpha, gamma, tol, max_iter, plus_sign ? 1 : 0};
     k_regularize_noalloc<<<1, 1024, 0, static_cast<cudaStream_t>(stream)>>>(

@@ -185,6 +185,12 @@ class Sim:
         """Replay whole chunks of steps as a captured CUDA graph (default on)."""
         L.check(self.lib.ibl_set_graphs(self.h, 1 if enable else 0))
 
+    def step_paths(self):
+        """(steps run eagerly, steps run by graph replay) by step() so far."""
+        a, b = ctypes.c_longlong(), ctypes.c_longlong()
+        L.check(self.lib.ibl_step_paths(self.h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
     def step_record(self):
         L.check(self.lib.ibl_step_record(self.h))
 
@@ -334,6 +340,25 @@ class Ensemble:
 
     def sync(self):
         L.check(self.lib.ibl_ensemble_sync(self.h))
+
+    def tune(self, steps_per_candidate: int = 8):
+        """Autotunes the launch shape of the batched lattice update by timing
+        real ensemble steps with each candidate (the members advance by
+        ENSEMBLE_SHAPES * (steps_per_candidate + 2) steps); returns
+        (chosen shape, ms per step of every candidate)."""
+        ms = np.zeros(L.ENSEMBLE_SHAPES)
+        k = ctypes.c_int()
+        L.check(self.lib.ibl_ensemble_tune(self.h, int(steps_per_candidate), _dp(ms), ctypes.byref(k)))
+        return k.value, ms
+
+    def set_shape(self, shape: int):
+        L.check(self.lib.ibl_ensemble_set_shape(self.h, int(shape)))
+
+    def shape(self):
+        """(shape index, threads per block, prefetch distance in waves)."""
+        k, t, w = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        L.check(self.lib.ibl_ensemble_shape(self.h, ctypes.byref(k), ctypes.byref(t), ctypes.byref(w)))
+        return k.value, t.value, w.value
 
     def close(self):
         if getattr(self, "h", None):
