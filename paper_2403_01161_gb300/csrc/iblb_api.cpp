@@ -62,8 +62,8 @@ bool lb_layout(const ibl_lb_params *p, int n_frames, Layout &L)
     L.frames = take(sizeof(double) * 9 * (size_t)n_frames);
     L.frames_t = take(es * 9 * (size_t)n_frames);
     L.f = take(es * 19 * (size_t)pop_stride(nodes));
-    L.force = take(es * 3 * (size_t)nodes);
-    L.vel = take(es * 3 * (size_t)nodes);
+    L.force = take(es * 4 * (size_t)nodes);  // [nodes][4]: x, y, z, 0
+    L.vel = take(es * 4 * (size_t)nodes);
     L.rec = p->record_fields ? take(es * 7 * (size_t)nodes) : 0;
     L.ind = take(((size_t)nodes + 3) / 4 * 4);  // inside flags, one byte per node
     L.total = off;
@@ -796,19 +796,18 @@ int ensemble_one_step(ibl_ensemble *e, cudaStream_t sL, cudaStream_t sH)
         err = cudaEventRecord(evNear[par], sH);
         if (err != cudaSuccess) return cuda_fail(err, "ensemble event");
     }
-    for (ibl_lb *lb : e->m) {
-        ibl_mesh *mm = lb->mesh;
-        if (mm->readout_every > 0 && next % mm->readout_every == 0) {
-            // the record reads the member's step counter, closed by the outside update
-            if (!obs) err = cudaStreamWaitEvent(sH, evFar[par], 0);
-            if (err == cudaSuccess) err = iblb::launch_observables(lb->v, mm->v, sH, e->hi_prio);
-            if (err != cudaSuccess) return cuda_fail(err, "ensemble observables launch");
-            obs = true;
-        }
+    std::vector<char> due(e->m.size(), 0);
+    for (size_t k = 0; k < e->m.size(); ++k) {
+        const ibl_mesh *mm = e->m[k]->mesh;
+        due[k] = mm->readout_every > 0 && next % mm->readout_every == 0;
+        obs = obs || due[k];
     }
     if (obs) {
-        err = cudaEventRecord(evNear[par], sH);
-        if (err != cudaSuccess) return cuda_fail(err, "ensemble event");
+        // the records read each member's step counter, closed by the outside update
+        err = cudaStreamWaitEvent(sH, evFar[par], 0);
+        if (err == cudaSuccess) err = iblb::launch_observables_batched(e->v, due, sH, e->hi_prio);
+        if (err == cudaSuccess) err = cudaEventRecord(evNear[par], sH);
+        if (err != cudaSuccess) return cuda_fail(err, "ensemble observables launch");
     }
     for (ibl_lb *lb : e->m) lb->host_step = next;
     return IBL_OK;
@@ -1043,8 +1042,8 @@ int ibl_lb_create(const ibl_lb_params *p, const double *A_frames, int n_frames, 
         e = cudaMemcpyAsync(lb->ws + L.frames, A_frames, sizeof(double) * 9 * n_frames, cudaMemcpyHostToDevice,
                             lb->stream);
     if (e == cudaSuccess) e = iblb::launch_convert_frames(v, 0, n_frames, lb->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(v.force, 0, es * 3 * nodes, lb->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(v.vel, 0, es * 3 * nodes, lb->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v.force, 0, es * 4 * nodes, lb->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v.vel, 0, es * 4 * nodes, lb->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(v.ind, 0, ((size_t)nodes + 3) / 4 * 4, lb->stream);
     if (e == cudaSuccess && v.rec) e = cudaMemsetAsync(v.rec, 0, es * 7 * nodes, lb->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(v.f, 0, es * 19 * v.qs, lb->stream);

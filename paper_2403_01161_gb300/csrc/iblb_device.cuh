@@ -152,7 +152,80 @@ struct L2Keep {
     {
         asm volatile("red.global.add.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(a), "d"(v), "l"(pol) : "memory");
     }
+    // three components of a 4-wide node record (16-byte aligned for float,
+    // 32-byte for double): one vector access per record in FP32
+    __device__ __forceinline__ void ld3(const float *a, float &x, float &y, float &z) const
+    {
+        float w;
+        asm volatile("ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                     : "=f"(x), "=f"(y), "=f"(z), "=f"(w)
+                     : "l"(a), "l"(pol)
+                     : "memory");
+    }
+    __device__ __forceinline__ void ld3(const double *a, double &x, double &y, double &z) const
+    {
+        asm volatile("ld.global.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(x), "=d"(y) : "l"(a), "l"(pol) : "memory");
+        z = ld(a + 2);
+    }
+    __device__ __forceinline__ void st3(float *a, float x, float y, float z) const
+    {
+        asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(a), "f"(x), "f"(y), "f"(z),
+                     "f"(0.f), "l"(pol)
+                     : "memory");
+    }
+    __device__ __forceinline__ void st3(double *a, double x, double y, double z) const
+    {
+        asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1, %2}, %3;" ::"l"(a), "d"(x), "d"(y), "l"(pol) : "memory");
+        st(a + 2, z);
+    }
+    __device__ __forceinline__ void red_add3(float *a, float x, float y, float z) const
+    {
+        asm volatile("red.global.add.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(a), "f"(x), "f"(y),
+                     "f"(z), "f"(0.f), "l"(pol)
+                     : "memory");
+    }
+    __device__ __forceinline__ void red_add3(double *a, double x, double y, double z) const
+    {
+        red_add(a, x);
+        red_add(a + 1, y);
+        red_add(a + 2, z);
+    }
 };
+
+// Plain-policy access to the three components of a 4-wide node record.
+__device__ __forceinline__ void rec_ld3(const float *a, float &x, float &y, float &z)
+{
+    const float4 v = *reinterpret_cast<const float4 *>(a);
+    x = v.x;
+    y = v.y;
+    z = v.z;
+}
+__device__ __forceinline__ void rec_ld3(const double *a, double &x, double &y, double &z)
+{
+    const double2 v = *reinterpret_cast<const double2 *>(a);
+    x = v.x;
+    y = v.y;
+    z = a[2];
+}
+__device__ __forceinline__ void rec_st3(float *a, float x, float y, float z)
+{
+    *reinterpret_cast<float4 *>(a) = make_float4(x, y, z, 0.f);
+}
+__device__ __forceinline__ void rec_st3(double *a, double x, double y, double z)
+{
+    *reinterpret_cast<double2 *>(a) = make_double2(x, y);
+    a[2] = z;
+}
+__device__ __forceinline__ void rec_red3(float *a, float x, float y, float z)
+{
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(a), "f"(x), "f"(y), "f"(z), "f"(0.f) : "memory");
+}
+__device__ __forceinline__ void rec_red3(double *a, double x, double y, double z)
+{
+    atomicAdd(a, x);
+    atomicAdd(a + 1, y);
+    atomicAdd(a + 2, z);
+}
 
 // The same interface with the default policy (plain loads, stores and
 // reductions), for the batched ensemble kernels: the droplet-side working
@@ -171,6 +244,21 @@ struct L2Plain {
     }
     __device__ __forceinline__ void red_add(float *a, float v) const { atomicAdd(a, v); }
     __device__ __forceinline__ void red_add(double *a, double v) const { atomicAdd(a, v); }
+    template <class V>
+    __device__ __forceinline__ void ld3(const V *a, V &x, V &y, V &z) const
+    {
+        rec_ld3(a, x, y, z);
+    }
+    template <class V>
+    __device__ __forceinline__ void st3(V *a, V x, V y, V z) const
+    {
+        rec_st3(a, x, y, z);
+    }
+    template <class V>
+    __device__ __forceinline__ void red_add3(V *a, V x, V y, V z) const
+    {
+        rec_red3(a, x, y, z);
+    }
 };
 
 struct NodeStencil {

@@ -45,8 +45,8 @@ struct LbView {
     float omega_f;
     float inv_nx;       // 1 / n[0] (rounded): row of a node within its z plane in the batched lattice kernel
     void *f;            // [19][qs]
-    void *force;        // [3][nodes]
-    void *vel;          // [3][nodes]
+    void *force;        // [nodes][4]: x, y, z, 0 (one 16-byte record per node in FP32)
+    void *vel;          // [nodes][4]
     void *rec;          // [7][nodes] or null: drho, u, F
     const double *frames;
     const void *frames_t;  // the frames in the storage precision
@@ -99,17 +99,21 @@ struct MeshGroup {
 };
 
 // Launch shapes of the ensemble step, the candidates of ibl_ensemble_tune:
-// shape k = 4 p + 2 t + w takes w resident waves of blocks of L2 prefetch
-// distance and 128 (t = 0) or 256 (t = 1) threads per block in the batched
-// lattice update (each block takes that many consecutive nodes of one z
-// plane of one member), and with p = 0 keeps the droplet-side working set
-// in L2 (evict_last, as the single droplet does), with p = 1 the default
-// policy.
+// shape k = 8 c + 4 p + 2 t + w takes w resident waves of blocks of L2
+// prefetch distance and 128 (t = 0) or 256 (t = 1) threads per block in the
+// batched lattice update (each block takes that many consecutive nodes of
+// one z plane of one member); p = 0 keeps the droplet-side working set in
+// L2 (evict_last, as the single droplet does), p = 1 uses the default
+// policy; c = 1 caps the grids of the droplet-side kernels at
+// kEnsChainBlocksPerSm blocks per SM (they then stride over their work),
+// c = 0 launches one block per work unit.
 constexpr int kEnsShapes = IBL_ENSEMBLE_SHAPES;
 constexpr int ens_shape_waves(int k) { return k & 1; }
 constexpr int ens_shape_threads(int k) { return (k & 2) ? 256 : 128; }
 constexpr bool ens_shape_keep(int k) { return (k & 4) == 0; }
-constexpr int kEnsDefaultShape = 5;
+constexpr bool ens_shape_capped(int k) { return (k & 8) != 0; }
+constexpr int kEnsChainBlocksPerSm = 2;
+constexpr int kEnsDefaultShape = 8;
 
 struct EnsembleView {
     std::vector<LbView> lv;      // host copies of the member views
@@ -176,6 +180,8 @@ cudaError_t launch_ensemble_pre(const EnsembleView &E, long long step, cudaStrea
 cudaError_t launch_ensemble_near(const EnsembleView &E, long long step, cudaStream_t s, int prio);
 cudaError_t launch_ensemble_far(const EnsembleView &E, long long step, cudaStream_t s);
 cudaError_t launch_ensemble_interp(const EnsembleView &E, cudaStream_t s, int prio);
+// the shape records of the members with due[k] != 0, one launch per group
+cudaError_t launch_observables_batched(const EnsembleView &E, const std::vector<char> &due, cudaStream_t s, int prio);
 
 // adjoint kernels (iblb_adjoint.cu); Mt.r holds the positions r_t of the
 // step, pc the control block recorded before it (its patch)

@@ -256,24 +256,16 @@ __device__ __forceinline__ bool lattice_node(const LbView &L, const int x, const
             bc_dispatch<T>(g, uw, L.rule, (sx + 1) + 3 * (sy + 1) + 9 * (sz + 1));
         }
 
-        // droplet patch: read the spread force (and clear it), store u below
+        // droplet patch: read the spread force (and clear it), store u below;
+        // both fields hold a 4-wide record (x, y, z, 0) per node
         T Fx = T(0), Fy = T(0), Fz = T(0);
         T *__restrict__ force = static_cast<T *>(L.force);
-        const int nodes = L.nodes;
         if constexpr (MODE == LAT_NEAR) {
-            Fx = K.ld(force + node);
-            Fy = K.ld(force + nodes + node);
-            Fz = K.ld(force + 2 * nodes + node);
-            K.st(force + node, T(0));
-            K.st(force + nodes + node, T(0));
-            K.st(force + 2 * nodes + node, T(0));
+            K.ld3(force + 4 * node, Fx, Fy, Fz);
+            K.st3(force + 4 * node, T(0), T(0), T(0));
         } else if (in_patch) {
-            Fx = force[node];
-            Fy = force[nodes + node];
-            Fz = force[2 * nodes + node];
-            force[node] = T(0);
-            force[nodes + node] = T(0);
-            force[2 * nodes + node] = T(0);
+            rec_ld3(force + 4 * node, Fx, Fy, Fz);
+            rec_st3(force + 4 * node, T(0), T(0), T(0));
         }
 
         T drho = T(0), jx = T(0), jy = T(0), jz = T(0);
@@ -361,17 +353,11 @@ __device__ __forceinline__ bool lattice_node(const LbView &L, const int x, const
         }
         if (in_patch) {
             T *__restrict__ vel = static_cast<T *>(L.vel);
-            if constexpr (MODE == LAT_NEAR) {
-                K.st(vel + node, ux);
-                K.st(vel + nodes + node, uy);
-                K.st(vel + 2 * nodes + node, uz);
-            } else {
-                vel[node] = ux;
-                vel[nodes + node] = uy;
-                vel[2 * nodes + node] = uz;
-            }
+            if constexpr (MODE == LAT_NEAR) K.st3(vel + 4 * node, ux, uy, uz);
+            else rec_st3(vel + 4 * node, ux, uy, uz);
         }
         if constexpr (REC) {
+            const int nodes = L.nodes;
             T *__restrict__ rec = static_cast<T *>(L.rec);
             rec[node] = drho;
             rec[nodes + node] = ux;
@@ -654,15 +640,12 @@ __device__ __forceinline__ void spread_body(const LbView &L, const MeshView &M, 
         M.fn[3 * i + 2] = F[2];
     }
     const NodeStencil S = node_stencil<LANES, P>(L, M.r + 3 * i, lane, &K);
-    if (!valid) return;
-    if (!S.ok) {
-        if (lane == 0) atomicOr(&L.ctl->err, IBL_ERRBIT_WALL);
-        return;
-    }
+    if (valid && !S.ok && lane == 0) atomicOr(&L.ctl->err, IBL_ERRBIT_WALL);
+    if (!valid || !S.ok) return;
     const bool perx = L.bc[0] == IBL_BC_PERIODIC, pery = L.bc[1] == IBL_BC_PERIODIC,
                perz = L.bc[2] == IBL_BC_PERIODIC;
-    const int nx = L.n[0], nxy = L.n[0] * L.n[1], nodes = L.nodes;
-    T *force = static_cast<T *>(L.force);
+    const int nx = L.n[0], nxy = L.n[0] * L.n[1];
+    T *force = static_cast<T *>(L.force);  // [nodes][4]
     const T Fx = T(F[0]), Fy = T(F[1]), Fz = T(F[2]);
     // the lane's (y, z) rows r = lane, lane + LANES, ...: (b, c) = (r & 3, r >> 2)
 #pragma unroll
@@ -676,9 +659,7 @@ __device__ __forceinline__ void spread_body(const LbView &L, const MeshView &M, 
         for (int a = 0; a < 4; ++a) {
             const T dl = w[a] * wy * wz;
             const int id = row + wrap_index(S.base[0] + a, nx, perx);
-            K.red_add(force + id, Fx * dl);
-            K.red_add(force + nodes + id, Fy * dl);
-            K.red_add(force + 2 * nodes + id, Fz * dl);
+            K.red_add3(force + 4 * id, Fx * dl, Fy * dl, Fz * dl);
         }
     }
 }
@@ -690,12 +671,12 @@ template <class P>
 __global__ void __launch_bounds__(128) k_tri_moment_batched(const __grid_constant__ MeshGroup MG)
 {
     const MeshView &M = MG.v[blockIdx.y];
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= M.nt) return;
     const P K;
-    double m[3];
-    tri_moment(M, t, m, K);
-    for (int a = 0; a < 3; ++a) K.st(M.tm + 3 * t + a, m[a]);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < M.nt; t += gridDim.x * blockDim.x) {
+        double m[3];
+        tri_moment(M, t, m, K);
+        for (int a = 0; a < 3; ++a) K.st(M.tm + 3 * t + a, m[a]);
+    }
 }
 
 template <typename T, int LANES>
@@ -835,8 +816,8 @@ __device__ __forceinline__ void interp_body(const LbView &L, const MeshView &M, 
     if (S.ok) {
         const bool perx = L.bc[0] == IBL_BC_PERIODIC, pery = L.bc[1] == IBL_BC_PERIODIC,
                    perz = L.bc[2] == IBL_BC_PERIODIC;
-        const int nx = L.n[0], nxy = L.n[0] * L.n[1], nodes = L.nodes;
-        const T *vel = static_cast<const T *>(L.vel);
+        const int nx = L.n[0], nxy = L.n[0] * L.n[1];
+        const T *vel = static_cast<const T *>(L.vel);  // [nodes][4]
         // the lane's (y, z) rows r = lane, lane + LANES, ...: (b, c) = (r & 3, r >> 2)
 #pragma unroll
         for (int q = 0; q < 16 / LANES; ++q) {
@@ -849,9 +830,11 @@ __device__ __forceinline__ void interp_body(const LbView &L, const MeshView &M, 
             for (int a = 0; a < 4; ++a) {
                 const T dl = w[a] * wy * wz;
                 const int id = row + wrap_index(S.base[0] + a, nx, perx);
-                v[0] += K.ld(vel + id) * dl;
-                v[1] += K.ld(vel + nodes + id) * dl;
-                v[2] += K.ld(vel + 2 * nodes + id) * dl;
+                T ua, ub, uc;
+                K.ld3(vel + 4 * id, ua, ub, uc);
+                v[0] += ua * dl;
+                v[1] += ub * dl;
+                v[2] += uc * dl;
             }
         }
     }
@@ -915,24 +898,33 @@ __global__ void __launch_bounds__(128) k_interp(LbView L, MeshView M)
 // local block b0 + b - blk_start[member]; node-group kernels use ceil(nv/8)
 // blocks per member.
 
+// The node groups b0 .. b0 + nb - 1 of a group of members, block-strided so
+// that a grid capped below nb leaves most SM slots to the concurrent
+// lattice update.
 template <typename T, class P>
 __global__ void __launch_bounds__(128)
     k_spread_batched(const __grid_constant__ LbGroup LG, const __grid_constant__ MeshGroup MG, const int m0,
-                     const int b0, const int *__restrict__ blk_member, const int *__restrict__ blk_start,
-                     const int next_buf)
+                     const int b0, const int nb, const int *__restrict__ blk_member,
+                     const int *__restrict__ blk_start, const int next_buf)
 {
-    const int mi = blk_member[b0 + blockIdx.x];
-    spread_body<T, true, kFwdLanes, P>(LG.v[mi - m0], MG.v[mi - m0], b0 + (int)blockIdx.x - blk_start[mi], next_buf);
+    for (int bb = b0 + (int)blockIdx.x; bb < b0 + nb; bb += (int)gridDim.x) {
+        const int mi = blk_member[bb];
+        spread_body<T, true, kFwdLanes, P>(LG.v[mi - m0], MG.v[mi - m0], bb - blk_start[mi], next_buf);
+    }
 }
 
 template <typename T, class P>
 __global__ void __launch_bounds__(128)
     k_interp_batched(const __grid_constant__ LbGroup LG, const __grid_constant__ MeshGroup MG, const int m0,
-                     const int b0, const int *__restrict__ blk_member, const int *__restrict__ blk_start)
+                     const int b0, const int nb, const int *__restrict__ blk_member,
+                     const int *__restrict__ blk_start)
 {
-    const int mi = blk_member[b0 + blockIdx.x];
-    interp_body<T, kFwdLanes, P>(LG.v[mi - m0], MG.v[mi - m0], b0 + (int)blockIdx.x - blk_start[mi],
-                   blk_start[mi + 1] - blk_start[mi]);
+    for (int bb = b0 + (int)blockIdx.x; bb < b0 + nb; bb += (int)gridDim.x) {
+        const int mi = blk_member[bb];
+        interp_body<T, kFwdLanes, P>(LG.v[mi - m0], MG.v[mi - m0], bb - blk_start[mi],
+                                     blk_start[mi + 1] - blk_start[mi]);
+        __syncthreads();  // the next pass reuses the body's shared rows
+    }
 }
 
 __device__ void block_bbox_patch(const LbView &L, const MeshView &M, const double *r, int nv, int buf)
@@ -1264,8 +1256,11 @@ __global__ void __launch_bounds__(256) k_patch(LbView L, MeshView M, int buf)
 
 // Shape record (Sec. 2): enclosed volume, centroid and second moment by
 // signed tetrahedra (ref, a, b, c), S = (5/V) M, eigen-decomposition, Taylor
-// D and beta of Eq. (beta).  One block.
-__global__ void __launch_bounds__(256) k_observables(LbView L, MeshView M)
+// D and beta of Eq. (beta).  Block blk of nblk sums its share of the
+// triangles; the last block to finish (a ticket in the control block) adds
+// the partial sums in block order and writes the record.
+__device__ __forceinline__ void observables_body(const LbView &L, const MeshView &M, const unsigned blk,
+                                                 const unsigned nblk)
 {
     __shared__ double sh11[8][11];
     __shared__ bool last;
@@ -1274,7 +1269,7 @@ __global__ void __launch_bounds__(256) k_observables(LbView L, MeshView M)
     const double ref[3] = {M.r[0], M.r[1], M.r[2]};
     double acc[11];
     for (int k = 0; k < 11; ++k) acc[k] = 0.0;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < M.nt; t += gridDim.x * blockDim.x) {
+    for (int t = blk * blockDim.x + threadIdx.x; t < M.nt; t += nblk * blockDim.x) {
         double p[3][3];
         for (int v = 0; v < 3; ++v) {
             const int id = M.tris[3 * t + v];
@@ -1307,16 +1302,16 @@ __global__ void __launch_bounds__(256) k_observables(LbView L, MeshView M)
     // per-block partial sums; the last block adds them in block order
     block_sum<11>(acc, sh11);
     if (threadIdx.x == 0) {
-        for (int k = 0; k < 11; ++k) M.obs_part[11 * blockIdx.x + k] = acc[k];
+        for (int k = 0; k < 11; ++k) M.obs_part[11 * blk + k] = acc[k];
         __threadfence();
         const unsigned t = atomicAdd(&L.ctl->obs_blocks_done, 1u);
-        last = (t == gridDim.x - 1);
+        last = (t == nblk - 1);
     }
     __syncthreads();
     if (!last || threadIdx.x != 0) return;
     __threadfence();
     for (int k = 0; k < 11; ++k) acc[k] = 0.0;
-    for (unsigned b = 0; b < gridDim.x; ++b)
+    for (unsigned b = 0; b < nblk; ++b)
         for (int k = 0; k < 11; ++k) acc[k] += __ldcg(M.obs_part + 11 * b + k);
     L.ctl->obs_blocks_done = 0u;
     const double V = acc[0];
@@ -1375,6 +1370,21 @@ __global__ void __launch_bounds__(256) k_observables(LbView L, MeshView M)
     const int slot = L.ctl->n_records % M.ring_cap;
     M.ring[slot] = o;
     L.ctl->n_records += 1;
+}
+
+__global__ void __launch_bounds__(256) k_observables(LbView L, MeshView M)
+{
+    observables_body(L, M, blockIdx.x, gridDim.x);
+}
+
+// Ensemble: the shape records of the members of a group whose bit is set in
+// `due` (blockIdx.y is the member within the group), all in one launch.
+__global__ void __launch_bounds__(256) k_observables_batched(const __grid_constant__ LbGroup LG,
+                                                             const __grid_constant__ MeshGroup MG,
+                                                             const unsigned long long due)
+{
+    if (!((due >> blockIdx.y) & 1ull)) return;
+    observables_body(LG.v[blockIdx.y], MG.v[blockIdx.y], blockIdx.x, gridDim.x);
 }
 
 }  // namespace
@@ -1622,6 +1632,16 @@ void fill_group(const EnsembleView &E, int m0, int m1)
 
 static int ens_shape(const EnsembleView &E) { return E.shape >= 0 && E.shape < kEnsShapes ? E.shape : kEnsDefaultShape; }
 
+// Blocks of a batched droplet-side kernel over nb node groups: all of them,
+// or, in the capped shapes, at most kEnsChainBlocksPerSm per SM (the kernels
+// then stride over the node groups).
+static int chain_grid(const EnsembleView &E, int nb)
+{
+    if (!ens_shape_capped(ens_shape(E))) return nb;
+    const int cap = kEnsChainBlocksPerSm * sm_count();
+    return nb < cap ? nb : cap;
+}
+
 template <class P>
 static cudaError_t ensemble_pre_t(const EnsembleView &E, int m0, int m1, int pbuf, int nxt, cudaStream_t s, int prio)
 {
@@ -1635,15 +1655,20 @@ static cudaError_t ensemble_pre_t(const EnsembleView &E, int m0, int m1, int pbu
     cudaError_t e = cudaSuccess;
     if (recentre)
         e = launch_p(k_centre_batched, dim3(kCentreBlocks, m1 - m0), dim3(kCentreThreads), s, prio, G.lg, G.mg, pbuf);
-    if (e == cudaSuccess)
-        e = launch_p(k_tri_moment_batched<P>, dim3((nt_max + 127) / 128, m1 - m0), dim3(128), s, prio, G.mg);
+    int tb = (nt_max + 127) / 128;
+    if (ens_shape_capped(ens_shape(E))) {
+        const int cap = kEnsChainBlocksPerSm * sm_count() / (m1 - m0);
+        tb = tb < cap ? tb : (cap < 1 ? 1 : cap);
+    }
+    if (e == cudaSuccess) e = launch_p(k_tri_moment_batched<P>, dim3(tb, m1 - m0), dim3(128), s, prio, G.mg);
     const int nb0 = E.node_start[m0], nb = E.node_start[m1] - nb0;
+    const dim3 g(chain_grid(E, nb));
     if (e == cudaSuccess) {
         if (E.precision == IBL_FP64)
-            e = launch_p(k_spread_batched<double, P>, dim3(nb), dim3(kIbThreads), s, prio, G.lg, G.mg, m0, nb0,
+            e = launch_p(k_spread_batched<double, P>, g, dim3(kIbThreads), s, prio, G.lg, G.mg, m0, nb0, nb,
                          E.node_member, E.node_start_d, nxt);
         else
-            e = launch_p(k_spread_batched<float, P>, dim3(nb), dim3(kIbThreads), s, prio, G.lg, G.mg, m0, nb0,
+            e = launch_p(k_spread_batched<float, P>, g, dim3(kIbThreads), s, prio, G.lg, G.mg, m0, nb0, nb,
                          E.node_member, E.node_start_d, nxt);
     }
     return e;
@@ -1668,7 +1693,14 @@ template <typename T, bool PER, class P>
 static cudaError_t ensemble_near_t(const EnsembleView &E, bool odd, int m0, int m1, int pbuf, cudaStream_t s, int prio)
 {
     Groups &G = groups();
-    const dim3 g(kEnsNearBlocks, m1 - m0), b(256);
+    // blocks per member: kEnsNearBlocks, or in the capped shapes about
+    // kEnsChainBlocksPerSm per SM over the whole group
+    int per = kEnsNearBlocks;
+    if (ens_shape_capped(ens_shape(E))) {
+        per = kEnsChainBlocksPerSm * sm_count() / (m1 - m0);
+        per = per < 1 ? 1 : (per > kEnsNearBlocks ? kEnsNearBlocks : per);
+    }
+    const dim3 g(per, m1 - m0), b(256);
     return odd ? launch_p(k_lattice_near_batched<T, true, PER, P>, g, b, s, prio, G.lg, pbuf)
                : launch_p(k_lattice_near_batched<T, false, PER, P>, g, b, s, prio, G.lg, pbuf);
 }
@@ -1761,18 +1793,42 @@ cudaError_t launch_ensemble_interp(const EnsembleView &E, cudaStream_t s, int pr
         const int m1 = m0 + kGroup < n ? m0 + kGroup : n;
         fill_group(E, m0, m1);
         const int nb0 = E.node_start[m0], nb = E.node_start[m1] - nb0;
-        const dim3 g(nb), b(kIbThreads);
+        const dim3 g(chain_grid(E, nb)), b(kIbThreads);
         cudaError_t e;
         if (E.precision == IBL_FP64)
-            e = keep ? launch_p(k_interp_batched<double, L2Keep>, g, b, s, prio, G.lg, G.mg, m0, nb0, E.node_member,
-                                E.node_start_d)
-                     : launch_p(k_interp_batched<double, L2Plain>, g, b, s, prio, G.lg, G.mg, m0, nb0, E.node_member,
-                                E.node_start_d);
+            e = keep ? launch_p(k_interp_batched<double, L2Keep>, g, b, s, prio, G.lg, G.mg, m0, nb0, nb,
+                                E.node_member, E.node_start_d)
+                     : launch_p(k_interp_batched<double, L2Plain>, g, b, s, prio, G.lg, G.mg, m0, nb0, nb,
+                                E.node_member, E.node_start_d);
         else
-            e = keep ? launch_p(k_interp_batched<float, L2Keep>, g, b, s, prio, G.lg, G.mg, m0, nb0, E.node_member,
-                                E.node_start_d)
-                     : launch_p(k_interp_batched<float, L2Plain>, g, b, s, prio, G.lg, G.mg, m0, nb0, E.node_member,
-                                E.node_start_d);
+            e = keep ? launch_p(k_interp_batched<float, L2Keep>, g, b, s, prio, G.lg, G.mg, m0, nb0, nb,
+                                E.node_member, E.node_start_d)
+                     : launch_p(k_interp_batched<float, L2Plain>, g, b, s, prio, G.lg, G.mg, m0, nb0, nb,
+                                E.node_member, E.node_start_d);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_observables_batched(const EnsembleView &E, const std::vector<char> &due, cudaStream_t s, int prio)
+{
+    const int n = (int)E.lv.size();
+    Groups &G = groups();
+    for (int m0 = 0; m0 < n; m0 += kGroup) {
+        const int m1 = m0 + kGroup < n ? m0 + kGroup : n;
+        unsigned long long mask = 0;
+        int nt_max = 0;
+        for (int k = m0; k < m1; ++k)
+            if (due[k]) {
+                mask |= 1ull << (k - m0);
+                nt_max = E.mv[k].nt > nt_max ? E.mv[k].nt : nt_max;
+            }
+        if (!mask) continue;
+        fill_group(E, m0, m1);
+        int g = (nt_max + 255) / 256;
+        if (g > kObsBlocksMax) g = kObsBlocksMax;
+        const cudaError_t e =
+            launch_p(k_observables_batched, dim3(g, m1 - m0), dim3(256), s, prio, G.lg, G.mg, mask);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
