@@ -345,18 +345,18 @@ int ibl_ensemble_create(int n_members, ibl_lb *const *members, void *workspace, 
 /* Enqueues n steps of every member (asynchronous). */
 int ibl_ensemble_step(ibl_ensemble *e, long long n);
 /* Launch shape of an ensemble step: IBL_ENSEMBLE_SHAPES candidates, shape
- * k = 8 c + 4 p + 2 t + w.  The batched lattice update of the nodes outside
+ * k = 8 c + 4 p + 2 t + w (c = 0..3).  The batched lattice update of the nodes outside
  * each droplet patch (almost all of a step's bytes) takes 128 (t = 0) or
  * 256 (t = 1) threads per block, each block updating that many consecutive
  * nodes of one z plane of one member, and prefetches the populations into
  * L2 w resident waves of blocks ahead (w = 0 or 1).  p = 0 keeps the
  * droplet-side data (mesh, patch populations, force and velocity) in L2
  * with an evict_last policy, as a single droplet's step does; p = 1 uses the
- * default policy.  c = 1 caps the droplet-side kernels (forces and spread,
- * patch nodes, interpolation), which run on the helper stream beside the
- * lattice update, at two blocks per SM; c = 0 gives them one block per
- * work unit.  The shape changes only launch geometry and cache policy:
- * every shape computes the same populations.  Default: shape 8.
+ * default policy.  c = 1, 2, 3 caps the droplet-side kernels (forces and
+ * spread, patch nodes, interpolation), which run on the helper stream beside
+ * the lattice update, at 1, 2 or 4 blocks per SM; c = 0 gives them one block
+ * per work unit.  The shape changes only launch geometry and cache policy:
+ * every shape computes the same populations.  Default: shape 16.
  *
  * ibl_ensemble_tune is the autotuner: it runs 2 untimed and
  * steps_per_candidate timed ensemble steps with each shape in turn (eager
@@ -369,7 +369,7 @@ int ibl_ensemble_step(ibl_ensemble *e, long long n);
  * ibl_ensemble_sync.  ibl_ensemble_set_shape sets a shape directly (for
  * instance one stored from an earlier tuning of the same member sizes);
  * ibl_ensemble_shape reports the current one (any pointer may be NULL). */
-#define IBL_ENSEMBLE_SHAPES 16
+#define IBL_ENSEMBLE_SHAPES 32
 int ibl_ensemble_tune(ibl_ensemble *e, int steps_per_candidate, double *ms, int *chosen);
 int ibl_ensemble_set_shape(ibl_ensemble *e, int shape);
 int ibl_ensemble_shape(const ibl_ensemble *e, int *shape, int *threads, int *prefetch_waves);

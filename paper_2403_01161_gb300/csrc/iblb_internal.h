@@ -104,16 +104,16 @@ struct MeshGroup {
 // batched lattice update (each block takes that many consecutive nodes of
 // one z plane of one member); p = 0 keeps the droplet-side working set in
 // L2 (evict_last, as the single droplet does), p = 1 uses the default
-// policy; c = 1 caps the grids of the droplet-side kernels at
-// kEnsChainBlocksPerSm blocks per SM (they then stride over their work),
-// c = 0 launches one block per work unit.
+// policy; c = 1, 2, 3 caps the grids of the droplet-side kernels at 1, 2, 4
+// blocks per SM (they then stride over their work), c = 0 launches one
+// block per work unit.
 constexpr int kEnsShapes = IBL_ENSEMBLE_SHAPES;
 constexpr int ens_shape_waves(int k) { return k & 1; }
 constexpr int ens_shape_threads(int k) { return (k & 2) ? 256 : 128; }
 constexpr bool ens_shape_keep(int k) { return (k & 4) == 0; }
-constexpr bool ens_shape_capped(int k) { return (k & 8) != 0; }
-constexpr int kEnsChainBlocksPerSm = 2;
-constexpr int kEnsDefaultShape = 8;
+constexpr int ens_shape_cap(int k) { return (k >> 3) == 0 ? 0 : ((k >> 3) == 3 ? 4 : (k >> 3)); }
+constexpr bool ens_shape_capped(int k) { return ens_shape_cap(k) > 0; }
+constexpr int kEnsDefaultShape = 16;
 
 struct EnsembleView {
     std::vector<LbView> lv;      // host copies of the member views

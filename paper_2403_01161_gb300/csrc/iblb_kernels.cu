@@ -410,31 +410,40 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 4) k_lattice(LbView 
     if (m != 0u && (threadIdx.x & 31) == 0) atomicOr(&L.ctl->err, IBL_ERRBIT_UNSTABLE);
 }
 
-// The patch nodes of the step (grid-stride over the patch box, x fastest).
-template <typename T, bool ODD, bool REC, bool PER>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_lattice_near(LbView L, int buf)
+// The patch nodes of the step: one warp per row (y, z) of the patch box,
+// its lanes along x (32 at a time), rows grid-strided over the warps of the
+// grid, so that each access of a warp is one contiguous run of a row.
+template <typename T, bool ODD, bool REC, bool PER, class P>
+__device__ __forceinline__ void patch_rows(const LbView &L, const int buf, const int warp0, const int nwarps)
 {
     const Ctl *c = L.ctl;
     const int ex = c->patch_ext[buf][0] + 1, ey = c->patch_ext[buf][1] + 1, ez = c->patch_ext[buf][2] + 1;
     const int lx = c->patch_lo[buf][0], ly = c->patch_lo[buf][1], lz = c->patch_lo[buf][2];
-    const int count = (ex > 0 && ey > 0 && ez > 0) ? ex * ey * ez : 0;
-    for (int base = blockIdx.x * blockDim.x; base < count; base += gridDim.x * blockDim.x) {
-        const int idx = base + threadIdx.x;
-        bool bad = false;
-        if (idx < count) {
-            const int pz = idx / (ex * ey);
-            const int rem = idx - pz * ex * ey;
-            const int py = rem / ex;
-            const int px = rem - py * ex;
-            int x = lx + px, y = ly + py, z = lz + pz;
-            if (x >= L.n[0]) x -= L.n[0];  // a periodic patch may wrap once
-            if (y >= L.n[1]) y -= L.n[1];
-            if (z >= L.n[2]) z -= L.n[2];
-            bad = lattice_node<T, ODD, REC, LAT_NEAR, PER>(L, x, y, z, buf);
+    const int rows = (ex > 0 && ey > 0 && ez > 0) ? ey * ez : 0;
+    const int lane = threadIdx.x & 31;
+    for (int row = warp0; row < rows; row += nwarps) {
+        const int pz = row / ey, py = row - pz * ey;
+        int y = ly + py, z = lz + pz;
+        if (y >= L.n[1]) y -= L.n[1];  // a periodic patch may wrap once
+        if (z >= L.n[2]) z -= L.n[2];
+        for (int x0 = 0; x0 < ex; x0 += 32) {
+            bool bad = false;
+            if (x0 + lane < ex) {
+                int x = lx + x0 + lane;
+                if (x >= L.n[0]) x -= L.n[0];
+                bad = lattice_node<T, ODD, REC, LAT_NEAR, PER, P>(L, x, y, z, buf);
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, bad);
+            if (m != 0u && lane == 0) atomicOr(&L.ctl->err, IBL_ERRBIT_UNSTABLE);
         }
-        const unsigned m = __ballot_sync(0xffffffffu, bad);
-        if (m != 0u && (threadIdx.x & 31) == 0) atomicOr(&L.ctl->err, IBL_ERRBIT_UNSTABLE);
     }
+}
+
+template <typename T, bool ODD, bool REC, bool PER>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_lattice_near(LbView L, int buf)
+{
+    const int wpb = blockDim.x >> 5;
+    patch_rows<T, ODD, REC, PER, L2Keep>(L, buf, blockIdx.x * wpb + (threadIdx.x >> 5), gridDim.x * wpb);
 }
 
 // Ensemble: the nodes outside each member's droplet patch, one launch over
@@ -484,33 +493,13 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 1024 : 512) / NT)
 }
 
 // Ensemble: the patch nodes of every member of a group (blockIdx.y is the
-// member within the group), grid-stride over each member's patch box.
+// member within the group), a warp per patch row as in k_lattice_near.
 template <typename T, bool ODD, bool PER, class P>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_lattice_near_batched(const __grid_constant__ LbGroup G,
                                                                                     const int buf)
 {
-    const LbView &L = G.v[blockIdx.y];
-    const Ctl *c = L.ctl;
-    const int ex = c->patch_ext[buf][0] + 1, ey = c->patch_ext[buf][1] + 1, ez = c->patch_ext[buf][2] + 1;
-    const int lx = c->patch_lo[buf][0], ly = c->patch_lo[buf][1], lz = c->patch_lo[buf][2];
-    const int count = (ex > 0 && ey > 0 && ez > 0) ? ex * ey * ez : 0;
-    for (int base = blockIdx.x * blockDim.x; base < count; base += gridDim.x * blockDim.x) {
-        const int idx = base + threadIdx.x;
-        bool bad = false;
-        if (idx < count) {
-            const int pz = idx / (ex * ey);
-            const int rem = idx - pz * ex * ey;
-            const int py = rem / ex;
-            const int px = rem - py * ex;
-            int x = lx + px, y = ly + py, z = lz + pz;
-            if (x >= L.n[0]) x -= L.n[0];  // a periodic patch may wrap once
-            if (y >= L.n[1]) y -= L.n[1];
-            if (z >= L.n[2]) z -= L.n[2];
-            bad = lattice_node<T, ODD, false, LAT_NEAR, PER, P>(L, x, y, z, buf);
-        }
-        const unsigned m = __ballot_sync(0xffffffffu, bad);
-        if (m != 0u && (threadIdx.x & 31) == 0) atomicOr(&L.ctl->err, IBL_ERRBIT_UNSTABLE);
-    }
+    const int wpb = blockDim.x >> 5;
+    patch_rows<T, ODD, false, PER, P>(G.v[blockIdx.y], buf, blockIdx.x * wpb + (threadIdx.x >> 5), gridDim.x * wpb);
 }
 
 
@@ -1633,12 +1622,12 @@ void fill_group(const EnsembleView &E, int m0, int m1)
 static int ens_shape(const EnsembleView &E) { return E.shape >= 0 && E.shape < kEnsShapes ? E.shape : kEnsDefaultShape; }
 
 // Blocks of a batched droplet-side kernel over nb node groups: all of them,
-// or, in the capped shapes, at most kEnsChainBlocksPerSm per SM (the kernels
-// then stride over the node groups).
+// or, in the capped shapes, at most the shape's cap per SM (the kernels then
+// stride over the node groups).
 static int chain_grid(const EnsembleView &E, int nb)
 {
     if (!ens_shape_capped(ens_shape(E))) return nb;
-    const int cap = kEnsChainBlocksPerSm * sm_count();
+    const int cap = ens_shape_cap(ens_shape(E)) * sm_count();
     return nb < cap ? nb : cap;
 }
 
@@ -1657,7 +1646,7 @@ static cudaError_t ensemble_pre_t(const EnsembleView &E, int m0, int m1, int pbu
         e = launch_p(k_centre_batched, dim3(kCentreBlocks, m1 - m0), dim3(kCentreThreads), s, prio, G.lg, G.mg, pbuf);
     int tb = (nt_max + 127) / 128;
     if (ens_shape_capped(ens_shape(E))) {
-        const int cap = kEnsChainBlocksPerSm * sm_count() / (m1 - m0);
+        const int cap = ens_shape_cap(ens_shape(E)) * sm_count() / (m1 - m0);
         tb = tb < cap ? tb : (cap < 1 ? 1 : cap);
     }
     if (e == cudaSuccess) e = launch_p(k_tri_moment_batched<P>, dim3(tb, m1 - m0), dim3(128), s, prio, G.mg);
@@ -1693,11 +1682,11 @@ template <typename T, bool PER, class P>
 static cudaError_t ensemble_near_t(const EnsembleView &E, bool odd, int m0, int m1, int pbuf, cudaStream_t s, int prio)
 {
     Groups &G = groups();
-    // blocks per member: kEnsNearBlocks, or in the capped shapes about
-    // kEnsChainBlocksPerSm per SM over the whole group
+    // blocks per member: kEnsNearBlocks, or in the capped shapes about the
+    // shape's cap per SM over the whole group
     int per = kEnsNearBlocks;
     if (ens_shape_capped(ens_shape(E))) {
-        per = kEnsChainBlocksPerSm * sm_count() / (m1 - m0);
+        per = ens_shape_cap(ens_shape(E)) * sm_count() / (m1 - m0);
         per = per < 1 ? 1 : (per > kEnsNearBlocks ? kEnsNearBlocks : per);
     }
     const dim3 g(per, m1 - m0), b(256);
