@@ -200,18 +200,20 @@ __device__ __forceinline__ bool lattice_node(const LbView &L, const int x, const
         const int sx = px ? 0 : (x == 0 ? -1 : (x == nx - 1 ? 1 : 0));
         const int sy = py ? 0 : (y == 0 ? -1 : (y == ny - 1 ? 1 : 0));
         const int sz = pz ? 0 : (z == 0 ? -1 : (z == nz - 1 ? 1 : 0));
-        // offsets to the neighbours along each axis; periodic axes wrap,
-        // Zou-He axes mark the missing neighbour invalid (bits of `miss`:
-        // 1 x-1, 2 x+1, 4 y-1, 8 y+1, 16 z-1, 32 z+1)
+        // offsets to the neighbours along each axis (odd step: the sources
+        // x - c_i).  Periodic axes wrap.  On a Zou-He axis a missing
+        // neighbour points back at the node itself: a population whose source
+        // lies outside the box is an unknown that the boundary rebuild below
+        // overwrites before anything reads it, so its load only needs an
+        // address inside the array, not a guard.
         int oxm = -1, oxp = 1, oym = -nx, oyp = nx, ozm = -nxy, ozp = nxy;
-        int miss = 0;
         if constexpr (ODD) {
-            if (x == 0) { if (px) oxm = nx - 1; else miss |= 1; }
-            if (x == nx - 1) { if (px) oxp = -(nx - 1); else miss |= 2; }
-            if (y == 0) { if (py) oym = (ny - 1) * nx; else miss |= 4; }
-            if (y == ny - 1) { if (py) oyp = -(ny - 1) * nx; else miss |= 8; }
-            if (z == 0) { if (pz) ozm = (nz - 1) * nxy; else miss |= 16; }
-            if (z == nz - 1) { if (pz) ozp = -(nz - 1) * nxy; else miss |= 32; }
+            if (x == 0) oxm = px ? nx - 1 : 0;
+            if (x == nx - 1) oxp = px ? -(nx - 1) : 0;
+            if (y == 0) oym = py ? (ny - 1) * nx : 0;
+            if (y == ny - 1) oyp = py ? -(ny - 1) * nx : 0;
+            if (z == 0) ozm = pz ? (nz - 1) * nxy : 0;
+            if (z == nz - 1) ozp = pz ? -(nz - 1) * nxy : 0;
         }
 
         T g[19];
@@ -226,12 +228,10 @@ __device__ __forceinline__ bool lattice_node(const LbView &L, const int x, const
             sfor<19>([&](auto I) {
                 constexpr int i = decltype(I)::value;
                 constexpr int cx = cxf(i), cy = cyf(i), cz = czf(i);
-                constexpr int need = (cx > 0 ? 1 : (cx < 0 ? 2 : 0)) | (cy > 0 ? 4 : (cy < 0 ? 8 : 0)) |
-                                     (cz > 0 ? 16 : (cz < 0 ? 32 : 0));
                 const int off = (cx > 0 ? oxm : (cx < 0 ? oxp : 0)) + (cy > 0 ? oym : (cy < 0 ? oyp : 0)) +
                                 (cz > 0 ? ozm : (cz < 0 ? ozp : 0));
-                if constexpr (MODE == LAT_NEAR) g[i] = (miss & need) == 0 ? K.ld(f + opp(i) * qs + node + off) : T(0);
-                else g[i] = (miss & need) == 0 ? f[opp(i) * qs + node + off] : T(0);
+                if constexpr (MODE == LAT_NEAR) g[i] = K.ld(f + opp(i) * qs + node + off);
+                else g[i] = f[opp(i) * qs + node + off];
             });
         }
 
