@@ -205,9 +205,19 @@ __device__ __forceinline__ bool lattice_node(const LbView &L, const int x, const
         // neighbour points back at the node itself: a population whose source
         // lies outside the box is an unknown that the boundary rebuild below
         // overwrites before anything reads it, so its load only needs an
-        // address inside the array, not a guard.
+        // address inside the array, not a guard.  The patch-node update
+        // (LAT_NEAR) keeps the guard instead (bits of `miss`: 1 x-1, 2 x+1,
+        // 4 y-1, 8 y+1, 16 z-1, 32 z+1), which measured faster there.
         int oxm = -1, oxp = 1, oym = -nx, oyp = nx, ozm = -nxy, ozp = nxy;
-        if constexpr (ODD) {
+        [[maybe_unused]] int miss = 0;
+        if constexpr (ODD && MODE == LAT_NEAR) {
+            if (x == 0) { if (px) oxm = nx - 1; else miss |= 1; }
+            if (x == nx - 1) { if (px) oxp = -(nx - 1); else miss |= 2; }
+            if (y == 0) { if (py) oym = (ny - 1) * nx; else miss |= 4; }
+            if (y == ny - 1) { if (py) oyp = -(ny - 1) * nx; else miss |= 8; }
+            if (z == 0) { if (pz) ozm = (nz - 1) * nxy; else miss |= 16; }
+            if (z == nz - 1) { if (pz) ozp = -(nz - 1) * nxy; else miss |= 32; }
+        } else if constexpr (ODD) {
             if (x == 0) oxm = px ? nx - 1 : 0;
             if (x == nx - 1) oxp = px ? -(nx - 1) : 0;
             if (y == 0) oym = py ? (ny - 1) * nx : 0;
@@ -230,8 +240,13 @@ __device__ __forceinline__ bool lattice_node(const LbView &L, const int x, const
                 constexpr int cx = cxf(i), cy = cyf(i), cz = czf(i);
                 const int off = (cx > 0 ? oxm : (cx < 0 ? oxp : 0)) + (cy > 0 ? oym : (cy < 0 ? oyp : 0)) +
                                 (cz > 0 ? ozm : (cz < 0 ? ozp : 0));
-                if constexpr (MODE == LAT_NEAR) g[i] = K.ld(f + opp(i) * qs + node + off);
-                else g[i] = f[opp(i) * qs + node + off];
+                if constexpr (MODE == LAT_NEAR) {
+                    constexpr int need = (cx > 0 ? 1 : (cx < 0 ? 2 : 0)) | (cy > 0 ? 4 : (cy < 0 ? 8 : 0)) |
+                                         (cz > 0 ? 16 : (cz < 0 ? 32 : 0));
+                    g[i] = (miss & need) == 0 ? K.ld(f + opp(i) * qs + node + off) : T(0);
+                } else {
+                    g[i] = f[opp(i) * qs + node + off];
+                }
             });
         }
 
