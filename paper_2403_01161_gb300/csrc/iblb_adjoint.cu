@@ -297,15 +297,9 @@ __device__ __forceinline__ bool adj_node(const LbView &L, const AdjView &J, cons
         Fx = rec[4 * nodes + node];
         Fy = rec[5 * nodes + node];
         Fz = rec[6 * nodes + node];
-        T *lu = static_cast<T *>(J.lam_u);
-        lux = lu[node];
-        luy = lu[nodes + node];
-        luz = lu[2 * nodes + node];
-        if (lux != T(0) || luy != T(0) || luz != T(0)) {
-            lu[node] = T(0);
-            lu[nodes + node] = T(0);
-            lu[2 * nodes + node] = T(0);
-        }
+        T *lu = static_cast<T *>(J.lam_u);  // [nodes][4]
+        rec_ld3(lu + 4 * node, lux, luy, luz);
+        if (lux != T(0) || luy != T(0) || luz != T(0)) rec_st3(lu + 4 * node, T(0), T(0), T(0));
     }
     const T rho = T(1) + drho;
     const T om = sizeof(T) == 4 ? T(L.omega_f) : T(L.omega);
@@ -335,10 +329,10 @@ __device__ __forceinline__ bool adj_node(const LbView &L, const AdjView &J, cons
     const T Luz = luz + T(3) * orho * P1z + T(9) * orho * P2z - T(3) * (orho * uz + fpre * Fz) * P0 + T(9) * fpre * P3z;
     const T ir = T(1) / rho;
     if constexpr (MODE == ADJ_NEAR) {
-        T *lF = static_cast<T *>(J.lam_F);
-        lF[node] = fpre * (T(3) * P1x - T(3) * ux * P0 + T(9) * P2x) + T(0.5) * Lux * ir;
-        lF[nodes + node] = fpre * (T(3) * P1y - T(3) * uy * P0 + T(9) * P2y) + T(0.5) * Luy * ir;
-        lF[2 * nodes + node] = fpre * (T(3) * P1z - T(3) * uz * P0 + T(9) * P2z) + T(0.5) * Luz * ir;
+        T *lF = static_cast<T *>(J.lam_F);  // [nodes][4]
+        rec_st3(lF + 4 * node, fpre * (T(3) * P1x - T(3) * ux * P0 + T(9) * P2x) + T(0.5) * Lux * ir,
+                fpre * (T(3) * P1y - T(3) * uy * P0 + T(9) * P2y) + T(0.5) * Luy * ir,
+                fpre * (T(3) * P1z - T(3) * uz * P0 + T(9) * P2z) + T(0.5) * Luz * ir);
     }
     T lt[19];
     const T base = Lrho - (Lux * ux + Luy * uy + Luz * uz) * ir;
@@ -454,14 +448,12 @@ __global__ void __launch_bounds__(128) k_adj_interp(LbView L, MeshView M, AdjVie
         stencil_weights_d<T>(S, b, c, w, dw, wy, dwy, wz, dwz);
         const int nx = L.n[0], nxy = L.n[0] * L.n[1], nodes = L.nodes;
         const int row = wrap_index(S.base[1] + b, L.n[1], pery) * nx + wrap_index(S.base[2] + c, L.n[2], perz) * nxy;
-        T *lu = static_cast<T *>(J.lam_u);
+        T *lu = static_cast<T *>(J.lam_u);  // [nodes][4]
         const T lrx = T(lr[0]), lry = T(lr[1]), lrz = T(lr[2]);
         for (int a = 0; a < 4; ++a) {
             const int id = row + wrap_index(S.base[0] + a, nx, perx);
             const T dl = w[a] * wy * wz;
-            atomicAdd(lu + id, lrx * dl);
-            atomicAdd(lu + nodes + id, lry * dl);
-            atomicAdd(lu + 2 * nodes + id, lrz * dl);
+            rec_red3(lu + 4 * id, lrx * dl, lry * dl, lrz * dl);
             const T ul = rec[nodes + id] * lrx + rec[2 * nodes + id] * lry + rec[3 * nodes + id] * lrz;
             g[0] += ul * (dw[a] * wy * wz);
             g[1] += ul * (w[a] * dwy * wz);
@@ -518,7 +510,8 @@ __global__ void __launch_bounds__(128) k_adj_surface(LbView L, MeshView M, AdjVi
 #pragma unroll
             for (int a4 = 0; a4 < 4; ++a4) {
                 const int id = row + wrap_index(S.base[0] + a4, nx, perx);
-                const T f[3] = {lF[id], lF[nodes + id], lF[2 * nodes + id]};
+                T f[3];
+                rec_ld3(lF + 4 * id, f[0], f[1], f[2]);
                 const T wt = w[a4] * wy * wz;
                 const T g[3] = {dw[a4] * wy * wz, w[a4] * dwy * wz, w[a4] * wy * dwz};
                 #pragma unroll

@@ -901,8 +901,8 @@ bool adj_layout(const ibl_lb *lb, const ibl_mesh *m, long long T, int K, AdjLayo
     };
     A.lam[0] = take(es * 19 * nodes);
     A.lam[1] = take(es * 19 * nodes);
-    A.lam_u = take(es * 3 * nodes);
-    A.lam_F = take(es * 3 * nodes);
+    A.lam_u = take(es * 4 * nodes);  // [nodes][4] records, as the forward force and velocity
+    A.lam_F = take(es * 4 * nodes);
     A.lam_r = take(A.r_bytes);
     iblb::adj_grid(lb->v, nt, &A.lat_blocks, &A.near_blocks, &A.tri_blocks);
     A.a_part = take(sizeof(double) * 9 * (size_t)lb->v.n_frames * (size_t)(A.lat_blocks + A.near_blocks));
@@ -1906,7 +1906,7 @@ int ibl_adjoint(ibl_lb *lb, long long n_steps, int K, void *workspace, size_t by
     J.t0 = reinterpret_cast<long long *>(ws + A.t0);
     void *lam[2] = {ws + A.lam[0], ws + A.lam[1]};
     cudaError_t e = cudaMemsetAsync(lam[0], 0, es * 19 * nodes, s);  // D does not depend on the final populations
-    if (e == cudaSuccess) e = cudaMemsetAsync(J.lam_u, 0, es * 3 * nodes, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(J.lam_u, 0, es * 4 * nodes, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(J.a_part, 0, sizeof(double) * 9 * (size_t)nf * J.acc_blocks, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(J.s_part, 0, sizeof(double) * (size_t)A.tri_blocks, s);
     // the initial state is the equilibrium of the current frame 0

@@ -131,8 +131,8 @@ struct EnsembleView {
 
 // Discrete adjoint of one step (device pointers in the adjoint workspace).
 struct AdjView {
-    void *lam_u;     // [3][nodes] adjoint of the lattice velocity seen by the interpolation (storage type); kept zero between steps
-    void *lam_F;     // [3][nodes] adjoint of the Eulerian force (storage type)
+    void *lam_u;     // [nodes][4] adjoint of the lattice velocity seen by the interpolation (storage type); kept zero between steps
+    void *lam_F;     // [nodes][4] adjoint of the Eulerian force (storage type)
     double *lam_r;   // [nv][3] adjoint of the node positions
     double *a_part;  // [n_frames][acc_blocks][9] per-block partial sums of dD/dA_k (block-private)
     double *s_part;  // [tri_blocks] per-block partial sums of dD/dsigma (block-private)
