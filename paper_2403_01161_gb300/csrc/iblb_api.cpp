@@ -13,6 +13,8 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "iblb_internal.h"
 
 using iblb::Ctl;
@@ -138,6 +140,16 @@ struct Profiler {
 }  // namespace
 
 int iblb::iblb_set_error(int code, const char *msg) { return fail(code, msg); }
+
+namespace {
+// NVTX range over a C-ABI call, so that a profiler's timeline shows which
+// library call issued which kernels (header-only NVTX: no cost unless a tool
+// is attached).
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+};
+}  // namespace
 
 struct ibl_lb {
     ibl_lb_params p;
@@ -1233,6 +1245,7 @@ int ibl_set_readout(ibl_mesh *m, int every)
 
 int ibl_step(ibl_lb *lb, long long n)
 {
+    TraceRange trace_("ibl_step");
     if (!lb || n < 0) return fail(IBL_EINVAL, "bad step request");
     if (n == 0) return IBL_OK;
     int st = ensure_streams(lb);
@@ -1308,6 +1321,7 @@ int ibl_set_graphs(ibl_lb *lb, int enable)
 
 int ibl_step_record(ibl_lb *lb)
 {
+    TraceRange trace_("ibl_step_record");
     if (!lb) return fail(IBL_EINVAL, "null lattice");
     if (!lb->v.rec) return fail(IBL_EINVAL, "lattice created without record_fields");
     int st = ensure_streams(lb);
@@ -1439,6 +1453,7 @@ int ibl_load(ibl_lb *lb, const char *path)
 
 int ibl_readout(ibl_mesh *m, ibl_observables *out)
 {
+    TraceRange trace_("ibl_readout");
     if (!m || !m->lb || !out) return fail(IBL_EINVAL, "null argument");
     ibl_lb *lb = m->lb;
     cudaError_t e = iblb::launch_observables(lb->v, m->v, lb->stream);
@@ -1571,6 +1586,7 @@ int ibl_copy_neighbours(ibl_mesh *m, int32_t *ptr, int32_t *idx, int *nnz)
 
 int ibl_regularize_now(ibl_mesh *m, int *iters)
 {
+    TraceRange trace_("ibl_regularize_now");
     if (!m || !m->lb) return fail(IBL_EINVAL, "null mesh");
     ibl_lb *lb = m->lb;
     iblb::RegParams now = m->reg;
@@ -1588,6 +1604,7 @@ int ibl_regularize_now(ibl_mesh *m, int *iters)
 int ibl_run_frames(ibl_lb *lb, ibl_mesh *m, const double *A_frames, int n_frames, int steps_per_frame,
                    ibl_observables *out)
 {
+    TraceRange trace_("ibl_run_frames");
     if (!lb || !m || m->lb != lb || !A_frames || !out || n_frames < 0) return fail(IBL_EINVAL, "bad arguments");
     if (steps_per_frame != lb->v.n_hold) return fail(IBL_EINVAL, "steps_per_frame differs from the lattice's");
     if (lb->host_step % lb->v.n_hold != 0) return fail(IBL_EINVAL, "step count is not at a frame boundary");
@@ -1693,6 +1710,7 @@ int ibl_ensemble_create(int n, ibl_lb *const *members, void *workspace, size_t b
 
 int ibl_ensemble_step(ibl_ensemble *en, long long n)
 {
+    TraceRange trace_("ibl_ensemble_step");
     if (!en || n < 0) return fail(IBL_EINVAL, "bad ensemble step request");
     if (n == 0) return IBL_OK;
     const long long h0 = en->m[0]->host_step;
@@ -1770,6 +1788,7 @@ int ibl_ensemble_shape(const ibl_ensemble *en, int *shape, int *threads, int *pr
 
 int ibl_ensemble_tune(ibl_ensemble *en, int steps_per_candidate, double *ms, int *chosen)
 {
+    TraceRange trace_("ibl_ensemble_tune");
     if (!en || steps_per_candidate < 1) return fail(IBL_EINVAL, "bad tuning request");
     const long long h0 = en->m[0]->host_step;
     for (ibl_lb *lb : en->m)
@@ -1875,6 +1894,7 @@ int ibl_adjoint_workspace_size(const ibl_lb *lb, long long n_steps, int K, size_
 int ibl_adjoint(ibl_lb *lb, long long n_steps, int K, void *workspace, size_t bytes, double *D, double *dD_dsigma,
                 double *dD_dA, double *dD_dr0)
 {
+    TraceRange trace_("ibl_adjoint");
     if (!lb || !lb->mesh) return fail(IBL_EINVAL, "the lattice has no droplet");
     ibl_mesh *m = lb->mesh;
     AdjLayout A;
