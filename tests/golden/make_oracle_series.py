@@ -18,10 +18,13 @@ NAME is one of
 Each writes tests/golden/oracle_<NAME>.npz.
 
 Trajectories: a shape record (Sec. 2: volume, area, centroid, eigenvalues of
-S, v_max, D, beta) every 100 steps, the final node positions, and the
-velocity u of the last step at a fixed sample of lattice nodes (every
-`stride`-th node of the box around the final droplet, plus seeded random
-nodes of the whole box).
+S, v_max, D, beta) every 100 steps, and the state at the last record before
+any sticky error (the node positions, and the velocity u of that step at a
+fixed sample of lattice nodes: every `stride`-th node of the box around the
+droplet, plus seeded random nodes of the whole box).  A trajectory stops at
+the first record whose error bits are set (a droplet stretched until its
+stencil reaches a wall, say): "last_step" is the last clean record and
+"first_err_step" the first flagged one (-1 if none).
 """
 from __future__ import annotations
 
@@ -56,19 +59,43 @@ def _oracle_for(w):
     return o, t
 
 
-def _run_records(o, t, w, steps, log):
-    """Steps the oracle `steps` steps, a shape record every RECORD_EVERY."""
+def _u_sample(w, r, stride, n_random, seed):
+    """Flat node indices [z][y][x] of the velocity sample: every stride-th
+    node of the box of the droplet grown by 3 nodes, and n_random seeded
+    nodes of the whole box."""
+    nx, ny, nz = w.n
+    lo = np.maximum(np.floor(r.min(0)).astype(int) - 3, 0)
+    hi = np.minimum(np.floor(r.max(0)).astype(int) + 4, np.array(w.n) - 1)
+    xs, ys, zs = (np.arange(lo[a], hi[a] + 1, stride) for a in range(3))
+    Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
+    near = (X + nx * (Y + ny * Z)).ravel()
+    rng = np.random.default_rng(seed)
+    far = rng.integers(0, nx * ny * nz, size=n_random)
+    return np.unique(np.concatenate([near, far])).astype(np.int64)
+
+
+def _run_records(o, t, w, steps, log, stride=None):
+    """Steps the oracle up to `steps` steps, a shape record every
+    RECORD_EVERY, stopping at the first record with error bits set.  With
+    `stride`, also keeps the positions and the velocity sample of the last
+    clean record."""
     import oracle as O
 
     rec = {k: [] for k in ("step", "V", "area", "xc", "lam", "vmax", "D", "beta", "err", "reg_iters")}
+    snap = {}
     t0 = time.time()
     done = 0
+    first_err = -1
     while done < steps:
         k = min(RECORD_EVERY, steps - done)
         o.step(k)
         done += k
         if done % RECORD_EVERY:
             continue
+        if o.error:
+            first_err = done
+            log("  %s: error bits %d at the record of step %d; stopping" % (w.name, o.error, done))
+            break
         r, _ = o.mesh()
         A = w.frames[_used_frame(done, w.n_hold, len(w.frames))]
         ob = O.observables(r, t, A)
@@ -82,37 +109,27 @@ def _run_records(o, t, w, steps, log):
         rec["beta"].append(ob["beta"])
         rec["err"].append(o.error)
         rec["reg_iters"].append(o.reg_iters)
+        snap["r"] = r
+        if stride is not None:
+            _, u, _ = o.fields()
+            idx = _u_sample(w, r, stride, 4096, 12345)
+            snap["u_idx"] = idx
+            snap["u_sample"] = u.reshape(3, -1)[:, idx]
+            snap["u_norm_all"] = np.linalg.norm(u)
         if done % (10 * RECORD_EVERY) == 0:
-            log("  %s step %d D %.6f err %d (%.0f s)" % (w.name, done, ob["D"], o.error, time.time() - t0))
-    return {k: np.asarray(v) for k, v in rec.items()}
-
-
-def _u_sample(w, r, stride, n_random, seed):
-    """Flat node indices [z][y][x] of the velocity sample: every stride-th
-    node of the box of the final droplet grown by 3 nodes, and n_random
-    seeded nodes of the whole box."""
-    nx, ny, nz = w.n
-    lo = np.maximum(np.floor(r.min(0)).astype(int) - 3, 0)
-    hi = np.minimum(np.floor(r.max(0)).astype(int) + 4, np.array(w.n) - 1)
-    xs, ys, zs = (np.arange(lo[a], hi[a] + 1, stride) for a in range(3))
-    Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
-    near = (X + nx * (Y + ny * Z)).ravel()
-    rng = np.random.default_rng(seed)
-    far = rng.integers(0, nx * ny * nz, size=n_random)
-    return np.unique(np.concatenate([near, far])).astype(np.int64)
+            log("  %s step %d D %.6f (%.0f s)" % (w.name, done, ob["D"], time.time() - t0))
+    out = {k: np.asarray(v) for k, v in rec.items()}
+    return out, snap, first_err
 
 
 def trajectory(w, stride, log):
     o, t = _oracle_for(w)
     t0 = time.time()
-    rec = _run_records(o, t, w, w.steps, log)
-    r, _ = o.mesh()
-    _, u, _ = o.fields()
-    idx = _u_sample(w, r, stride, 4096, 12345)
+    rec, snap, first_err = _run_records(o, t, w, w.steps, log, stride)
     out = {f"rec_{k}": v for k, v in rec.items()}
-    out.update({"r_final": r, "tris": t, "u_idx": idx, "u_sample": u.reshape(3, -1)[:, idx],
-                "u_norm_all": np.linalg.norm(u), "err_final": o.error, "steps": w.steps,
-                "oracle_seconds": time.time() - t0})
+    out.update({"r_last": snap["r"], "tris": t, "u_idx": snap["u_idx"], "u_sample": snap["u_sample"],
+                "u_norm_all": snap["u_norm_all"], "last_step": int(rec["step"][-1]), "first_err_step": first_err,
+                "steps": w.steps, "oracle_seconds": time.time() - t0})
     o.close()
     return out
 
@@ -135,14 +152,14 @@ def ensemble8(log):
     out = {}
     for k, w in enumerate(config.ensemble_workloads(8, steps=10000)):
         o, t = _oracle_for(w)
-        rec = _run_records(o, t, w, w.steps, log)
-        r, _ = o.mesh()
+        rec, snap, first_err = _run_records(o, t, w, w.steps, log)
         for key, v in rec.items():
             out[f"m{k}_rec_{key}"] = v
-        out[f"m{k}_r_final"] = r
-        out[f"m{k}_err_final"] = o.error
+        out[f"m{k}_r_last"] = snap["r"]
+        out[f"m{k}_last_step"] = int(rec["step"][-1])
+        out[f"m{k}_first_err_step"] = first_err
         o.close()
-        log("member %d (%s) done" % (k, w.name))
+        log("member %d (%s) done: last clean record %d, first flagged %d" % (k, w.name, rec["step"][-1], first_err))
     out["members"] = 8
     out["steps"] = 10000
     return out
