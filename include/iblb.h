@@ -64,10 +64,16 @@ extern "C" {
 #define IBL_ERRBIT_WALL 4
 
 enum { IBL_BC_ZOU_HE = 0, IBL_BC_PERIODIC = 1 };
-/* Edge/corner rule with a moving wall: the printed rule of Eq. (ZH_edges)
- * plus the moving-wall term -2 w_i (c_i.u_w)/c_s^2 (default), or literally
- * as printed (no velocity term at edges and corners). */
-enum { IBL_EDGE_PAPER_PLUS_WALL = 0, IBL_EDGE_PAPER_LITERAL = 1 };
+/* Edge/corner rule, Eqs. (ZH_edges), (zh-buried-links-edges),
+ * (zh-buried-links-corners).  IBL_EDGE_COUNTER_SLIP (default): the face
+ * rule's construction of Eq. (ZH_bulk) carried to two normals -- the
+ * tangential sum with the sign that removes the edge-line momentum, the
+ * moving-wall bounce-back term -2 w_i (c_i.u_w)/c_s^2, the wall's edge-line
+ * share -(t_i.u_w)/12, and each buried link plus 3 w_j (c_j.u_w) -- so that
+ * every edge and corner node carries exactly the momentum u_w (rho0 = 1).
+ * IBL_EDGE_PAPER_LITERAL: the equations as printed (minus sign, no wall
+ * velocity at edges and corners). */
+enum { IBL_EDGE_COUNTER_SLIP = 0, IBL_EDGE_PAPER_LITERAL = 1 };
 /* Population storage: FP32 deviations f_i - w_i, or FP64 deviations. */
 enum { IBL_FP32_DEV = 0, IBL_FP64 = 1 };
 

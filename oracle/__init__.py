@@ -31,7 +31,7 @@ from .oracle import (  # noqa: F401
     OracleSim,
     BC_ZOU_HE,
     BC_PERIODIC,
-    EDGE_PAPER_PLUS_WALL,
+    EDGE_COUNTER_SLIP,
     EDGE_PAPER_LITERAL,
     ERR_UNSTABLE,
     ERR_NOCONV,

@@ -39,9 +39,12 @@
  * half-space test and the solid-angle winding number; interpolation and
  * advection by exact transport in a uniform flow, exact reproduction of a
  * linear velocity field and the (k - 1/2) g velocity of a fluid under a
- * uniform force), except the edge and
- * corner rules with a moving wall (EDGE_PAPER_PLUS_WALL), whose agreement
- * with the paper is "parity unpinned" (only the rest state is pinned).
+ * uniform force).  The edge and corner rules with a moving wall
+ * (EDGE_COUNTER_SLIP) are a reading of Eqs. (ZH_edges),
+ * (zh-buried-links-edges) and (zh-buried-links-corners), pinned by what that
+ * reading is built to meet: the rest state, the no-slip of an edge at rest,
+ * the exact wall momentum of every edge and corner node for any input, and
+ * a linear shear kept inside the box.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -129,7 +132,7 @@ double orc_peskin_phi(double x)
  * streaming when the node it would come from, x - c_j, lies outside the box:
  * c_ja * side[a] < 0 on some boundary axis.
  * ------------------------------------------------------------------------- */
-enum { EDGE_PAPER_PLUS_WALL = 0, EDGE_PAPER_LITERAL = 1 };
+enum { EDGE_COUNTER_SLIP = 0, EDGE_PAPER_LITERAL = 1 };
 
 static int unknown(int j, const int side[3])
 {
@@ -172,11 +175,25 @@ static double bc_face(double f[Q], int a, int s, const double uw[3])
     return rho;
 }
 
-/* Edge node, case (b): Eq. (ZH_edges) for the non-buried unknowns (t_i read
- * as c_i projected on the edge line; with EDGE_PAPER_PLUS_WALL the moving
- * wall term -2 w_i rho0 (c_i.u_w)/c_s^2, rho0 = 1, is added), then the
- * buried links of Eq. (zh-buried-links-edges) and f_0 = 12 f^(1,2).
- * Parity unpinned for a moving wall. */
+/* Edge node, case (b): Eq. (ZH_edges) for the non-buried unknowns, t_i read
+ * as c_i projected on the edge line, then the buried links of
+ * Eq. (zh-buried-links-edges) and f_0 = 12 f^(1,2).
+ *
+ * EDGE_PAPER_LITERAL takes the equation as printed: the tangential sum with
+ * a minus sign and no wall velocity.  Read with the face rule's convention
+ * (c_i outgoing, f_{-i} reflected), that sign adds the along-edge momentum
+ * of the edge-line pair a second time instead of removing it, so an edge at
+ * rest slips.  EDGE_COUNTER_SLIP is the face rule's construction carried to
+ * two normals, rho0 = 1:
+ *   f_{-i} = f_i - 2 w_i rho0 (c_i.u_w)/c_s^2 - rho0/12 (t_i.u_w)
+ *            + 1/4 sum_j f_j (t_i.c_j)(1 - |c_j.n1|)(1 - |c_j.n2|),
+ * whose sum cancels the edge-line momentum (four reflected links with a
+ * component along the edge, 1/4 each) and whose t_i.u_w term restores the
+ * wall's own share of it (the edge-line pair carries 1/3 of rho u in
+ * equilibrium, 1/4 of which each link would remove); and each buried link
+ * gets f^(1,2) plus its half of the moving-wall difference,
+ * w_j rho0 (c_j.u_w)/c_s^2.  The node then carries the momentum rho0 u_w
+ * exactly, whatever arrived, and an edge at rest imposes no slip. */
 static void bc_edge(double f[Q], const int side[3], const double uw[3], int rule)
 {
     double n1[3] = {0, 0, 0}, n2[3] = {0, 0, 0};
@@ -203,8 +220,13 @@ static void bc_edge(double f[Q], const int side[3], const double uw[3], int rule
             double tc = t[0] * CV[k][0] + t[1] * CV[k][1] + t[2] * CV[k][2];
             corr += f[k] * tc * (1.0 - k1) * (1.0 - k2);
         }
-        double v = f[i] - 0.25 * corr;
-        if (rule == EDGE_PAPER_PLUS_WALL) v -= 2.0 * weight(i) * 1.0 * cdot(i, uw) / CS2;
+        double v;
+        if (rule == EDGE_PAPER_LITERAL) {
+            v = f[i] - 0.25 * corr;
+        } else {
+            double tu = t[0] * uw[0] + t[1] * uw[1] + t[2] * uw[2];
+            v = f[i] - 2.0 * weight(i) * 1.0 * cdot(i, uw) / CS2 - 1.0 / 12.0 * tu + 0.25 * corr;
+        }
         g[j] = v;
     }
     double e[3] = {n1[1] * n2[2] - n1[2] * n2[1], n1[2] * n2[0] - n1[0] * n2[2],
@@ -219,16 +241,22 @@ static void bc_edge(double f[Q], const int side[3], const double uw[3], int rule
         if (wgt != 0.0) fb += g[i] * wgt; /* buried terms have weight 0 */
     }
     fb /= 22.0;
-    for (int j = 1; j < Q; ++j)
-        if (unknown(j, side) && unknown(opposite(j), side)) g[j] = fb;
+    for (int j = 1; j < Q; ++j) {
+        if (!(unknown(j, side) && unknown(opposite(j), side))) continue;
+        g[j] = fb;
+        if (rule == EDGE_COUNTER_SLIP) g[j] += weight(j) * 1.0 * cdot(j, uw) / CS2;
+    }
     g[0] = 12.0 * fb;
     memcpy(f, g, sizeof g);
 }
 
 /* Corner node, case (c): Eq. (zh-buried-links-corners) and f_0 = 12 f^(1..6).
- * The paper gives no rule for the non-buried unknowns; they take moving-wall
- * bounce-back (plain bounce-back under EDGE_PAPER_LITERAL).  Parity unpinned
- * for a moving wall. */
+ * The paper gives no rule for the non-buried unknowns (three normals leave
+ * no tangential direction); they take moving-wall bounce-back, and under
+ * EDGE_COUNTER_SLIP each buried link adds its half of the moving-wall
+ * difference, w_j rho0 (c_j.u_w)/c_s^2, as at an edge, so that the node
+ * carries rho0 u_w exactly.  EDGE_PAPER_LITERAL: plain bounce-back and the
+ * buried value alone. */
 static void bc_corner(double f[Q], const int side[3], const double uw[3], int rule)
 {
     double s[3] = {(double)-side[0], (double)-side[1], (double)-side[2]}; /* n1+n2+n3 */
@@ -240,7 +268,7 @@ static void bc_corner(double f[Q], const int side[3], const double uw[3], int ru
         if (cs == 0.0) continue; /* buried */
         int i = opposite(j);
         double v = f[i];
-        if (rule == EDGE_PAPER_PLUS_WALL) v -= 2.0 * weight(i) * 1.0 * cdot(i, uw) / CS2;
+        if (rule == EDGE_COUNTER_SLIP) v -= 2.0 * weight(i) * 1.0 * cdot(i, uw) / CS2;
         g[j] = v;
     }
     double fb = 0.0;
@@ -252,7 +280,9 @@ static void bc_corner(double f[Q], const int side[3], const double uw[3], int ru
     fb /= 18.0;
     for (int j = 1; j < Q; ++j) {
         double cs = CV[j][0] * s[0] + CV[j][1] * s[1] + CV[j][2] * s[2];
-        if (cs == 0.0) g[j] = fb;
+        if (cs != 0.0) continue;
+        g[j] = fb;
+        if (rule == EDGE_COUNTER_SLIP) g[j] += weight(j) * 1.0 * cdot(j, uw) / CS2;
     }
     g[0] = 12.0 * fb;
     memcpy(f, g, sizeof g);

@@ -26,7 +26,7 @@ _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
 
 BC_ZOU_HE, BC_PERIODIC = 0, 1
-EDGE_PAPER_PLUS_WALL, EDGE_PAPER_LITERAL = 0, 1
+EDGE_COUNTER_SLIP, EDGE_PAPER_LITERAL = 0, 1
 ERR_UNSTABLE, ERR_NOCONV, ERR_WALL = 1, 2, 4
 
 _lock = threading.Lock()
@@ -142,7 +142,7 @@ def peskin_phi(x: float) -> float:
     return lib().orc_peskin_phi(float(x))
 
 
-def bc_node(f, side, uw, rule: int = EDGE_PAPER_PLUS_WALL) -> np.ndarray:
+def bc_node(f, side, uw, rule: int = EDGE_COUNTER_SLIP) -> np.ndarray:
     """Boundary reconstruction of one node's 19 populations (returns a copy)."""
     g = np.array(f, dtype=np.float64).copy()
     s = np.ascontiguousarray(side, dtype=np.int32)
@@ -352,7 +352,7 @@ class OracleSim:
     BC_PERIODIC.
     """
 
-    def __init__(self, n, tau, frames, n_hold, bc=(BC_ZOU_HE,) * 3, rule=EDGE_PAPER_PLUS_WALL):
+    def __init__(self, n, tau, frames, n_hold, bc=(BC_ZOU_HE,) * 3, rule=EDGE_COUNTER_SLIP):
         self.L = lib()
         self.n = tuple(int(v) for v in n)
         self.nn = self.n[0] * self.n[1] * self.n[2]

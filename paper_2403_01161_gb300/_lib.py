@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libiblb.so")
 IBL_ABI_VERSION = 1
 IBL_OK, IBL_EINVAL, IBL_ENOMEM, IBL_ECUDA, IBL_EUNSTABLE, IBL_ENOCONV, IBL_EWALL = 0, -1, -2, -3, -4, -5, -6
 BC_ZOU_HE, BC_PERIODIC = 0, 1
-EDGE_PAPER_PLUS_WALL, EDGE_PAPER_LITERAL = 0, 1
+EDGE_COUNTER_SLIP, EDGE_PAPER_LITERAL = 0, 1
 FP32_DEV, FP64 = 0, 1
 ENSEMBLE_SHAPES = 32
 ERRBIT_UNSTABLE, ERRBIT_NOCONV, ERRBIT_WALL = 1, 2, 4

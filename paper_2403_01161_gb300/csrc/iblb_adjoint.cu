@@ -67,6 +67,15 @@ __device__ __forceinline__ void stencil_weights_d(const NodeStencil &S, int b, i
     dwz = peskin_dphi<T>(fz + T(1 - c));
 }
 
+// Transpose of a buried link's moving-wall share 3 w_j (c_j.u_w).
+template <typename T, int J>
+__device__ __forceinline__ void buried_wall_share_adjoint(T l, T (&luw)[3])
+{
+    if constexpr (cxf(J) != 0) luw[0] += T(3.0 * wgt(J)) * T(cxf(J)) * l;
+    if constexpr (cyf(J) != 0) luw[1] += T(3.0 * wgt(J)) * T(cyf(J)) * l;
+    if constexpr (czf(J) != 0) luw[2] += T(3.0 * wgt(J)) * T(czf(J)) * l;
+}
+
 // ---------------------------------------------------------------------------
 // Transpose of the boundary rebuild.  lt: adjoint of the rebuilt populations
 // (outputs), lin: adjoint of the streamed populations (inputs; unknown and
@@ -130,11 +139,14 @@ __device__ __forceinline__ void bc_adjoint(const T (&lt)[19], T (&lin)[19], T rh
     } else if constexpr (NB == 2) {
         constexpr int E = SX == 0 ? 0 : (SY == 0 ? 1 : 2);
         constexpr int PE = E + 1, ME = E + 10;
-        const bool wall = (rule == IBL_EDGE_PAPER_PLUS_WALL);
+        const bool slip = (rule == IBL_EDGE_COUNTER_SLIP);
         T lfb = T(12) * lt[0];
         sfor<19>([&](auto J) {
             constexpr int j = decltype(J)::value;
-            if constexpr (j != 0 && unknown_dir<SX, SY, SZ>(j) && unknown_dir<SX, SY, SZ>(opp(j))) lfb += lt[j];
+            if constexpr (j != 0 && unknown_dir<SX, SY, SZ>(j) && unknown_dir<SX, SY, SZ>(opp(j))) {
+                lfb += lt[j];
+                if (slip) buried_wall_share_adjoint<T, j>(lt[j], luw);
+            }
         });
         // adjoint of each non-buried value, including its share of f_b
         T lv[19];
@@ -155,23 +167,28 @@ __device__ __forceinline__ void bc_adjoint(const T (&lt)[19], T (&lin)[19], T rh
                 constexpr int i = opp(j);
                 lin[i] += lv[j];
                 if constexpr (comp(i, E) != 0) {
-                    lin[PE] -= T(0.25) * T(comp(i, E)) * lv[j];
-                    lin[ME] += T(0.25) * T(comp(i, E)) * lv[j];
+                    const T q = (slip ? T(0.25) : T(-0.25)) * T(comp(i, E)) * lv[j];
+                    lin[PE] += q;
+                    lin[ME] -= q;
                 }
-                if (wall) {
+                if (slip) {
                     if constexpr (cxf(i) != 0) luw[0] -= T(6.0 * wgt(i)) * T(cxf(i)) * lv[j];
                     if constexpr (cyf(i) != 0) luw[1] -= T(6.0 * wgt(i)) * T(cyf(i)) * lv[j];
                     if constexpr (czf(i) != 0) luw[2] -= T(6.0 * wgt(i)) * T(czf(i)) * lv[j];
+                    if constexpr (comp(i, E) != 0) luw[E] -= T(1.0 / 12.0) * T(comp(i, E)) * lv[j];
                 }
             }
         });
     } else if constexpr (NB == 3) {
-        const bool wall = (rule == IBL_EDGE_PAPER_PLUS_WALL);
+        const bool wall = (rule == IBL_EDGE_COUNTER_SLIP);
         T lfb = T(12) * lt[0];
         sfor<19>([&](auto J) {
             constexpr int j = decltype(J)::value;
             constexpr int cs = cxf(j) * SX + cyf(j) * SY + czf(j) * SZ;
-            if constexpr (j != 0 && cs == 0) lfb += lt[j];
+            if constexpr (j != 0 && cs == 0) {
+                lfb += lt[j];
+                if (wall) buried_wall_share_adjoint<T, j>(lt[j], luw);
+            }
         });
         T lv[19];
         sfor<19>([&](auto K) {

@@ -1003,7 +1003,7 @@ int ibl_lb_create(const ibl_lb_params *p, const double *A_frames, int n_frames, 
     if (!out || !A_frames) return fail(IBL_EINVAL, "null argument");
     if (!lb_layout(p, n_frames, L)) return fail(IBL_EINVAL, "invalid lattice parameters (version, sizes, bc, precision)");
     if (!(p->tau > 0.5) || !std::isfinite(p->tau)) return fail(IBL_EINVAL, "tau must be > 1/2");
-    if (p->edge_rule != IBL_EDGE_PAPER_PLUS_WALL && p->edge_rule != IBL_EDGE_PAPER_LITERAL)
+    if (p->edge_rule != IBL_EDGE_COUNTER_SLIP && p->edge_rule != IBL_EDGE_PAPER_LITERAL)
         return fail(IBL_EINVAL, "unknown edge rule");
     if (steps_per_frame < 1) return fail(IBL_EINVAL, "steps_per_frame must be >= 1");
     for (int k = 0; k < 9 * n_frames; ++k)

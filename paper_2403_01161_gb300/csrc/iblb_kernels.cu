@@ -31,6 +31,18 @@
 namespace iblb {
 namespace {
 
+// Half of the moving-wall difference f_eq(c_j) - f_eq(-c_j) at rho0 = 1:
+// 3 w_j (c_j.u_w).
+template <typename T, int J>
+__device__ __forceinline__ T buried_wall_share(const T (&uw)[3])
+{
+    T cu = T(0);
+    if constexpr (cxf(J) != 0) cu += T(cxf(J)) * uw[0];
+    if constexpr (cyf(J) != 0) cu += T(cyf(J)) * uw[1];
+    if constexpr (czf(J) != 0) cu += T(czf(J)) * uw[2];
+    return T(3.0 * wgt(J)) * cu;
+}
+
 template <typename T, int SX, int SY, int SZ>
 __device__ __forceinline__ void bc_apply(T (&f)[19], const T (&uw)[3], int rule)
 {
@@ -73,23 +85,31 @@ __device__ __forceinline__ void bc_apply(T (&f)[19], const T (&uw)[3], int rule)
     } else if constexpr (NB == 2) {
         // Edge, Eq. (ZH_edges) (t_i = projection of c_i on the edge line),
         // then the buried links, Eq. (zh-buried-links-edges), f_0 = 12 f_b.
+        // Counter-slip reading (default): the tangential sum with the face
+        // rule's sign, so that it cancels the edge-line momentum f_{+e} -
+        // f_{-e}, moving-wall bounce-back, the wall's edge-line share
+        // -(t_i.u_w)/12, and each buried link plus its half of the
+        // moving-wall difference 3 w_j (c_j.u_w): the node then carries
+        // exactly u_w (rho0 = 1).  The literal rule: the printed sign and no
+        // wall terms.
         constexpr int E = SX == 0 ? 0 : (SY == 0 ? 1 : 2);
         constexpr int PE = E + 1, ME = E + 10;  // +e_E and -e_E in the library order
         static_assert(comp(PE, E) == 1 && comp(ME, E) == -1, "axis links");
         const T dE = f[PE] - f[ME];
-        const bool wall = (rule == IBL_EDGE_PAPER_PLUS_WALL);
+        const bool slip = (rule == IBL_EDGE_COUNTER_SLIP);
         sfor<19>([&](auto J) {
             constexpr int j = decltype(J)::value;
             if constexpr (j != 0 && unknown_dir<SX, SY, SZ>(j) && !unknown_dir<SX, SY, SZ>(opp(j))) {
                 constexpr int i = opp(j);
                 T v = f[i];
-                if constexpr (comp(i, E) != 0) v -= T(0.25) * T(comp(i, E)) * dE;
-                if (wall) {
+                if constexpr (comp(i, E) != 0) v += (slip ? T(0.25) : T(-0.25)) * T(comp(i, E)) * dE;
+                if (slip) {
                     T cu = T(0);
                     if constexpr (cxf(i) != 0) cu += T(cxf(i)) * uw[0];
                     if constexpr (cyf(i) != 0) cu += T(cyf(i)) * uw[1];
                     if constexpr (czf(i) != 0) cu += T(czf(i)) * uw[2];
                     v -= T(6.0 * wgt(i)) * cu;
+                    if constexpr (comp(i, E) != 0) v -= T(1.0 / 12.0) * T(comp(i, E)) * uw[E];
                 }
                 f[j] = v;
             }
@@ -102,13 +122,15 @@ __device__ __forceinline__ void bc_apply(T (&f)[19], const T (&uw)[3], int rule)
         const T fb = sb * T(1.0 / 22.0);
         sfor<19>([&](auto J) {
             constexpr int j = decltype(J)::value;
-            if constexpr (j != 0 && unknown_dir<SX, SY, SZ>(j) && unknown_dir<SX, SY, SZ>(opp(j))) f[j] = fb;
+            if constexpr (j != 0 && unknown_dir<SX, SY, SZ>(j) && unknown_dir<SX, SY, SZ>(opp(j)))
+                f[j] = slip ? fb + buried_wall_share<T, j>(uw) : fb;
         });
         f[0] = T(12) * fb;
     } else if constexpr (NB == 3) {
         // Corner, Eq. (zh-buried-links-corners); non-buried unknowns take
-        // (moving-wall) bounce-back; f_0 = 12 f_b.
-        const bool wall = (rule == IBL_EDGE_PAPER_PLUS_WALL);
+        // (moving-wall) bounce-back, buried links (plus their moving-wall
+        // share under the counter-slip reading); f_0 = 12 f_b.
+        const bool wall = (rule == IBL_EDGE_COUNTER_SLIP);
         sfor<19>([&](auto J) {
             constexpr int j = decltype(J)::value;
             constexpr int cs = -(cxf(j) * SX + cyf(j) * SY + czf(j) * SZ);
@@ -135,7 +157,7 @@ __device__ __forceinline__ void bc_apply(T (&f)[19], const T (&uw)[3], int rule)
         sfor<19>([&](auto J) {
             constexpr int j = decltype(J)::value;
             constexpr int cs = cxf(j) * SX + cyf(j) * SY + czf(j) * SZ;
-            if constexpr (j != 0 && cs == 0) f[j] = fb;
+            if constexpr (j != 0 && cs == 0) f[j] = wall ? fb + buried_wall_share<T, j>(uw) : fb;
         });
         f[0] = T(12) * fb;
     }

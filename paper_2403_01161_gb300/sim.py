@@ -64,7 +64,7 @@ class Sim:
     """
 
     def __init__(self, n: Sequence[int], tau: float, frames, n_hold: int, *, bc=(L.BC_ZOU_HE,) * 3,
-                 precision: str = "fp32", edge_rule: int = L.EDGE_PAPER_PLUS_WALL, record_fields: bool = False,
+                 precision: str = "fp32", edge_rule: int = L.EDGE_COUNTER_SLIP, record_fields: bool = False,
                  device=None, stream: Optional[torch.cuda.Stream] = None):
         self.lib = L.load()
         self.device = torch.device(device if device is not None else "cuda")
