@@ -1950,18 +1950,21 @@ int ibl_adjoint(ibl_lb *lb, long long n_steps, int K, void *workspace, size_t by
         return ws + A.traj + A.traj_step * ((size_t)set * A.kmax + k);
     };
     std::map<int, cudaGraphExec_t> rec_graph;
-    const size_t patch_off = offsetof(Ctl, patch_lo);
     int hook_set = 0;
-    auto record_hook = [&](int k, cudaStream_t, cudaStream_t sH) -> int {
+    // step k of a recording: its force/spread kernel copies r_k and the
+    // step's patch into the trajectory slot, its lattice kernels store the
+    // moments into the moment slot
+    auto record_hook = [&](int k, cudaStream_t, cudaStream_t) -> int {
         char *slot = traj_slot(hook_set, k);
-        cudaError_t ee = cudaMemcpyAsync(slot, m->v.r, A.r_bytes, cudaMemcpyDeviceToDevice, sH);
-        // the patch of the step (written by the previous force kernel on this stream)
-        if (ee == cudaSuccess)
-            ee = cudaMemcpyAsync(slot + A.traj_ctl + patch_off, reinterpret_cast<char *>(lb->v.ctl) + patch_off,
-                                 sizeof(Ctl) - patch_off, cudaMemcpyDeviceToDevice, sH);
-        if (ee != cudaSuccess) return cuda_fail(ee, "trajectory copy");
+        m->v.rec_r = reinterpret_cast<double *>(slot);
+        m->v.rec_ctl = reinterpret_cast<Ctl *>(slot + A.traj_ctl);
         lb->v.rec = rec_slot(hook_set, k);
         return IBL_OK;
+    };
+    auto end_recording = [&]() {
+        lb->v.rec = rec_saved;
+        m->v.rec_r = nullptr;
+        m->v.rec_ctl = nullptr;
     };
     // graph of a full-length recording starting at t0 (captured on first use)
     auto record_graph = [&](long long t0, bool shape_records, int set, cudaGraphExec_t *out) -> int {
@@ -1974,7 +1977,7 @@ int ibl_adjoint(ibl_lb *lb, long long n_steps, int K, void *workspace, size_t by
             m->readout_every = shape_records ? readout : 0;
             cudaGraphExec_t g = nullptr;
             const int r = capture_steps(lb, K, true, record_hook, &g);
-            lb->v.rec = rec_saved;
+            end_recording();
             m->readout_every = readout;
             lb->host_step = saved;
             if (r != IBL_OK) return r;
@@ -2005,7 +2008,7 @@ int ibl_adjoint(ibl_lb *lb, long long n_steps, int K, void *workspace, size_t by
             r = record_hook(k, q, q);
             if (r == IBL_OK) r = one_step(lb, true, q, q);
         }
-        lb->v.rec = rec_saved;
+        end_recording();
         m->readout_every = readout;
         return r;
     };
@@ -2158,7 +2161,7 @@ int ibl_adjoint(ibl_lb *lb, long long n_steps, int K, void *workspace, size_t by
     if (e == cudaSuccess) e = cudaEventRecord(ev[12], s_rec);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[12], 0);
     if (e != cudaSuccess && st == IBL_OK) st = cuda_fail(e, "adjoint join");
-    lb->v.rec = rec_saved;
+    end_recording();
     // the initial populations depend on frame 0
     if (st == IBL_OK) {
         e = iblb::launch_adj_init(lb->v, J, lam[cur], s);

@@ -77,6 +77,11 @@ struct MeshView {
     double *obs_part;      // per-block partial sums of the shape-record kernel, [kObsBlocksMax][11]
     ibl_observables *ring;
     int ring_cap;
+    // Adjoint recording (null otherwise): the force/spread kernel of a step
+    // copies the positions the step starts from to rec_r [nv][3] and the
+    // step's patch (its buffer's patch_lo / patch_ext) to rec_ctl.
+    double *rec_r = nullptr;
+    Ctl *rec_ctl = nullptr;
 };
 
 struct RegParams {

@@ -664,6 +664,19 @@ __device__ __forceinline__ void spread_body(const LbView &L, const MeshView &M, 
         M.fn[3 * i] = F[0];
         M.fn[3 * i + 1] = F[1];
         M.fn[3 * i + 2] = F[2];
+        if (M.rec_r) {
+            M.rec_r[3 * i] = M.r[3 * i];
+            M.rec_r[3 * i + 1] = M.r[3 * i + 1];
+            M.rec_r[3 * i + 2] = M.r[3 * i + 2];
+        }
+    }
+    if (M.rec_ctl && blk == 0 && threadIdx.x == 32) {
+        // this step's patch buffer; warp 0 writes the next step's
+        const int pb = (next_buf + 2) % 3;
+        for (int a = 0; a < 4; ++a) {
+            M.rec_ctl->patch_lo[pb][a] = L.ctl->patch_lo[pb][a];
+            M.rec_ctl->patch_ext[pb][a] = L.ctl->patch_ext[pb][a];
+        }
     }
     const NodeStencil S = node_stencil<LANES, P>(L, M.r + 3 * i, lane, &K);
     if (valid && !S.ok && lane == 0) atomicOr(&L.ctl->err, IBL_ERRBIT_WALL);
