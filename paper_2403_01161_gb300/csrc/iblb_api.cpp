@@ -164,7 +164,10 @@ struct ibl_lb {
     // CUDA-graph replay of whole chunks of steps
     bool graphs = true;
     int chunk = 0;                       // steps per captured chunk (0 = none captured)
-    cudaGraphExec_t gexec = nullptr;
+    // one graph per position in the schedule period when that period is the
+    // bare 6 (AA parity x three patch buffers), else only slot 0
+    static constexpr int kPhases = 6;
+    cudaGraphExec_t gexec[kPhases] = {};
     long long steps_eager = 0, steps_replayed = 0;  // counts of ibl_step's two paths
     cudaStream_t cap_stream = nullptr;   // private streams used only for capture
     cudaStream_t cap_helper = nullptr;
@@ -185,7 +188,8 @@ struct ibl_lb {
     cudaEvent_t cFork = nullptr, cJoin = nullptr, cCentre = nullptr;
     ~ibl_lb()
     {
-        if (gexec) cudaGraphExecDestroy(gexec);
+        for (cudaGraphExec_t g : gexec)
+            if (g) cudaGraphExecDestroy(g);
         if (cap_stream) cudaStreamDestroy(cap_stream);
         if (cap_helper) cudaStreamDestroy(cap_helper);
         if (helper) cudaStreamDestroy(helper);
@@ -543,25 +547,35 @@ namespace {
 
 void drop_graph(ibl_lb *lb)
 {
-    if (lb && lb->gexec) {
-        cudaGraphExecDestroy(lb->gexec);
-        lb->gexec = nullptr;
-    }
-    if (lb) lb->chunk = 0;
+    if (!lb) return;
+    for (cudaGraphExec_t &g : lb->gexec)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    lb->chunk = 0;
 }
 
 long long gcd_ll(long long a, long long b) { return b == 0 ? a : gcd_ll(b, a % b); }
 
-// Steps per chunk: a multiple of 6 (AA parity and the three patch buffers)
-// and of the regularisation and readout periods, at least 32; 0 when that
-// would exceed 2048.
-int chunk_length(const ibl_lb *lb)
+// Schedule period: the launches of a step repeat with this period in the
+// step index -- 6 (AA parity and the three patch buffers), times the
+// regularisation and readout periods.
+long long schedule_period(const ibl_lb *lb)
 {
     long long c = 6;
     const ibl_mesh *m = lb->mesh;
     auto lcm = [&](long long a, long long b) { return a / gcd_ll(a, b) * b; };
     if (m && m->reg_every > 0) c = lcm(c, m->reg_every);
     if (m && m->readout_every > 0) c = lcm(c, m->readout_every);
+    return c;
+}
+
+// Steps per chunk: a multiple of the schedule period, at least 32; 0 when
+// that would exceed 2048.
+int chunk_length(const ibl_lb *lb)
+{
+    long long c = schedule_period(lb);
     if (c > 2048) return 0;
     while (c < 32) c *= 2;
     return (int)c;
@@ -634,11 +648,12 @@ int capture_steps(ibl_lb *lb, int n, bool record, Hook &&hook, cudaGraphExec_t *
     return st;
 }
 
-// Captures one chunk of plain steps starting at an aligned step
-// (host_step % chunk == 0).
-int capture_chunk(ibl_lb *lb, int chunk)
+// Captures one chunk of plain steps starting at the current step into
+// graph slot `slot`.
+int capture_chunk(ibl_lb *lb, int chunk, int slot)
 {
-    const int st = capture_steps(lb, chunk, false, [](int, cudaStream_t, cudaStream_t) { return IBL_OK; }, &lb->gexec);
+    const int st =
+        capture_steps(lb, chunk, false, [](int, cudaStream_t, cudaStream_t) { return IBL_OK; }, &lb->gexec[slot]);
     if (st == IBL_OK) lb->chunk = chunk;
     else drop_graph(lb);
     return st;
@@ -1256,6 +1271,10 @@ int ibl_step(ibl_lb *lb, long long n)
     if (e != cudaSuccess) return cuda_fail(e, "stream fork");
     bool forked = true;  // eager steps may use the helper stream
     const int chunk = lb->graphs ? chunk_length(lb) : 0;
+    // with the bare period of 6, a chunk may start at any step (one graph
+    // per phase); otherwise only at multiples of the chunk
+    const long long period = chunk > 0 ? schedule_period(lb) : 0;
+    const bool keyed = chunk > 0 && period <= ibl_lb::kPhases;
     long long done = 0;
     // whole chunks at chunk boundaries, eager steps elsewhere (consecutive
     // eager steps pipeline across steps on the two streams, while a graph
@@ -1274,13 +1293,14 @@ int ibl_step(ibl_lb *lb, long long n)
         return IBL_OK;
     };
     while (done < n) {
-        if (chunk > 0 && lb->host_step % chunk == 0 && n - done >= chunk) {
-            if (lb->chunk != chunk || !lb->gexec) {
-                drop_graph(lb);
-                st = capture_chunk(lb, chunk);
+        if (chunk > 0 && n - done >= chunk && (keyed || lb->host_step % chunk == 0)) {
+            const int slot = keyed ? (int)(lb->host_step % period) : 0;
+            if (lb->chunk != chunk) drop_graph(lb);
+            if (!lb->gexec[slot]) {
+                st = capture_chunk(lb, chunk, slot);
                 if (st != IBL_OK) return st;
             }
-            st = replay(lb->gexec, chunk);
+            st = replay(lb->gexec[slot], chunk);
             if (st != IBL_OK) return st;
             continue;
         }

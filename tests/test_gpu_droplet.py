@@ -168,6 +168,29 @@ def test_wall_contact_is_reported():
     assert g.status() == L.IBL_EWALL
 
 
+def test_graph_replay_any_phase_matches_eager_fp64():
+    """With no regularisation and no readout a step's launches repeat every 6
+    steps (AA parity x three patch buffers), so a chunk may start at any step:
+    one captured graph per phase.  Steps 7, 100, 13, 50, 49 in turn start
+    chunks at phases 1, 0 and 2; the result equals eager launches."""
+    fr = frames_ou(52, 3, 5e-3)
+    out = []
+    for graphs in (True, False):
+        g, _, t = _droplet_pair((24, 24, 24), 4.5, 2, 0.02, fr, 30, "fp64")
+        g.set_graphs(graphs)
+        for n in (7, 100, 13, 50, 49):
+            g.step(n)
+        g.sync()
+        out.append((g.mesh()[0], g.steps_done, g.step_paths(), g.status()))
+    (ra, na, pa, sa), (rb, nb, pb, sb) = out
+    assert na == nb == 219 and sa == sb == 0
+    # chunks of 48: 7 eager; 48 + 48 replayed from step 7, 4 eager; 13 eager;
+    # 48 from step 120, 2 eager; 48 from step 170, 1 eager
+    assert pa == (27, 192)
+    assert pb == (219, 0)
+    assert np.abs(ra - rb).max() < 1e-12
+
+
 def test_graph_replay_matches_eager_fp64():
     """Whole chunks replayed as a captured CUDA graph give the same result as
     eager launches (regularisation every 10 steps, a record every 20)."""
