@@ -91,17 +91,6 @@ def traffic_from_profiles(name):
 CHUNK_128 = 300  # graph chunk of the single-droplet workload: lcm(6, readout period 100)
 
 
-def warm_up_aligned(sim, warmup, chunk, steps):
-    """W warm-up steps; when the timed region holds whole graph chunks, then
-    enough more that it starts at a chunk boundary with the chunk graph
-    already captured and replayed once.  Returns the steps run."""
-    sim.step(warmup)
-    if steps >= chunk:
-        sim.step((-sim.steps_done) % chunk)
-        sim.step(chunk)
-    return sim.steps_done
-
-
 class ClockSampler:
     """nvidia-smi clock samples during the timed region."""
 
@@ -703,13 +692,18 @@ def run_ours(args):
     # steps or more); an odd stride samples both step parities (the AA
     # pattern's even and odd kernels differ)
     every = max(1, min(99, args.steps // 5)) | 1
-    sim.profile(True, mask=1, every=every)
-    warm = warm_up_aligned(sim, args.warmup, CHUNK_128, args.steps)
+    sim.step(args.warmup)
     sim.sync()
+    sim.profile(True, mask=1, every=every)  # clears the warm-up's marks (and its graphs)
+    # capture, without running them, the graphs the timed call replays: its
+    # whole chunks and the runs of steps around them (a user stepping in
+    # fixed increments reaches the same state after the first calls)
+    sim.prepare(args.steps)
+    sim.sync()
+    warm = sim.steps_done
     paths0 = sim.step_paths()
     clocks = ClockSampler(local)
     clocks.start()
-    sim.profile(True, mask=1, every=every)  # clears the marks of the warm-up, keeps the captures
     stream = torch.cuda.current_stream(dev)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)

@@ -233,11 +233,25 @@ int ibl_step_record(ibl_lb *lb);
 
 /* Graph replay (default on): ibl_step runs whole chunks of steps -- a
  * multiple of 6 and of the regularisation and readout periods, at least 32
- * -- as one captured CUDA graph launched on the bound stream, and the steps
- * before the first chunk boundary and after the last one eagerly.  The
- * chunk is captured on a private stream at the first use and again after
- * any schedule change.  enable = 0 launches every kernel eagerly. */
+ * -- as one captured CUDA graph launched on the bound stream.  The chunk is
+ * captured on a private stream at the first use and again after any
+ * schedule change.  The shorter runs before the first chunk boundary and
+ * after the last one (segments) run eagerly the first time a segment of
+ * that length starts at that position in the schedule period, and from its
+ * second occurrence on replay a graph of their own (up to 32 such graphs
+ * are kept, least recently used dropped first): stepping in fixed
+ * increments replays graphs throughout once each phase has come round
+ * twice.  enable = 0 launches every kernel eagerly. */
 int ibl_set_graphs(ibl_lb *lb, int enable);
+
+/* Captures, without running any step, the CUDA graphs that the next call
+ * ibl_step(lb, n) replays -- its whole chunks and the segments between them
+ * (runs of 2 steps or more) -- and uploads them to the device, so that the
+ * next ibl_step(lb, n) launches graphs only and pays no capture.  The
+ * capture runs on private streams; only the graphs' uploads are enqueued on
+ * the bound stream.  A no-op when graph replay is off.  IBL_EINVAL for n < 0, IBL_ECUDA for a failed
+ * capture. */
+int ibl_prepare_steps(ibl_lb *lb, long long n);
 
 /* Steps ibl_step has run eagerly and by graph replay since the lattice was
  * created (ibl_step_record and the adjoint's recomputations not counted). */

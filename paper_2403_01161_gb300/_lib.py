@@ -76,6 +76,7 @@ SIGNATURES = [
     ("ibl_save", ctypes.c_int, [_P, ctypes.c_char_p]),
     ("ibl_load", ctypes.c_int, [_P, ctypes.c_char_p]),
     ("ibl_step", ctypes.c_int, [_P, ctypes.c_longlong]),
+    ("ibl_prepare_steps", ctypes.c_int, [_P, ctypes.c_longlong]),
     ("ibl_step_record", ctypes.c_int, [_P]),
     ("ibl_set_graphs", ctypes.c_int, [_P, ctypes.c_int]),
     ("ibl_step_paths", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),

@@ -163,11 +163,26 @@ struct ibl_lb {
     Profiler prof;
     // CUDA-graph replay of whole chunks of steps
     bool graphs = true;
-    int chunk = 0;                       // steps per captured chunk (0 = none captured)
+    int chunk = 0;                       // chunk length of the schedule the graphs belong to (0 = none captured)
     // one graph per position in the schedule period when that period is the
     // bare 6 (AA parity x three patch buffers), else only slot 0
     static constexpr int kPhases = 6;
     cudaGraphExec_t gexec[kPhases] = {};
+    // graphs of the shorter runs of steps around whole chunks (segments),
+    // keyed by length and by the start's position in the schedule period;
+    // captured by ibl_prepare_steps, or at a segment's second occurrence
+    // (seen[] remembers the last kSeen segments run eagerly); the least
+    // recently used graph is dropped first
+    struct Segment {
+        long long phase = -1, len = 0, used = 0;
+        cudaGraphExec_t g = nullptr;
+    };
+    static constexpr int kSegments = 32, kSeen = 64;
+    static constexpr long long kMaxSegment = 2048;
+    Segment seg[kSegments];
+    long long seg_clock = 0;
+    long long seen[kSeen][2] = {};
+    int seen_next = 0;
     long long steps_eager = 0, steps_replayed = 0;  // counts of ibl_step's two paths
     cudaStream_t cap_stream = nullptr;   // private streams used only for capture
     cudaStream_t cap_helper = nullptr;
@@ -190,6 +205,8 @@ struct ibl_lb {
     {
         for (cudaGraphExec_t g : gexec)
             if (g) cudaGraphExecDestroy(g);
+        for (Segment &sg : seg)
+            if (sg.g) cudaGraphExecDestroy(sg.g);
         if (cap_stream) cudaStreamDestroy(cap_stream);
         if (cap_helper) cudaStreamDestroy(cap_helper);
         if (helper) cudaStreamDestroy(helper);
@@ -553,6 +570,11 @@ void drop_graph(ibl_lb *lb)
             cudaGraphExecDestroy(g);
             g = nullptr;
         }
+    for (ibl_lb::Segment &sg : lb->seg) {
+        if (sg.g) cudaGraphExecDestroy(sg.g);
+        sg = ibl_lb::Segment{};
+    }
+    for (auto &k : lb->seen) k[0] = k[1] = 0;
     lb->chunk = 0;
 }
 
@@ -657,6 +679,100 @@ int capture_chunk(ibl_lb *lb, int chunk, int slot)
     if (st == IBL_OK) lb->chunk = chunk;
     else drop_graph(lb);
     return st;
+}
+
+// A run of steps as ibl_step executes it: a whole chunk (graph slot `slot`)
+// or a segment of `len` steps (graph keyed by `phase`, else eager).
+struct Piece {
+    bool chunk;
+    int slot;
+    long long start, len, phase;
+};
+
+// Splits n steps from the current step into whole chunks -- at chunk
+// boundaries, or at any step when the schedule period is the bare 6 (one
+// graph per phase) -- and the segments between them (at most kMaxSegment
+// steps each).
+void plan_steps(const ibl_lb *lb, long long n, std::vector<Piece> &out)
+{
+    out.clear();
+    const int chunk = lb->graphs ? chunk_length(lb) : 0;
+    const long long period = schedule_period(lb);
+    const bool keyed = chunk > 0 && period <= ibl_lb::kPhases;
+    long long s = lb->host_step, done = 0;
+    while (done < n) {
+        if (chunk > 0 && n - done >= chunk && (keyed || s % chunk == 0)) {
+            out.push_back({true, keyed ? (int)(s % period) : 0, s, chunk, s % period});
+            s += chunk;
+            done += chunk;
+            continue;
+        }
+        long long len = n - done;
+        if (chunk > 0 && !keyed) {
+            const long long to_boundary = (chunk - s % chunk) % chunk;
+            if (n - done - to_boundary >= chunk) len = to_boundary;
+        }
+        len = std::min(len, ibl_lb::kMaxSegment);
+        out.push_back({false, 0, s, len, s % period});
+        s += len;
+        done += len;
+    }
+}
+
+ibl_lb::Segment *find_segment(ibl_lb *lb, long long phase, long long len)
+{
+    for (ibl_lb::Segment &sg : lb->seg)
+        if (sg.g && sg.phase == phase && sg.len == len) {
+            sg.used = ++lb->seg_clock;
+            return &sg;
+        }
+    return nullptr;
+}
+
+// Whether the segment (phase, len) ran eagerly before (since the graphs were
+// last dropped); records it if not.
+bool seen_before(ibl_lb *lb, long long phase, long long len)
+{
+    for (const auto &k : lb->seen)
+        if (k[1] == len && k[0] == phase) return true;
+    lb->seen[lb->seen_next][0] = phase;
+    lb->seen[lb->seen_next][1] = len;
+    lb->seen_next = (lb->seen_next + 1) % ibl_lb::kSeen;
+    return false;
+}
+
+// Captures the segment piece `pc` into the least recently used slot and
+// uploads it to the device (its first launch then costs no more than the
+// next ones).
+int capture_segment(ibl_lb *lb, const Piece &pc, ibl_lb::Segment **out)
+{
+    ibl_lb::Segment *slot = &lb->seg[0];
+    for (ibl_lb::Segment &sg : lb->seg) {
+        if (!sg.g) {
+            slot = &sg;
+            break;
+        }
+        if (sg.used < slot->used) slot = &sg;
+    }
+    if (slot->g) cudaGraphExecDestroy(slot->g);
+    *slot = ibl_lb::Segment{};
+    const long long saved = lb->host_step;
+    lb->host_step = pc.start;
+    const int st = capture_steps(lb, (int)pc.len, false, [](int, cudaStream_t, cudaStream_t) { return IBL_OK; },
+                                 &slot->g);
+    lb->host_step = saved;
+    if (st != IBL_OK) {
+        slot->g = nullptr;
+        return st;
+    }
+    const cudaError_t e = cudaGraphUpload(slot->g, lb->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "graph upload");
+    slot->phase = pc.phase;
+    slot->len = pc.len;
+    slot->used = ++lb->seg_clock;
+    lb->chunk = chunk_length(lb);  // the schedule the graphs belong to
+    *out = slot;
+    return IBL_OK;
 }
 
 }  // namespace
@@ -1271,15 +1387,14 @@ int ibl_step(ibl_lb *lb, long long n)
     if (e != cudaSuccess) return cuda_fail(e, "stream fork");
     bool forked = true;  // eager steps may use the helper stream
     const int chunk = lb->graphs ? chunk_length(lb) : 0;
-    // with the bare period of 6, a chunk may start at any step (one graph
-    // per phase); otherwise only at multiples of the chunk
-    const long long period = chunk > 0 ? schedule_period(lb) : 0;
-    const bool keyed = chunk > 0 && period <= ibl_lb::kPhases;
-    long long done = 0;
-    // whole chunks at chunk boundaries, eager steps elsewhere (consecutive
-    // eager steps pipeline across steps on the two streams, while a graph
-    // boundary drains them); a graph starts after all eager work
-    auto replay = [&](cudaGraphExec_t g, int len) -> int {
+    if (chunk > 0 && lb->chunk != chunk) drop_graph(lb);
+    std::vector<Piece> plan;
+    plan_steps(lb, n, plan);
+    // whole chunks and captured segments replay as graphs, other steps run
+    // eagerly (consecutive eager steps pipeline across steps on the two
+    // streams, while a graph boundary drains them); a graph starts after
+    // all eager work
+    auto replay = [&](cudaGraphExec_t g, long long len) -> int {
         if (forked) {
             e = join(sH, sL, lb->evJoin);
             if (e != cudaSuccess) return cuda_fail(e, "stream join");
@@ -1289,35 +1404,77 @@ int ibl_step(ibl_lb *lb, long long n)
         if (e != cudaSuccess) return cuda_fail(e, "graph launch");
         lb->host_step += len;
         lb->steps_replayed += len;
-        done += len;
         return IBL_OK;
     };
-    while (done < n) {
-        if (chunk > 0 && n - done >= chunk && (keyed || lb->host_step % chunk == 0)) {
-            const int slot = keyed ? (int)(lb->host_step % period) : 0;
-            if (lb->chunk != chunk) drop_graph(lb);
-            if (!lb->gexec[slot]) {
-                st = capture_chunk(lb, chunk, slot);
+    for (const Piece &pc : plan) {
+        if (pc.chunk) {
+            if (!lb->gexec[pc.slot]) {
+                st = capture_chunk(lb, chunk, pc.slot);
                 if (st != IBL_OK) return st;
             }
-            st = replay(lb->gexec[slot], chunk);
+            st = replay(lb->gexec[pc.slot], pc.len);
             if (st != IBL_OK) return st;
             continue;
         }
-        if (!forked) {
-            e = join(sL, sH, lb->evFork);
-            if (e != cudaSuccess) return cuda_fail(e, "stream fork");
-            forked = true;
+        if (lb->graphs && pc.len >= 2) {
+            // a segment met for the second time is captured (stepping in
+            // fixed increments then replays graphs throughout once every
+            // phase has come round twice)
+            ibl_lb::Segment *sg = find_segment(lb, pc.phase, pc.len);
+            if (!sg && seen_before(lb, pc.phase, pc.len)) {
+                st = capture_segment(lb, pc, &sg);
+                if (st != IBL_OK) return st;
+            }
+            if (sg) {
+                st = replay(sg->g, pc.len);
+                if (st != IBL_OK) return st;
+                continue;
+            }
         }
-        st = one_step(lb, false, sL, sH);
-        if (st != IBL_OK) return st;
-        ++lb->steps_eager;
-        ++done;
+        for (long long k = 0; k < pc.len; ++k) {
+            if (!forked) {
+                e = join(sL, sH, lb->evFork);
+                if (e != cudaSuccess) return cuda_fail(e, "stream fork");
+                forked = true;
+            }
+            st = one_step(lb, false, sL, sH);
+            if (st != IBL_OK) return st;
+            ++lb->steps_eager;
+        }
     }
     // the bound stream resumes after all helper-stream work
     if (forked) {
         e = join(sH, sL, lb->evJoin);
         if (e != cudaSuccess) return cuda_fail(e, "stream join");
+    }
+    return IBL_OK;
+}
+
+int ibl_prepare_steps(ibl_lb *lb, long long n)
+{
+    TraceRange trace_("ibl_prepare_steps");
+    if (!lb || n < 0) return fail(IBL_EINVAL, "bad step request");
+    if (!lb->graphs || n == 0) return IBL_OK;
+    const int chunk = chunk_length(lb);
+    if (chunk > 0 && lb->chunk != chunk) drop_graph(lb);
+    std::vector<Piece> plan;
+    plan_steps(lb, n, plan);
+    const long long saved = lb->host_step;
+    int st = IBL_OK;
+    for (const Piece &pc : plan) {
+        if (pc.chunk && !lb->gexec[pc.slot]) {
+            lb->host_step = pc.start;
+            st = capture_chunk(lb, chunk, pc.slot);
+            lb->host_step = saved;
+            if (st == IBL_OK) {
+                const cudaError_t e = cudaGraphUpload(lb->gexec[pc.slot], lb->stream);
+                if (e != cudaSuccess) st = cuda_fail(e, "graph upload");
+            }
+        } else if (!pc.chunk && pc.len >= 2 && !find_segment(lb, pc.phase, pc.len)) {
+            ibl_lb::Segment *sg = nullptr;
+            st = capture_segment(lb, pc, &sg);
+        }
+        if (st != IBL_OK) return st;
     }
     return IBL_OK;
 }

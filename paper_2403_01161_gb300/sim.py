@@ -181,6 +181,10 @@ class Sim:
     def step(self, n: int = 1):
         L.check(self.lib.ibl_step(self.h, int(n)))
 
+    def prepare(self, n: int):
+        """Capture (without running) the graphs the next step(n) replays."""
+        L.check(self.lib.ibl_prepare_steps(self.h, int(n)))
+
     def set_graphs(self, enable: bool):
         """Replay whole chunks of steps as a captured CUDA graph (default on)."""
         L.check(self.lib.ibl_set_graphs(self.h, 1 if enable else 0))

@@ -191,6 +191,45 @@ def test_graph_replay_any_phase_matches_eager_fp64():
     assert np.abs(ra - rb).max() < 1e-12
 
 
+def test_segment_graphs_match_eager_fp64():
+    """Runs shorter than a chunk replay graphs of their own: prepare(n)
+    captures the graphs of the next step(n) without running a step, and a
+    segment met a second time is captured on the spot.  With a record every
+    20 steps and regularisation every 10 (chunk 60), steps of 25 from step 3
+    start segments at phases 3, 28, 53, 18, 43, 8, ...; the trajectory, the
+    shape records and the step count equal eager launches."""
+    fr = frames_ou(53, 3, 5e-3)
+    out = []
+    for graphs in (True, False):
+        g, _, t = _droplet_pair((24, 24, 24), 4.5, 2, 0.02, fr, 30, "fp64")
+        g.set_graphs(graphs)
+        g.set_regularization(0.1, 0.51, 0.01, 100, 10, True)
+        g.set_readout(20)
+        g.step(3)
+        g.sync()
+        p0 = g.step_paths()
+        g.prepare(25)
+        g.sync()
+        assert g.steps_done == 3 and g.step_paths() == p0  # nothing ran
+        g.step(25)  # replays the prepared segment graph
+        p1 = g.step_paths()
+        for _ in range(13):  # phases 28, 53, 18, 43, 8, 33, 58, 23, 48, 13, 38, 3, 28
+            g.step(25)
+        g.sync()
+        out.append((g.mesh()[0], g.series(), g.steps_done, p0, p1, g.step_paths(), g.status()))
+    (ra, sa, na, a0, a1, a2, sta), (rb, sb, nb, b0, b1, b2, stb) = out
+    assert na == nb == 3 + 14 * 25 and sta == stb == 0
+    assert a1[1] - a0[1] == 25 and a1[0] == a0[0]
+    # phases repeat every 12 calls (60 / gcd(25, 60)): the call at phase 28
+    # comes round again at the last call and is captured then; the call at
+    # phase 3 follows the prepared one and replays its graph
+    assert a2[1] - a1[1] == 2 * 25
+    assert b2 == (3 + 14 * 25, 0)
+    assert np.abs(ra - rb).max() < 1e-12
+    assert [x["step"] for x in sa] == [x["step"] for x in sb]
+    assert max(abs(x["D"] - y["D"]) for x, y in zip(sa, sb)) < 1e-12
+
+
 def test_graph_replay_matches_eager_fp64():
     """Whole chunks replayed as a captured CUDA graph give the same result as
     eager launches (regularisation every 10 steps, a record every 20)."""
