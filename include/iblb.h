@@ -57,11 +57,13 @@ extern "C" {
 #define IBL_EUNSTABLE (-4) /* NaN density or |u| > 0.3 on some node */
 #define IBL_ENOCONV (-5)   /* mesh regularisation reached max_iter */
 #define IBL_EWALL (-6)     /* a droplet node's 4x4x4 stencil reached a wet boundary node */
+#define IBL_ETIMEOUT (-7)  /* a kernel gave up waiting for its staged copies (never expected) */
 
 /* sticky device error bits, as in ibl_observables.err */
 #define IBL_ERRBIT_UNSTABLE 1
 #define IBL_ERRBIT_NOCONV 2
 #define IBL_ERRBIT_WALL 4
+#define IBL_ERRBIT_TIMEOUT 8
 
 enum { IBL_BC_ZOU_HE = 0, IBL_BC_PERIODIC = 1 };
 /* Edge/corner rule, Eqs. (ZH_edges), (zh-buried-links-edges),
@@ -252,6 +254,19 @@ int ibl_set_graphs(ibl_lb *lb, int enable);
  * the bound stream.  A no-op when graph replay is off.  IBL_EINVAL for n < 0, IBL_ECUDA for a failed
  * capture. */
 int ibl_prepare_steps(ibl_lb *lb, long long n);
+
+/* Kernel of the lattice update outside the droplet patch (and of the whole
+ * box without a droplet), Eqs. (LBMEQ)-(density_velocity_LB) with the
+ * boundary rebuild of Sec. 3.2: kind 0 = one thread per node with direct
+ * loads; kind 1..4 = a pipeline of persistent blocks that stage each tile's
+ * populations into shared memory with bulk asynchronous copies, in one of
+ * four launch shapes.  Every kind computes the same update bit for bit.  The
+ * staged kinds need FP32 populations and Zou-He walls on every axis
+ * (IBL_EINVAL otherwise); a step that stores the fields (ibl_step_record)
+ * uses kind 0.  Synchronises the bound stream and drops captured graphs.
+ * ibl_outside_update reads the kind in use. */
+int ibl_set_outside_update(ibl_lb *lb, int kind);
+int ibl_outside_update(const ibl_lb *lb, int *kind);
 
 /* Steps ibl_step has run eagerly and by graph replay since the lattice was
  * created (ibl_step_record and the adjoint's recomputations not counted). */

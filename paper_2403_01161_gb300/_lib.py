@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libiblb.so")
 
 IBL_ABI_VERSION = 1
-IBL_OK, IBL_EINVAL, IBL_ENOMEM, IBL_ECUDA, IBL_EUNSTABLE, IBL_ENOCONV, IBL_EWALL = 0, -1, -2, -3, -4, -5, -6
+IBL_OK, IBL_EINVAL, IBL_ENOMEM, IBL_ECUDA, IBL_EUNSTABLE, IBL_ENOCONV, IBL_EWALL, IBL_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6, -7
 BC_ZOU_HE, BC_PERIODIC = 0, 1
 EDGE_COUNTER_SLIP, EDGE_PAPER_LITERAL = 0, 1
 FP32_DEV, FP64 = 0, 1
@@ -77,6 +77,8 @@ SIGNATURES = [
     ("ibl_load", ctypes.c_int, [_P, ctypes.c_char_p]),
     ("ibl_step", ctypes.c_int, [_P, ctypes.c_longlong]),
     ("ibl_prepare_steps", ctypes.c_int, [_P, ctypes.c_longlong]),
+    ("ibl_set_outside_update", ctypes.c_int, [_P, ctypes.c_int]),
+    ("ibl_outside_update", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     ("ibl_step_record", ctypes.c_int, [_P]),
     ("ibl_set_graphs", ctypes.c_int, [_P, ctypes.c_int]),
     ("ibl_step_paths", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),

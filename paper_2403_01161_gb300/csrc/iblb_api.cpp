@@ -250,6 +250,8 @@ int lb_status_from_device(ibl_lb *lb)
     if (c.err & IBL_ERRBIT_WALL)
         return fail(IBL_EWALL, "a droplet node's stencil reached a wet boundary node (or its position is invalid)");
     if (c.err & IBL_ERRBIT_NOCONV) return fail(IBL_ENOCONV, "mesh regularisation did not converge within max_iter");
+    if (c.err & IBL_ERRBIT_TIMEOUT)
+        return fail(IBL_ETIMEOUT, "the staged lattice update gave up waiting for its copies into shared memory");
     return IBL_OK;
 }
 
@@ -1172,6 +1174,7 @@ int ibl_lb_create(const ibl_lb_params *p, const double *A_frames, int n_frames, 
     v.n_frames = n_frames;
     v.n_hold = steps_per_frame;
     v.ctl = reinterpret_cast<Ctl *>(lb->ws + L.ctl);
+    v.staged = 0;
     Ctl c;
     std::memset(&c, 0, sizeof c);
     for (int b = 0; b < 3; ++b)
@@ -1476,6 +1479,27 @@ int ibl_prepare_steps(ibl_lb *lb, long long n)
         }
         if (st != IBL_OK) return st;
     }
+    return IBL_OK;
+}
+
+int ibl_set_outside_update(ibl_lb *lb, int kind)
+{
+    if (!lb) return fail(IBL_EINVAL, "null lattice");
+    if (kind < 0 || kind > iblb::kStagedShapes) return fail(IBL_EINVAL, "outside-update kind out of range");
+    if (kind > 0 && !iblb::staged_ok(lb->v))
+        return fail(IBL_EINVAL, "the staged outside update needs FP32 populations and Zou-He walls on every axis");
+    cudaStreamSynchronize(lb->stream);
+    const cudaError_t e = iblb::staged_prepare(kind);
+    if (e != cudaSuccess) return cuda_fail(e, "staged kernel attributes");
+    drop_graph(lb);  // captured chunks hold the lattice view by value
+    lb->v.staged = kind;
+    return IBL_OK;
+}
+
+int ibl_outside_update(const ibl_lb *lb, int *kind)
+{
+    if (!lb || !kind) return fail(IBL_EINVAL, "null argument");
+    *kind = lb->v.staged;
     return IBL_OK;
 }
 

@@ -488,4 +488,63 @@ static inline cudaError_t launch_p(void (*k)(KArgs...), dim3 g, dim3 b, cudaStre
     return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
 }
 
+// ---- bulk asynchronous copies into shared memory (sm_90 and later) -------
+// A bulk copy (cp.async.bulk) moves a contiguous run of global memory into
+// shared memory without occupying registers and signals completion on an
+// mbarrier in shared memory by the bytes it delivered (complete_tx).  Both
+// addresses and the size must be multiples of 16 bytes.
+__device__ __forceinline__ unsigned smem_addr(const void *p)
+{
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+// Makes barrier initialisations visible to the asynchronous proxy (the copy
+// engine) before any copy signals them.
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// One arrival that also announces `bytes` of copies to be completed in the
+// barrier's current phase.
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+// Waits until the phase with parity `parity` of the barrier has completed;
+// gives up after `limit` polls (each poll may suspend the thread for a
+// while) and returns false then.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, unsigned limit)
+{
+    const unsigned a = smem_addr(bar);
+    for (unsigned k = 0; k < limit; ++k) {
+        unsigned done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
 }  // namespace iblb

@@ -58,6 +58,7 @@ struct LbView {
     float omega_in_f;
     unsigned int *ind;  // [ceil(nodes / 4)] inside flags, one byte per node (set by the indicator kernel, cleared by the patch update)
     Ctl *ctl;
+    int staged;         // outside / whole-box update: 0 one thread per node with direct loads (k_lattice), v > 0 the staged pipeline's launch shape v (k_lattice_staged)
 };
 
 struct MeshView {
@@ -154,6 +155,13 @@ constexpr int kObsBlocksMax = 304;
 
 cudaError_t launch_init(const LbView &L, cudaStream_t s);
 cudaError_t launch_lattice(const LbView &L, bool odd, bool record, int mode, int pbuf, cudaStream_t s);
+// Whether the staged outside update can run on this lattice (FP32, Zou-He
+// walls on every axis, 16-byte aligned population arrays).
+bool staged_ok(const LbView &L);
+// Sets the shared-memory attributes of the staged kernels of launch shape
+// `kind` on the current device (outside any stream capture).
+cudaError_t staged_prepare(int kind);
+constexpr int kStagedShapes = 4;
 cudaError_t launch_near(const LbView &L, bool odd, bool record, int pbuf, cudaStream_t s, int prio = 0);
 enum { LAUNCH_FULL = 0, LAUNCH_FAR = 1 };
 cudaError_t launch_convert_frames(const LbView &L, int k0, int k1, cudaStream_t s);

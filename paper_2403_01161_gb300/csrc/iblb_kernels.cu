@@ -21,7 +21,9 @@
 
 #include <cmath>
 #include <cstdint>
+#include <algorithm>
 #include <mutex>
+#include <set>
 #include <type_traits>
 #include <utility>
 
@@ -197,6 +199,185 @@ __device__ __forceinline__ void bc_dispatch(T (&f)[19], const T (&uw)[3], int ru
 // and written by one node only within a step.
 enum { LAT_FULL = 0, LAT_FAR = 1, LAT_NEAR = 2 };
 
+// 3 w_i, the weight of the odd (momentum) parts of the equilibrium and of
+// the Guo source.  The exact values are 1/6 (|c_i|^2 = 1) and 1/12 (|c_i|^2
+// = 2), and sum_i c_ia c_ia 3 w_i = 2/6 + 8/12 = 1 carries the momentum
+// through the collision.  Rounded to nearest in FP32 both come out 2^-25
+// relatively high, so that every collision would multiply the momentum by
+// 1 + 3.0e-8 -- a bias that accumulates over the thousands of steps a
+// velocity perturbation lives (L^2 / nu).  In FP32 1/6 is therefore rounded
+// down instead (0x3E2AAAAA, 2^-24 relatively low), which makes
+// 2 (3 w_1) + 8 (3 w_2) equal to 1 exactly; what remains of each product's
+// error is its own rounding, without a common sign.
+template <typename T, int i>
+__device__ __forceinline__ T odd_weight()
+{
+    if constexpr (sizeof(T) == 4) return __int_as_float(c2(i) == 1 ? 0x3E2AAAAA : 0x3DAAAAAB);
+    else return T(3.0 * wgt(i));
+}
+
+// The part of a node update after its 19 incoming populations g are in
+// registers: boundary rebuild (sx, sy, sz: -1 / 0 / +1 where the node lies on
+// a wall of that axis), patch force, moments, BGK + Guo, stores (AA pattern:
+// even step own slots opp(i), odd step slot i at x + c_i), velocity record.
+// Returns whether the node is unstable.
+template <typename T, bool ODD, bool REC, int MODE, bool PER, class P = L2Keep>
+__device__ __forceinline__ bool lattice_finish(const LbView &L, T (&g)[19], const int x, const int y, const int z,
+                                               const int node, const bool in_patch, const int pbuf, const int sx,
+                                               const int sy, const int sz)
+{
+    const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
+    const int nxy = nx * ny;
+    bool bad = false;
+    {
+        T *__restrict__ f = static_cast<T *>(L.f);
+        struct NoKeep {};
+        [[maybe_unused]] const std::conditional_t<MODE == LAT_NEAR, P, NoKeep> K;
+        const int qs = (int)L.qs;
+        const bool px = PER && L.bc[0] == IBL_BC_PERIODIC, py = PER && L.bc[1] == IBL_BC_PERIODIC,
+                   pz = PER && L.bc[2] == IBL_BC_PERIODIC;
+        if (sx | sy | sz) {
+            // Eq. (velo_facce_cubo_da_gradiente) in the storage precision,
+            // about the box centre or, with re-centring, about the droplet's
+            // centre of mass at the start of the step (the offset in FP64)
+            const T *A = static_cast<const T *>(L.frames_t) + 9 * L.ctl->frame_par[ODD ? 1 : 0];
+            T lx, ly, lz;
+            if (L.recentre) {
+                const double *c = L.ctl->centre[pbuf];
+                lx = T(double(x) - c[0]);
+                ly = T(double(y) - c[1]);
+                lz = T(double(z) - c[2]);
+            } else {
+                lx = T(x) - T(0.5) * T(nx - 1);
+                ly = T(y) - T(0.5) * T(ny - 1);
+                lz = T(z) - T(0.5) * T(nz - 1);
+            }
+            const T uw[3] = {A[0] * lx + A[1] * ly + A[2] * lz, A[3] * lx + A[4] * ly + A[5] * lz,
+                             A[6] * lx + A[7] * ly + A[8] * lz};
+            bc_dispatch<T>(g, uw, L.rule, (sx + 1) + 3 * (sy + 1) + 9 * (sz + 1));
+        }
+
+        // droplet patch: read the spread force (and clear it), store u below;
+        // both fields hold a 4-wide record (x, y, z, 0) per node
+        T Fx = T(0), Fy = T(0), Fz = T(0);
+        T *__restrict__ force = static_cast<T *>(L.force);
+        if constexpr (MODE == LAT_NEAR) {
+            K.ld3(force + 4 * node, Fx, Fy, Fz);
+            K.st3(force + 4 * node, T(0), T(0), T(0));
+        } else if (in_patch) {
+            rec_ld3(force + 4 * node, Fx, Fy, Fz);
+            rec_st3(force + 4 * node, T(0), T(0), T(0));
+        }
+
+        T drho = T(0), jx = T(0), jy = T(0), jz = T(0);
+        sfor<19>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            drho += g[i];
+            if constexpr (cxf(i) != 0) jx += T(cxf(i)) * g[i];
+            if constexpr (cyf(i) != 0) jy += T(cyf(i)) * g[i];
+            if constexpr (czf(i) != 0) jz += T(czf(i)) * g[i];
+        });
+        const T rho = T(1) + drho;
+        const T ir = T(1) / rho;
+        // rho u = j + F/2 (Eq. (density_velocity_LB)); the odd (momentum)
+        // parts of the equilibrium are formed from it directly
+        const T mx = jx + T(0.5) * Fx, my = jy + T(0.5) * Fy, mz = jz + T(0.5) * Fz;
+        const T ux = mx * ir, uy = my * ir, uz = mz * ir;
+        const T uu = ux * ux + uy * uy + uz * uz;
+        bad = !(uu <= T(0.09)) || !(drho == drho);
+        T om = sizeof(T) == 4 ? T(L.omega_f) : T(L.omega);
+        if constexpr (MODE == LAT_NEAR) {
+            // viscosity ratio: relaxation of the inside nodes (flags read and cleared)
+            if (L.visc) {
+                unsigned char *flag = reinterpret_cast<unsigned char *>(L.ind) + node;
+                if (*flag) om = sizeof(T) == 4 ? T(L.omega_in_f) : T(L.omega_in);
+                *flag = 0;
+            }
+        }
+        const T fpre = T(1) - T(0.5) * om;
+        const T uF = ux * Fx + uy * Fy + uz * Fz;
+        const T dmr = drho - rho * (T(1.5) * uu);  // drho - (3/2) rho u.u
+        {
+            constexpr double w0 = wgt(0);
+            const T geq = T(w0) * dmr;
+            const T src = fpre * T(w0) * (T(-3) * uF);
+            g[0] = g[0] + om * (geq - g[0]) + src;
+        }
+        sfor<9>([&](auto I) {
+            constexpr int i = decltype(I)::value + 1;
+            constexpr int j = opp(i);
+            T cp = T(0), cF = T(0);  // c_i . rho u, c_i . F
+            if constexpr (cxf(i) != 0) { cp += T(cxf(i)) * mx; cF += T(cxf(i)) * Fx; }
+            if constexpr (cyf(i) != 0) { cp += T(cyf(i)) * my; cF += T(cyf(i)) * Fy; }
+            if constexpr (czf(i) != 0) { cp += T(czf(i)) * mz; cF += T(czf(i)) * Fz; }
+            const T cu = cp * ir;
+            constexpr double w = wgt(i);
+            const T w3 = odd_weight<T, i>();
+            const T even_eq = T(w) * (T(4.5) * cp * cu + dmr);
+            const T odd_eq = w3 * cp;
+            const T even_src = fpre * T(w) * (T(9) * cu * cF - T(3) * uF);
+            const T odd_src = fpre * w3 * cF;
+            g[i] = g[i] + om * (even_eq + odd_eq - g[i]) + (even_src + odd_src);
+            g[j] = g[j] + om * (even_eq - odd_eq - g[j]) + (even_src - odd_src);
+        });
+
+        if constexpr (!ODD) {
+            sfor<19>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                if constexpr (MODE == LAT_NEAR) K.st(f + opp(i) * qs + node, g[i]);
+                else f[opp(i) * qs + node] = g[i];
+            });
+        } else {
+            // destination x + c_i, slot i.  The node coordinates pass through
+            // an opaque move, so the neighbour offsets are recomputed here
+            // instead of being held in registers across the collision (which
+            // made this kernel spill).
+            int xs = x, ys = y, zs = z;
+            asm volatile("mov.b32 %0, %0;" : "+r"(xs));
+            asm volatile("mov.b32 %0, %0;" : "+r"(ys));
+            asm volatile("mov.b32 %0, %0;" : "+r"(zs));
+            const int nodes_ = xs + nx * ys + nxy * zs;
+            int sxm = -1, sxp = 1, sym = -nx, syp = nx, szm = -nxy, szp = nxy, smiss = 0;
+            if (xs == 0) { if (px) sxm = nx - 1; else smiss |= 1; }
+            if (xs == nx - 1) { if (px) sxp = -(nx - 1); else smiss |= 2; }
+            if (ys == 0) { if (py) sym = (ny - 1) * nx; else smiss |= 4; }
+            if (ys == ny - 1) { if (py) syp = -(ny - 1) * nx; else smiss |= 8; }
+            if (zs == 0) { if (pz) szm = (nz - 1) * nxy; else smiss |= 16; }
+            if (zs == nz - 1) { if (pz) szp = -(nz - 1) * nxy; else smiss |= 32; }
+            sfor<19>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                constexpr int cx = cxf(i), cy = cyf(i), cz = czf(i);
+                constexpr int need = (cx > 0 ? 2 : (cx < 0 ? 1 : 0)) | (cy > 0 ? 8 : (cy < 0 ? 4 : 0)) |
+                                     (cz > 0 ? 32 : (cz < 0 ? 16 : 0));
+                const int off = (cx > 0 ? sxp : (cx < 0 ? sxm : 0)) + (cy > 0 ? syp : (cy < 0 ? sym : 0)) +
+                                (cz > 0 ? szp : (cz < 0 ? szm : 0));
+                if ((smiss & need) == 0) {
+                    if constexpr (MODE == LAT_NEAR) K.st(f + i * qs + nodes_ + off, g[i]);
+                    else f[i * qs + nodes_ + off] = g[i];
+                }
+            });
+        }
+        if (in_patch) {
+            T *__restrict__ vel = static_cast<T *>(L.vel);
+            if constexpr (MODE == LAT_NEAR) K.st3(vel + 4 * node, ux, uy, uz);
+            else rec_st3(vel + 4 * node, ux, uy, uz);
+        }
+        if constexpr (REC) {
+            const int nodes = L.nodes;
+            T *__restrict__ rec = static_cast<T *>(L.rec);
+            rec[node] = drho;
+            rec[nodes + node] = ux;
+            rec[2 * nodes + node] = uy;
+            rec[3 * nodes + node] = uz;
+            rec[4 * nodes + node] = Fx;
+            rec[5 * nodes + node] = Fy;
+            rec[6 * nodes + node] = Fz;
+        }
+    }
+    return bad;
+}
+
+// One node update with its loads from global memory.
 // PER: some axis may be periodic (false: every axis has Zou-He walls, so
 // the neighbour offsets are fixed and only the boundary tests remain).
 // P: L2 policy of the patch nodes' accesses (LAT_NEAR).
@@ -204,7 +385,6 @@ template <typename T, bool ODD, bool REC, int MODE, bool PER, class P = L2Keep>
 __device__ __forceinline__ bool lattice_node(const LbView &L, const int x, const int y, const int z, const int pbuf)
 {
     const int nx = L.n[0], ny = L.n[1], nz = L.n[2];
-    bool bad = false;
     // the patch of this step lives in buffer pbuf (step % 3)
     bool in_patch = (MODE == LAT_NEAR);
     if constexpr (MODE != LAT_NEAR) in_patch = node_in_patch(L, L.ctl, pbuf, x, y, z);
@@ -272,140 +452,8 @@ __device__ __forceinline__ bool lattice_node(const LbView &L, const int x, const
             });
         }
 
-        if (sx | sy | sz) {
-            // Eq. (velo_facce_cubo_da_gradiente) in the storage precision,
-            // about the box centre or, with re-centring, about the droplet's
-            // centre of mass at the start of the step (the offset in FP64)
-            const T *A = static_cast<const T *>(L.frames_t) + 9 * L.ctl->frame_par[ODD ? 1 : 0];
-            T lx, ly, lz;
-            if (L.recentre) {
-                const double *c = L.ctl->centre[pbuf];
-                lx = T(double(x) - c[0]);
-                ly = T(double(y) - c[1]);
-                lz = T(double(z) - c[2]);
-            } else {
-                lx = T(x) - T(0.5) * T(nx - 1);
-                ly = T(y) - T(0.5) * T(ny - 1);
-                lz = T(z) - T(0.5) * T(nz - 1);
-            }
-            const T uw[3] = {A[0] * lx + A[1] * ly + A[2] * lz, A[3] * lx + A[4] * ly + A[5] * lz,
-                             A[6] * lx + A[7] * ly + A[8] * lz};
-            bc_dispatch<T>(g, uw, L.rule, (sx + 1) + 3 * (sy + 1) + 9 * (sz + 1));
-        }
-
-        // droplet patch: read the spread force (and clear it), store u below;
-        // both fields hold a 4-wide record (x, y, z, 0) per node
-        T Fx = T(0), Fy = T(0), Fz = T(0);
-        T *__restrict__ force = static_cast<T *>(L.force);
-        if constexpr (MODE == LAT_NEAR) {
-            K.ld3(force + 4 * node, Fx, Fy, Fz);
-            K.st3(force + 4 * node, T(0), T(0), T(0));
-        } else if (in_patch) {
-            rec_ld3(force + 4 * node, Fx, Fy, Fz);
-            rec_st3(force + 4 * node, T(0), T(0), T(0));
-        }
-
-        T drho = T(0), jx = T(0), jy = T(0), jz = T(0);
-        sfor<19>([&](auto I) {
-            constexpr int i = decltype(I)::value;
-            drho += g[i];
-            if constexpr (cxf(i) != 0) jx += T(cxf(i)) * g[i];
-            if constexpr (cyf(i) != 0) jy += T(cyf(i)) * g[i];
-            if constexpr (czf(i) != 0) jz += T(czf(i)) * g[i];
-        });
-        const T rho = T(1) + drho;
-        const T ir = T(1) / rho;
-        const T ux = (jx + T(0.5) * Fx) * ir, uy = (jy + T(0.5) * Fy) * ir, uz = (jz + T(0.5) * Fz) * ir;
-        const T uu = ux * ux + uy * uy + uz * uz;
-        bad = !(uu <= T(0.09)) || !(drho == drho);
-        T om = sizeof(T) == 4 ? T(L.omega_f) : T(L.omega);
-        if constexpr (MODE == LAT_NEAR) {
-            // viscosity ratio: relaxation of the inside nodes (flags read and cleared)
-            if (L.visc) {
-                unsigned char *flag = reinterpret_cast<unsigned char *>(L.ind) + node;
-                if (*flag) om = sizeof(T) == 4 ? T(L.omega_in_f) : T(L.omega_in);
-                *flag = 0;
-            }
-        }
-        const T fpre = T(1) - T(0.5) * om;
-        const T uF = ux * Fx + uy * Fy + uz * Fz;
-        const T base = T(1.5) * uu;
-        {
-            constexpr double w0 = wgt(0);
-            const T geq = T(w0) * (drho - rho * base);
-            const T src = fpre * T(w0) * (T(-3) * uF);
-            g[0] = g[0] + om * (geq - g[0]) + src;
-        }
-        sfor<9>([&](auto I) {
-            constexpr int i = decltype(I)::value + 1;
-            constexpr int j = opp(i);
-            T cu = T(0), cF = T(0);
-            if constexpr (cxf(i) != 0) { cu += T(cxf(i)) * ux; cF += T(cxf(i)) * Fx; }
-            if constexpr (cyf(i) != 0) { cu += T(cyf(i)) * uy; cF += T(cyf(i)) * Fy; }
-            if constexpr (czf(i) != 0) { cu += T(czf(i)) * uz; cF += T(czf(i)) * Fz; }
-            constexpr double w = wgt(i);
-            const T even_eq = T(w) * (drho + rho * (T(4.5) * cu * cu - base));
-            const T odd_eq = T(3.0 * w) * rho * cu;
-            const T even_src = fpre * T(w) * (T(9) * cu * cF - T(3) * uF);
-            const T odd_src = fpre * T(3.0 * w) * cF;
-            g[i] = g[i] + om * (even_eq + odd_eq - g[i]) + (even_src + odd_src);
-            g[j] = g[j] + om * (even_eq - odd_eq - g[j]) + (even_src - odd_src);
-        });
-
-        if constexpr (!ODD) {
-            sfor<19>([&](auto I) {
-                constexpr int i = decltype(I)::value;
-                if constexpr (MODE == LAT_NEAR) K.st(f + opp(i) * qs + node, g[i]);
-                else f[opp(i) * qs + node] = g[i];
-            });
-        } else {
-            // destination x + c_i, slot i.  The node coordinates pass through
-            // an opaque move, so the neighbour offsets are recomputed here
-            // instead of being held in registers across the collision (which
-            // made this kernel spill).
-            int xs = x, ys = y, zs = z;
-            asm volatile("mov.b32 %0, %0;" : "+r"(xs));
-            asm volatile("mov.b32 %0, %0;" : "+r"(ys));
-            asm volatile("mov.b32 %0, %0;" : "+r"(zs));
-            const int nodes_ = xs + nx * ys + nxy * zs;
-            int sxm = -1, sxp = 1, sym = -nx, syp = nx, szm = -nxy, szp = nxy, smiss = 0;
-            if (xs == 0) { if (px) sxm = nx - 1; else smiss |= 1; }
-            if (xs == nx - 1) { if (px) sxp = -(nx - 1); else smiss |= 2; }
-            if (ys == 0) { if (py) sym = (ny - 1) * nx; else smiss |= 4; }
-            if (ys == ny - 1) { if (py) syp = -(ny - 1) * nx; else smiss |= 8; }
-            if (zs == 0) { if (pz) szm = (nz - 1) * nxy; else smiss |= 16; }
-            if (zs == nz - 1) { if (pz) szp = -(nz - 1) * nxy; else smiss |= 32; }
-            sfor<19>([&](auto I) {
-                constexpr int i = decltype(I)::value;
-                constexpr int cx = cxf(i), cy = cyf(i), cz = czf(i);
-                constexpr int need = (cx > 0 ? 2 : (cx < 0 ? 1 : 0)) | (cy > 0 ? 8 : (cy < 0 ? 4 : 0)) |
-                                     (cz > 0 ? 32 : (cz < 0 ? 16 : 0));
-                const int off = (cx > 0 ? sxp : (cx < 0 ? sxm : 0)) + (cy > 0 ? syp : (cy < 0 ? sym : 0)) +
-                                (cz > 0 ? szp : (cz < 0 ? szm : 0));
-                if ((smiss & need) == 0) {
-                    if constexpr (MODE == LAT_NEAR) K.st(f + i * qs + nodes_ + off, g[i]);
-                    else f[i * qs + nodes_ + off] = g[i];
-                }
-            });
-        }
-        if (in_patch) {
-            T *__restrict__ vel = static_cast<T *>(L.vel);
-            if constexpr (MODE == LAT_NEAR) K.st3(vel + 4 * node, ux, uy, uz);
-            else rec_st3(vel + 4 * node, ux, uy, uz);
-        }
-        if constexpr (REC) {
-            const int nodes = L.nodes;
-            T *__restrict__ rec = static_cast<T *>(L.rec);
-            rec[node] = drho;
-            rec[nodes + node] = ux;
-            rec[2 * nodes + node] = uy;
-            rec[3 * nodes + node] = uz;
-            rec[4 * nodes + node] = Fx;
-            rec[5 * nodes + node] = Fy;
-            rec[6 * nodes + node] = Fz;
-        }
+        return lattice_finish<T, ODD, REC, MODE, PER, P>(L, g, x, y, z, node, in_patch, pbuf, sx, sy, sz);
     }
-    return bad;
 }
 
 // Closes step t: the step counter becomes t + 1 and the frame of step t + 1
@@ -445,6 +493,164 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 4) k_lattice(LbView 
     // sticky instability flag, one atomic per warp at most
     const unsigned m = __ballot_sync(0xffffffffu, bad);
     if (m != 0u && (threadIdx.x & 31) == 0) atomicOr(&L.ctl->err, IBL_ERRBIT_UNSTABLE);
+}
+
+// Outside update (FAR) or whole-box update (FULL) through a shared-memory
+// pipeline, for FP32 populations in a box with Zou-He walls on every axis.
+// The one-thread-per-node kernel above holds its 19 loads in registers, so
+// the bytes it keeps in flight are capped by the resident threads (8 blocks
+// of 128 at 64 registers fill the register file), and a droplet-kernel
+// block that takes a slot on an SM cuts that SM's share of the stream.
+// Here each block is persistent (B per SM) and walks tiles of NT
+// consecutive nodes of the flattened box; warp 0 stages the 19 source
+// runs of a tile (one lane per run) with bulk asynchronous copies (cp.async.bulk, completion
+// counted in bytes on an mbarrier) S tiles ahead, so the bytes in flight do
+// not depend on registers.
+// Source runs: even step, slot i of the tile's own nodes; odd step, slot
+// opp(i) of the nodes n - o_i, o_i = c_ix + c_iy nx + c_iz nx ny (the
+// source x - c_i).  A run [n0 - o_i, n0 - o_i + NT) is widened down to the
+// 16-byte boundary u_i = (n0 - o_i) & ~3 and up to the next one, and placed
+// in its stage slot as if it started at u_i, so that node n0 + t reads
+// element t + d_i with d_i = (n0 - o_i) - u_i = (-o_i) & 3 (n0 is a multiple
+// of 4), the same for every tile.  The part of a widened run outside its
+// array is not copied: those elements, like any other element of a source
+// outside the box (a row, plane or array end crossed), are unknowns the
+// boundary rebuild overwrites.  Stores go straight from registers
+// (lattice_finish).
+constexpr unsigned kStageWaitPolls = 1u << 22;  // try_wait polls before a stage counts as lost
+
+template <int NT>
+__host__ __device__ constexpr int stage_run()
+{
+    return NT + 8;  // floats per population per stage: NT plus the widening to 16-byte boundaries
+}
+
+template <int NT, int S>
+__host__ __device__ constexpr size_t stage_bytes()
+{
+    return sizeof(float) * (size_t)S * 19 * stage_run<NT>();
+}
+
+template <bool ODD, int i>
+__device__ __forceinline__ int src_offset(const int nx, const int nxy)
+{
+    return ODD ? cxf(i) + cyf(i) * nx + czf(i) * nxy : 0;
+}
+
+// a / b for 0 <= a < 2^26 and b >= 1 from a float reciprocal, corrected to
+// the exact quotient
+__device__ __forceinline__ int div_by(const int a, const int b, const float inv_b)
+{
+    int q = __float2int_rz(__int2float_rn(a) * inv_b);
+    const int r = a - q * b;
+    q += (r >= b) - (r < 0);
+    return q;
+}
+
+// Registers are capped near 80 per thread whatever the resident blocks B (the
+// bound is 6 blocks of 128 threads, or 3 of 256), leaving part of the
+// register file free for the droplet kernels beside this one.
+template <int NT, int S, int B, bool ODD, int MODE>
+__global__ void __launch_bounds__(NT, (B > 768 / NT ? B : 768 / NT)) k_lattice_staged(LbView L, int pbuf)
+{
+    constexpr int RUN = stage_run<NT>();
+    extern __shared__ __align__(128) float stage[];  // [S][19][RUN]
+    __shared__ __align__(8) unsigned long long full[S];
+    const int tid = threadIdx.x;
+    const int nodes = L.nodes, nx = L.n[0], ny = L.n[1], nz = L.n[2], nxy = nx * ny;
+    const int qs = (int)L.qs;
+    const float *__restrict__ f = static_cast<const float *>(L.f);
+    const int ntiles = (nodes + NT - 1) / NT;
+    const float inv_nx = 1.0f / (float)nx, inv_nxy = 1.0f / (float)nxy;
+    if ((blockIdx.x | tid) == 0) close_step(L);
+    if (tid == 0) {
+        for (int k = 0; k < S; ++k) mbar_init(&full[k], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    // d_i of every population, two bits each
+    unsigned long long dpack = 0;
+    if constexpr (ODD)
+        sfor<19>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            dpack |= (unsigned long long)((-src_offset<ODD, i>(nx, nxy)) & 3) << (2 * i);
+        });
+    // warp 0: the 19 source runs of `tile` into stage `s`, lane i copying
+    // run i.  Lane 0's single arrival, which also announces the bytes of all
+    // 19 copies, comes after the copies are issued: until it arrives the
+    // phase cannot complete, whatever the copies have delivered by then.
+    const int lane = tid & 31;
+    int off_l = 0, arr_l = 0;  // lane i < 19: source offset and array of population i
+    sfor<19>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        if (lane == i) {
+            off_l = src_offset<ODD, i>(nx, nxy);
+            arr_l = ODD ? opp(i) : i;
+        }
+    });
+    auto issue = [&](const int tile, const int s) {
+        const int n0 = tile * NT, len = min(NT, nodes - n0);
+        unsigned nb = 0;
+        if (lane < 19) {
+            const int u = (n0 - off_l) & ~3;  // widened start, may lie before the array
+            const int a = max(u, 0), b = min((n0 - off_l + len + 3) & ~3, qs);
+            if (b > a) {
+                nb = 4u * (unsigned)(b - a);
+                bulk_g2s(stage + (s * 19 + lane) * RUN + (a - u), f + (size_t)arr_l * qs + a, nb, &full[s]);
+            }
+        }
+        const unsigned total = __reduce_add_sync(0xffffffffu, nb);
+        if (lane == 0) mbar_arrive_expect_tx(&full[s], total);
+    };
+    if (tid < 32)
+        for (int k = 0; k < S; ++k) {
+            const int t = blockIdx.x + k * gridDim.x;
+            if (t < ntiles) issue(t, k);
+        }
+    int k = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
+        const int s = k % S;
+        const bool arrived = mbar_wait(&full[s], (unsigned)(k / S) & 1u, kStageWaitPolls);
+        if (!__syncthreads_and(arrived)) {
+            // a stage that never completes: report it, let the copies still
+            // in flight land (bounded), and leave without touching memory
+            if (tid == 0) {
+                atomicOr(&L.ctl->err, IBL_ERRBIT_TIMEOUT);
+                for (int j = 0; j < S; ++j) {
+                    const int kk = k + j;
+                    if (blockIdx.x + kk * (int)gridDim.x < ntiles)
+                        mbar_wait(&full[kk % S], (unsigned)(kk / S) & 1u, kStageWaitPolls);
+                }
+            }
+            return;
+        }
+        const int n = tile * NT + tid;
+        bool bad = false;
+        if (n < nodes) {
+            const int z = div_by(n, nxy, inv_nxy), rem = n - z * nxy, y = div_by(rem, nx, inv_nx), x = rem - y * nx;
+            const bool in_patch = node_in_patch(L, L.ctl, pbuf, x, y, z);
+            if (!(MODE == LAT_FAR && in_patch)) {
+                const int sx = x == 0 ? -1 : (x == nx - 1 ? 1 : 0);
+                const int sy = y == 0 ? -1 : (y == ny - 1 ? 1 : 0);
+                const int sz = z == 0 ? -1 : (z == nz - 1 ? 1 : 0);
+                const float *src = stage + s * 19 * RUN + tid;
+                float g[19];
+                sfor<19>([&](auto I) {
+                    constexpr int i = decltype(I)::value;
+                    if constexpr (ODD) g[i] = src[i * RUN + (int)((dpack >> (2 * i)) & 3u)];
+                    else g[i] = src[i * RUN];
+                });
+                bad = lattice_finish<float, ODD, false, MODE, false>(L, g, x, y, z, n, in_patch, pbuf, sx, sy, sz);
+            }
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, bad);
+        if (m != 0u && (tid & 31) == 0) atomicOr(&L.ctl->err, IBL_ERRBIT_UNSTABLE);
+        __syncthreads();  // every thread is done with stage s
+        if (tid < 32) {
+            const int t = tile + S * (int)gridDim.x;
+            if (t < ntiles) issue(t, s);
+        }
+    }
 }
 
 // The patch nodes of the step: one warp per row (y, z) of the patch box,
@@ -1480,8 +1686,104 @@ static void lattice_launch_t(const LbView &L, int mode, int pbuf, dim3 g, dim3 b
     }
 }
 
+// Opts a kernel into its dynamic shared memory and the largest shared-memory
+// carveout, once per kernel and device.
+static cudaError_t prefer_shared(const void *kernel, size_t dyn)
+{
+    static std::mutex mu;
+    static std::set<std::pair<const void *, int>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count({kernel, dev})) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess) done.insert({kernel, dev});
+    return e;
+}
+
+// Launch shapes of the staged outside update: nodes per tile (= threads per
+// block), pipeline stages, resident blocks per SM.
+template <int V>
+struct StagedShape;
+template <>
+struct StagedShape<1> {
+    static constexpr int NT = 128, S = 4, B = 4;
+};
+template <>
+struct StagedShape<2> {
+    static constexpr int NT = 128, S = 3, B = 6;
+};
+template <>
+struct StagedShape<3> {
+    static constexpr int NT = 128, S = 2, B = 8;
+};
+template <>
+struct StagedShape<4> {
+    static constexpr int NT = 256, S = 3, B = 3;
+};
+
+template <int V, bool ODD>
+static cudaError_t staged_launch(const LbView &L, int mode, int pbuf, cudaStream_t s)
+{
+    constexpr int NT = StagedShape<V>::NT, S = StagedShape<V>::S, B = StagedShape<V>::B;
+    constexpr size_t smem = stage_bytes<NT, S>();
+    void (*k)(LbView, int) = mode == LAT_FAR ? k_lattice_staged<NT, S, B, ODD, LAT_FAR>
+                                             : k_lattice_staged<NT, S, B, ODD, LAT_FULL>;
+    cudaError_t e = prefer_shared(reinterpret_cast<const void *>(k), smem);
+    if (e != cudaSuccess) return e;
+    const long long tiles = ((long long)L.nodes + NT - 1) / NT;
+    const unsigned g = (unsigned)std::min<long long>(tiles, (long long)sm_count() * B);
+    k<<<g, NT, smem, s>>>(L, pbuf);
+    return cudaGetLastError();
+}
+
+template <bool ODD>
+static cudaError_t staged_dispatch(const LbView &L, int mode, int pbuf, cudaStream_t s)
+{
+    switch (L.staged) {
+    case 1: return staged_launch<1, ODD>(L, mode, pbuf, s);
+    case 2: return staged_launch<2, ODD>(L, mode, pbuf, s);
+    case 3: return staged_launch<3, ODD>(L, mode, pbuf, s);
+    default: return staged_launch<4, ODD>(L, mode, pbuf, s);
+    }
+}
+
+template <int V>
+static cudaError_t staged_prepare_v()
+{
+    constexpr int NT = StagedShape<V>::NT, S = StagedShape<V>::S, B = StagedShape<V>::B;
+    constexpr size_t smem = stage_bytes<NT, S>();
+    cudaError_t e = cudaSuccess;
+    for (void (*k)(LbView, int) : {k_lattice_staged<NT, S, B, false, LAT_FAR>, k_lattice_staged<NT, S, B, false, LAT_FULL>,
+                                   k_lattice_staged<NT, S, B, true, LAT_FAR>, k_lattice_staged<NT, S, B, true, LAT_FULL>})
+        if (e == cudaSuccess) e = prefer_shared(reinterpret_cast<const void *>(k), smem);
+    return e;
+}
+
+cudaError_t staged_prepare(int kind)
+{
+    switch (kind) {
+    case 1: return staged_prepare_v<1>();
+    case 2: return staged_prepare_v<2>();
+    case 3: return staged_prepare_v<3>();
+    case 4: return staged_prepare_v<4>();
+    default: return cudaSuccess;
+    }
+}
+
+bool staged_ok(const LbView &L)
+{
+    return L.precision == IBL_FP32_DEV && !any_periodic(L) && (reinterpret_cast<uintptr_t>(L.f) & 15u) == 0 &&
+           (L.qs & 3) == 0 && L.nodes < (1 << 26);
+}
+
 cudaError_t launch_lattice(const LbView &L, bool odd, bool record, int mode, int pbuf, cudaStream_t s)
 {
+    if (L.staged > 0 && !record && staged_ok(L))
+        return odd ? staged_dispatch<true>(L, mode, pbuf, s) : staged_dispatch<false>(L, mode, pbuf, s);
     dim3 g, b;
     lattice_grid(L, g, b);
     if (L.precision == IBL_FP64) {

@@ -185,6 +185,17 @@ class Sim:
         """Capture (without running) the graphs the next step(n) replays."""
         L.check(self.lib.ibl_prepare_steps(self.h, int(n)))
 
+    def set_outside_update(self, kind: int):
+        """Kernel of the update outside the droplet patch: 0 direct loads,
+        1..4 the staged shared-memory pipeline in one of its launch shapes."""
+        L.check(self.lib.ibl_set_outside_update(self.h, int(kind)))
+
+    @property
+    def outside_update(self) -> int:
+        k = ctypes.c_int()
+        L.check(self.lib.ibl_outside_update(self.h, ctypes.byref(k)))
+        return k.value
+
     def set_graphs(self, enable: bool):
         """Replay whole chunks of steps as a captured CUDA graph (default on)."""
         L.check(self.lib.ibl_set_graphs(self.h, 1 if enable else 0))

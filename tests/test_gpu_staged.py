@@ -1,0 +1,123 @@
+"""The staged outside update (persistent blocks that copy each tile's
+populations into shared memory with bulk asynchronous copies, completion
+counted on an mbarrier) against the one-thread-per-node kernel with direct
+loads: the same arithmetic on the same values, so the lattice-only update is
+equal bit for bit in every launch shape, on boxes whose sizes make the
+copied runs cross rows, planes and both ends of the arrays (the widened,
+clipped runs and the clamped reads of the odd step).  With a droplet the
+spread's unordered FP32 reductions allow rounding-level differences only."""
+import numpy as np
+import pytest
+
+from paper_2403_01161_gb300 import _lib as L
+from paper_2403_01161_gb300 import config
+from parity import frames_ou, lib_to_oracle_perm, rel
+
+pytestmark = pytest.mark.gpu
+
+KINDS = (1, 2, 3, 4)
+
+
+def _lattice(n, kind, steps, frames, graphs=False):
+    from paper_2403_01161_gb300.sim import Sim
+
+    g = Sim(n, 1.0, frames, 3, precision="fp32")
+    g.set_graphs(graphs)
+    g.set_outside_update(kind)
+    assert g.outside_update == kind
+    g.step(steps)
+    assert g.status() == 0
+    f = g.populations()
+    g.close()
+    return f
+
+
+@pytest.mark.parametrize("n", [(20, 18, 22), (17, 19, 23), (5, 4, 6), (64, 40, 33)])
+def test_lattice_only_equals_direct_kernel_bit_for_bit(n):
+    fr = frames_ou(61, 6, 3e-3)
+    ref = _lattice(n, 0, 9, fr)
+    for kind in KINDS:
+        got = _lattice(n, kind, 9, fr)
+        assert np.array_equal(got, ref), (kind, np.abs(got - ref).max())
+
+
+def test_lattice_only_graph_replay_equals_direct_kernel():
+    fr = frames_ou(62, 40, 3e-3)
+    n = (24, 20, 28)
+    ref = _lattice(n, 0, 101, fr, graphs=True)
+    got = _lattice(n, 1, 101, fr, graphs=True)
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_droplet_staged_matches_direct_and_oracle(kind):
+    import oracle as O
+    from paper_2403_01161_gb300.sim import Sim
+
+    n = (24, 22, 26)
+    fr = frames_ou(21, 4, 4e-3)
+    c = tuple(0.5 * (k - 1) for k in n)
+    out = []
+    for k in (0, kind):
+        g = Sim(n, 1.0, fr, 4, precision="fp32", record_fields=True)
+        g.add_icosphere(2, 4.5, 0.02, center=c)
+        g.set_outside_update(k)
+        g.step(10)
+        g.step_record()
+        assert g.status() == 0
+        out.append((g.populations(), g.mesh()[0], g.fields()[1]))
+        g.close()
+    (fa, ra, ua), (fb, rb, ub) = out
+    assert np.abs(fa - fb).max() < 1e-6
+    assert np.abs(ra - rb).max() < 1e-7
+    o = O.OracleSim(n, 1.0, fr, 4)
+    r0, t = O.icosphere(2, 4.5, c)
+    o.set_mesh(r0, t, 0.02)
+    o.step(11)
+    assert rel(ub, o.fields()[1]) < 1e-5
+    assert np.abs(rb - o.mesh()[0]).max() < 1e-6
+    perm = lib_to_oracle_perm()
+    assert np.abs(fb[perm] - o.populations()).max() < 2e-6
+
+
+def test_single_droplet_128_staged_one_step_against_oracle():
+    """The measured workload (128^3, R 12, level 4) with the staged kernel:
+    after 61 GPU steps the state goes to the oracle and both take one more."""
+    import oracle as O
+    from paper_2403_01161_gb300.sim import Sim
+
+    w = config.single_droplet_128(steps=100)
+    g = Sim(w.n, w.tau, w.frames, w.n_hold, precision=w.precision, record_fields=True)
+    g.add_icosphere(w.level, w.R, w.sigma)
+    g.set_outside_update(1)
+    g.step(61)
+    g.sync()
+    perm = lib_to_oracle_perm()
+    f_k = g.populations()[perm]
+    r_k, _, tris = g.mesh()
+    o = O.OracleSim(w.n, w.tau, w.frames, w.n_hold)
+    o.set_mesh(r_k, tris, w.sigma)
+    o.set_populations(f_k, 61)
+    g.step(1)  # a plain step: the staged kernel updates the outside nodes
+    g.sync()
+    o.step(1)
+    assert np.abs(g.populations()[perm] - o.populations()).max() < 2e-6
+    assert np.abs(g.mesh()[0] - o.mesh()[0]).max() < 1e-8
+    assert g.status() == 0
+
+
+def test_staged_kernel_refuses_periodic_and_fp64():
+    from paper_2403_01161_gb300.sim import Sim
+
+    fr = frames_ou(63, 2, 1e-3)
+    g = Sim((16, 16, 16), 1.0, fr, 3, bc=(L.BC_PERIODIC, L.BC_ZOU_HE, L.BC_ZOU_HE), precision="fp32")
+    with pytest.raises(L.IblError) as e:
+        g.set_outside_update(1)
+    assert e.value.code == L.IBL_EINVAL
+    g.close()
+    g = Sim((16, 16, 16), 1.0, fr, 3, precision="fp64")
+    with pytest.raises(L.IblError):
+        g.set_outside_update(2)
+    with pytest.raises(L.IblError):
+        g.set_outside_update(5)
+    g.close()

@@ -53,11 +53,14 @@ def _sim(w, record_fields):
 
 
 def _check_records(series, d, prefix, last_step, label):
-    """Every GPU shape record up to last_step against the oracle's."""
+    """Every GPU shape record up to last_step against the oracle's: the
+    worst error of each observable (and the step it occurred at) is printed
+    and then held to its bound."""
     by_step = {int(s["step"]): s for s in series}
     steps = d[prefix + "rec_step"]
-    worst = {"D": 0.0, "beta": 0.0, "V": 0.0, "lam": 0.0}
-    n_beta = 0
+    worst = {"D": (0.0, 0), "beta": (0.0, 0), "V": (0.0, 0), "lam_max": (0.0, 0)}
+    n = 0
+    trace = []
     for k, st in enumerate(steps):
         st = int(st)
         if st > last_step:
@@ -65,35 +68,34 @@ def _check_records(series, d, prefix, last_step, label):
         assert st in by_step, "%s: GPU has no record at step %d" % (label, st)
         s = by_step[st]
         assert s["err"] == 0, "%s: GPU flagged error bits %d at step %d" % (label, s["err"], st)
+        n += 1
         D_o = float(d[prefix + "rec_D"][k])
-        eD = abs(s["D"] - D_o) / max(abs(D_o), 0.05)
-        V_o = float(d[prefix + "rec_V"][k])
-        eV = abs(s["V"] - V_o) / abs(V_o)
         lam_o = np.asarray(d[prefix + "rec_lam"][k], dtype=np.float64)
-        lmax_o = float(lam_o.max())
-        eL = abs(max(s["lam"]) - lmax_o) / lmax_o
-        worst["D"] = max(worst["D"], eD)
-        worst["V"] = max(worst["V"], eV)
-        worst["lam"] = max(worst["lam"], eL)
-        assert eD <= 1e-4, "%s step %d: D %.9f vs oracle %.9f" % (label, st, s["D"], D_o)
-        assert eV <= 1e-5, "%s step %d: V %.9f vs oracle %.9f" % (label, st, s["V"], V_o)
-        assert eL <= 1e-5, "%s step %d: lam_max %.9f vs oracle %.9f" % (label, st, max(s["lam"]), lmax_o)
+        e = {"D": abs(s["D"] - D_o) / max(abs(D_o), 0.05),
+             "V": abs(s["V"] - float(d[prefix + "rec_V"][k])) / abs(float(d[prefix + "rec_V"][k])),
+             "lam_max": abs(max(s["lam"]) - lam_o.max()) / lam_o.max()}
         ls = np.sort(lam_o)[::-1]
         b_o = float(d[prefix + "rec_beta"][k])
         if ls[0] - ls[1] >= 1e-2 * ls[0] and np.isfinite(b_o):
-            eb = abs(s["beta"] - b_o)
-            worst["beta"] = max(worst["beta"], eb)
-            n_beta += 1
-            assert eb <= 1e-4, "%s step %d: beta %.8f vs oracle %.8f" % (label, st, s["beta"], b_o)
-    print("%s: %d records to step %d, worst D %.2e, beta %.2e (%d records), V %.2e, lam_max %.2e"
-          % (label, len([s for s in steps if s <= last_step]), last_step, worst["D"], worst["beta"], n_beta,
-             worst["V"], worst["lam"]))
+            e["beta"] = abs(s["beta"] - b_o)
+        for key, v in e.items():
+            if v > worst[key][0]:
+                worst[key] = (v, st)
+        if st % 2500 == 0:
+            trace.append("%d: D %.1e lam %.1e" % (st, e["D"], e["lam_max"]))
+    print("%s: %d records to step %d; worst %s" % (label, n, last_step,
+                                                    ", ".join("%s %.2e (step %d)" % (k, v[0], v[1]) for k, v in worst.items())))
+    if trace:
+        print("  by step: " + "; ".join(trace))
+    bounds = {"D": 1e-4, "beta": 1e-4, "V": 1e-5, "lam_max": 1e-5}
+    return ["%s: %s error %.3e at step %d above %.0e" % (label, key, worst[key][0], worst[key][1], b)
+            for key, b in bounds.items() if worst[key][0] > b]
 
 
 def _check_positions(r_g, r_o, label):
     e = np.linalg.norm(r_g - r_o) / np.linalg.norm(r_o - r_o.mean(axis=0))
     print("%s: positions relative %.2e" % (label, e))
-    assert e <= 1e-6, "%s: positions differ by %.3e relative" % (label, e)
+    return [] if e <= 1e-6 else ["%s: positions differ by %.3e relative" % (label, e)]
 
 
 def _trajectory(w, name):
@@ -103,10 +105,10 @@ def _trajectory(w, name):
     g.step(last - 1)
     g.step_record()
     assert g.status() == 0
-    _check_records(g.series(), d, "", last, name)
+    bad = _check_records(g.series(), d, "", last, name)
     r_g, _, tris = g.mesh()
     assert np.array_equal(tris, d["tris"])
-    _check_positions(r_g, d["r_last"], name)
+    bad += _check_positions(r_g, d["r_last"], name)
     _, u, _ = g.fields()
     u = u.reshape(3, -1)
     idx = d["u_idx"]
@@ -114,9 +116,10 @@ def _trajectory(w, name):
     eu = np.linalg.norm(u[:, idx] - u_o) / np.linalg.norm(u_o)
     en = abs(np.linalg.norm(u) - float(d["u_norm_all"])) / float(d["u_norm_all"])
     print("%s: u sample relative %.2e (%d nodes), whole-field norm %.2e" % (name, eu, idx.size, en))
-    assert eu <= 1e-5
-    assert en <= 1e-5
+    if eu > 1e-5 or en > 1e-5:
+        bad.append("%s: u relative %.3e (sample), %.3e (norm)" % (name, eu, en))
     g.close()
+    assert not bad, "; ".join(bad)
 
 
 def test_single_droplet_128_trajectory():
@@ -146,11 +149,13 @@ def test_ensemble_members_trajectories():
     stop = min(last)
     E.step(stop)
     E.sync()
+    bad = []
     for k, (g, w) in enumerate(zip(members, ws)):
-        _check_records(g.series(), d, "m%d_" % k, min(last[k], stop), "ensemble member %d (%s)" % (k, w.name))
+        bad += _check_records(g.series(), d, "m%d_" % k, min(last[k], stop), "ensemble member %d (%s)" % (k, w.name))
         if last[k] == stop:
             r_g, _, _ = g.mesh()
-            _check_positions(r_g, d["m%d_r_last" % k], "ensemble member %d" % k)
+            bad += _check_positions(r_g, d["m%d_r_last" % k], "ensemble member %d" % k)
     E.close()
     for g in members:
         g.close()
+    assert not bad, "; ".join(bad)
