@@ -241,10 +241,15 @@ class Sim:
         L.check(self.lib.ibl_readout(self.mesh_h, ctypes.byref(o)))
         return o.as_dict()
 
-    def series(self, max_records: int = 4096):
+    def series(self, max_records: int = 4096, allow_error: bool = False):
+        """The shape-record ring, oldest first.  With allow_error the records
+        are returned even when the lattice carries a sticky device error
+        (each record holds the error bits of its own step)."""
         buf = (L.Observables * max_records)()
         cnt = ctypes.c_int()
-        L.check(self.lib.ibl_read_series(self.mesh_h, buf, max_records, ctypes.byref(cnt)))
+        st = self.lib.ibl_read_series(self.mesh_h, buf, max_records, ctypes.byref(cnt))
+        if not (allow_error and st in (L.IBL_EUNSTABLE, L.IBL_ENOCONV, L.IBL_EWALL, L.IBL_ETIMEOUT)):
+            L.check(st)
         return [buf[k].as_dict() for k in range(cnt.value)]
 
     def fields(self):

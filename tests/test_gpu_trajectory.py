@@ -20,7 +20,19 @@ Per-observable bounds (FP32 deviation populations, FP64 mesh geometry):
   r       relative 1e-6: |r_gpu - r_oracle|_2 / |r_oracle - mean(r_oracle)|_2,
           i.e. against the droplet's size, not its place in the box.
 A trajectory the oracle stopped at a flagged record (a stencil reaching a
-wall) is compared up to its last clean record."""
+wall) is compared up to its last clean record.
+
+Comparison horizon.  Without regularisation (Sec. 3.3) a droplet's mesh can
+degrade until its triangles are several lattice units long; the scheme then
+amplifies rounding exponentially, and two FP64 evaluations of the same step
+that differ only in the order of their sums separate (the ensemble member of
+seed 1007: FP64 GPU path and FP64 oracle agree to 7e-13 at step 7500, 3e-7 at
+8000).  Past that point no implementation reproduces another, at any
+precision.  The same trajectory is therefore also run on the FP64 GPU path,
+and the FP32 path is compared up to the last record at which the FP64 path
+still matches the oracle to 1e-9 in D and lam_max; the test requires that
+horizon to cover at least half of the trajectory."""
+import dataclasses
 import os
 
 import numpy as np
@@ -92,6 +104,24 @@ def _check_records(series, d, prefix, last_step, label):
             for key, b in bounds.items() if worst[key][0] > b]
 
 
+def _fp64_horizon(series64, d, prefix, last_step):
+    """Last oracle record step up to which the FP64 GPU records match the
+    oracle's to 1e-9 (D relative to max(|D|, 0.05), lam_max relative)."""
+    by_step = {int(s["step"]): s for s in series64}
+    h = 0
+    for k, st in enumerate(d[prefix + "rec_step"]):
+        st = int(st)
+        if st > last_step or st not in by_step:
+            break
+        s = by_step[st]
+        D_o = float(d[prefix + "rec_D"][k])
+        lam_o = float(np.max(d[prefix + "rec_lam"][k]))
+        if abs(s["D"] - D_o) > 1e-9 * max(abs(D_o), 0.05) or abs(max(s["lam"]) - lam_o) > 1e-9 * lam_o:
+            break
+        h = st
+    return h
+
+
 def _check_positions(r_g, r_o, label):
     e = np.linalg.norm(r_g - r_o) / np.linalg.norm(r_o - r_o.mean(axis=0))
     print("%s: positions relative %.2e" % (label, e))
@@ -101,13 +131,24 @@ def _check_positions(r_g, r_o, label):
 def _trajectory(w, name):
     d = _golden(name)
     last = int(d["last_step"])
+    g64 = _sim(dataclasses.replace(w, precision="fp64"), record_fields=False)
+    g64.step(last)
+    assert g64.status() == 0
+    horizon = _fp64_horizon(g64.series(), d, "", last)
+    g64.close()
+    print("%s: FP64 path matches the oracle to 1e-9 up to step %d of %d" % (name, horizon, last))
+    assert horizon >= last // 2
     g = _sim(w, record_fields=True)
     g.step(last - 1)
     g.step_record()
     assert g.status() == 0
-    bad = _check_records(g.series(), d, "", last, name)
+    bad = _check_records(g.series(), d, "", horizon, name)
     r_g, _, tris = g.mesh()
     assert np.array_equal(tris, d["tris"])
+    if horizon < last:  # the stored state lies past the horizon
+        g.close()
+        assert not bad, "; ".join(bad)
+        return
     bad += _check_positions(r_g, d["r_last"], name)
     _, u, _ = g.fields()
     u = u.reshape(3, -1)
@@ -136,23 +177,40 @@ def test_precision_stress_256_trajectory():
 
 def test_ensemble_members_trajectories():
     """The first 8 members of the uneven ensemble (seeds 1000-1007, boxes
-    48^3-96^3), stepped together by the batched kernels for 10000 steps."""
+    48^3-96^3), stepped together by the batched kernels for 10000 steps.
+    A member the oracle stopped at a flagged record (its stencil reaching a
+    wall) is compared up to its last clean record; the ensemble reports it,
+    and the other members run on unaffected."""
+    from paper_2403_01161_gb300 import _lib as L
     from paper_2403_01161_gb300.sim import Ensemble
 
     d = _golden("ensemble8")
     ws = config.ensemble_workloads(8, steps=10000)
+    last = [int(d["m%d_last_step" % k]) for k in range(8)]
+    flagged = [int(d["m%d_first_err_step" % k]) > 0 for k in range(8)]
+    m64 = [_sim(dataclasses.replace(w, precision="fp64"), record_fields=False) for w in ws]
+    E64 = Ensemble(m64)
+    E64.step(10000)
+    horizon = [_fp64_horizon(g.series(allow_error=flagged[k]), d, "m%d_" % k, last[k]) for k, g in enumerate(m64)]
+    E64.close()
+    for g in m64:
+        g.close()
+    print("ensemble: FP64 path matches the oracle to 1e-9 up to steps %s (last clean records %s)" % (horizon, last))
+    assert all(h >= 5000 for h in horizon)
     members = [_sim(w, record_fields=False) for w in ws]
     E = Ensemble(members)
-    last = [int(d["m%d_last_step" % k]) for k in range(8)]
-    # members the oracle found clean to the end run the full length; a
-    # flagged member stops every member at its last clean record
-    stop = min(last)
-    E.step(stop)
-    E.sync()
+    E.step(10000)
+    if any(flagged):
+        with pytest.raises(L.IblError) as e:
+            E.sync()
+        assert e.value.code in (L.IBL_EWALL, L.IBL_EUNSTABLE)
+    else:
+        E.sync()
     bad = []
     for k, (g, w) in enumerate(zip(members, ws)):
-        bad += _check_records(g.series(), d, "m%d_" % k, min(last[k], stop), "ensemble member %d (%s)" % (k, w.name))
-        if last[k] == stop:
+        bad += _check_records(g.series(allow_error=flagged[k]), d, "m%d_" % k, horizon[k],
+                              "ensemble member %d (%s)" % (k, w.name))
+        if horizon[k] == last[k] == 10000:
             r_g, _, _ = g.mesh()
             bad += _check_positions(r_g, d["m%d_r_last" % k], "ensemble member %d" % k)
     E.close()
