@@ -687,11 +687,12 @@ def run_ours(args):
 
     # event pairs around one launch in `every` of the lattice kernel (nodes
     # outside the droplet patch), eager or inside a replayed graph: an event
-    # pair costs its step a little of the two streams' overlap, so sampling
-    # stays sparse (at least 4 launches of the timed region when it has 16
-    # steps or more); an odd stride samples both step parities (the AA
-    # pattern's even and odd kernels differ)
-    every = max(1, min(99, args.steps // 5)) | 1
+    # pair costs its step part of the two streams' overlap (measured in a
+    # 20-step window: 56.7 us per step without pairs, 59.0 with four, 57.5
+    # with two), so sampling stays sparse -- at least two launches once the
+    # region has 3 steps or more; an odd stride samples both step parities
+    # (the AA pattern's even and odd kernels differ)
+    every = max(1, min(99, args.steps // 2)) | 1
     sim.step(args.warmup)
     sim.sync()
     sim.profile(True, mask=1, every=every)  # clears the warm-up's marks (and its graphs)
