@@ -268,6 +268,16 @@ int ibl_prepare_steps(ibl_lb *lb, long long n);
 int ibl_set_outside_update(ibl_lb *lb, int kind);
 int ibl_outside_update(const ibl_lb *lb, int *kind);
 
+/* For tests of the failure path only (no counterpart in the paper): with
+ * on != 0 the staged outside update (kinds 1..4) announces more bytes than
+ * its copies deliver, so that no stage completes.  Each block then gives up
+ * after 1 s of waiting, sets the sticky bit IBL_ERRBIT_TIMEOUT, waits at
+ * most 0.2 s per stage still outstanding and returns without updating a
+ * node; the next synchronising call reports IBL_ETIMEOUT and the device
+ * stays usable.
+ * Synchronises the bound stream and drops captured graphs. */
+int ibl_test_stage_timeout(ibl_lb *lb, int on);
+
 /* Steps ibl_step has run eagerly and by graph replay since the lattice was
  * created (ibl_step_record and the adjoint's recomputations not counted). */
 int ibl_step_paths(const ibl_lb *lb, long long *eager, long long *replayed);

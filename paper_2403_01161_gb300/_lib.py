@@ -79,6 +79,7 @@ SIGNATURES = [
     ("ibl_prepare_steps", ctypes.c_int, [_P, ctypes.c_longlong]),
     ("ibl_set_outside_update", ctypes.c_int, [_P, ctypes.c_int]),
     ("ibl_outside_update", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
+    ("ibl_test_stage_timeout", ctypes.c_int, [_P, ctypes.c_int]),
     ("ibl_step_record", ctypes.c_int, [_P]),
     ("ibl_set_graphs", ctypes.c_int, [_P, ctypes.c_int]),
     ("ibl_step_paths", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),

@@ -1175,6 +1175,7 @@ int ibl_lb_create(const ibl_lb_params *p, const double *A_frames, int n_frames, 
     v.n_hold = steps_per_frame;
     v.ctl = reinterpret_cast<Ctl *>(lb->ws + L.ctl);
     v.staged = 0;
+    v.stage_fault = 0;
     Ctl c;
     std::memset(&c, 0, sizeof c);
     for (int b = 0; b < 3; ++b)
@@ -1493,6 +1494,15 @@ int ibl_set_outside_update(ibl_lb *lb, int kind)
     if (e != cudaSuccess) return cuda_fail(e, "staged kernel attributes");
     drop_graph(lb);  // captured chunks hold the lattice view by value
     lb->v.staged = kind;
+    return IBL_OK;
+}
+
+int ibl_test_stage_timeout(ibl_lb *lb, int on)
+{
+    if (!lb) return fail(IBL_EINVAL, "null lattice");
+    cudaStreamSynchronize(lb->stream);
+    drop_graph(lb);  // captured chunks hold the lattice view by value
+    lb->v.stage_fault = on ? 1 : 0;
     return IBL_OK;
 }
 

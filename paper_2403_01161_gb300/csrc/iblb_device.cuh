@@ -527,13 +527,21 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
                  : "memory");
 }
 
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // Waits until the phase with parity `parity` of the barrier has completed;
-// gives up after `limit` polls (each poll may suspend the thread for a
-// while) and returns false then.
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, unsigned limit)
+// gives up after `limit_ns` nanoseconds of the global timer and returns
+// false then.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, unsigned long long limit_ns)
 {
     const unsigned a = smem_addr(bar);
-    for (unsigned k = 0; k < limit; ++k) {
+    const unsigned long long t0 = global_ns();
+    for (;;) {
         unsigned done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -543,8 +551,8 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
             : "r"(a), "r"(parity)
             : "memory");
         if (done) return true;
+        if (global_ns() - t0 > limit_ns) return false;
     }
-    return false;
 }
 
 }  // namespace iblb

@@ -59,6 +59,7 @@ struct LbView {
     unsigned int *ind;  // [ceil(nodes / 4)] inside flags, one byte per node (set by the indicator kernel, cleared by the patch update)
     Ctl *ctl;
     int staged;         // outside / whole-box update: 0 one thread per node with direct loads (k_lattice), v > 0 the staged pipeline's launch shape v (k_lattice_staged)
+    int stage_fault;    // tests only: the staged update's stages never complete (its waits run out: IBL_ETIMEOUT)
 };
 
 struct MeshView {

@@ -517,7 +517,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 4) k_lattice(LbView 
 // outside the box (a row, plane or array end crossed), are unknowns the
 // boundary rebuild overwrites.  Stores go straight from registers
 // (lattice_finish).
-constexpr unsigned kStageWaitPolls = 1u << 22;  // try_wait polls before a stage counts as lost
+constexpr unsigned long long kStageWaitNs = 1000000000ull;  // a stage that has not arrived after 1 s is lost
+constexpr unsigned long long kDrainWaitNs = 200000000ull;  // then each copy still in flight gets 0.2 s
 
 template <int NT>
 __host__ __device__ constexpr int stage_run()
@@ -600,7 +601,9 @@ __global__ void __launch_bounds__(NT, (B > 768 / NT ? B : 768 / NT)) k_lattice_s
             }
         }
         const unsigned total = __reduce_add_sync(0xffffffffu, nb);
-        if (lane == 0) mbar_arrive_expect_tx(&full[s], total);
+        // L.stage_fault (tests of the timeout path only): announce 16 bytes
+        // more than the copies deliver, so that the phase never completes
+        if (lane == 0) mbar_arrive_expect_tx(&full[s], total + (L.stage_fault ? 16u : 0u));
     };
     if (tid < 32)
         for (int k = 0; k < S; ++k) {
@@ -610,7 +613,7 @@ __global__ void __launch_bounds__(NT, (B > 768 / NT ? B : 768 / NT)) k_lattice_s
     int k = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
         const int s = k % S;
-        const bool arrived = mbar_wait(&full[s], (unsigned)(k / S) & 1u, kStageWaitPolls);
+        const bool arrived = mbar_wait(&full[s], (unsigned)(k / S) & 1u, kStageWaitNs);
         if (!__syncthreads_and(arrived)) {
             // a stage that never completes: report it, let the copies still
             // in flight land (bounded), and leave without touching memory
@@ -619,7 +622,7 @@ __global__ void __launch_bounds__(NT, (B > 768 / NT ? B : 768 / NT)) k_lattice_s
                 for (int j = 0; j < S; ++j) {
                     const int kk = k + j;
                     if (blockIdx.x + kk * (int)gridDim.x < ntiles)
-                        mbar_wait(&full[kk % S], (unsigned)(kk / S) & 1u, kStageWaitPolls);
+                        mbar_wait(&full[kk % S], (unsigned)(kk / S) & 1u, kDrainWaitNs);
                 }
             }
             return;

@@ -3,8 +3,9 @@ frame or position (refused before any device work), a gradient frame whose
 wall velocity breaks the Mach limit |u| <= 0.3 (the lattice kernels flag it,
 the next synchronising call reports IBL_EUNSTABLE), a regularisation that
 cannot meet its tolerance in max_iter iterations (Sec. 3.3 exit criterion;
-IBL_ENOCONV), and an ensemble naming the member that failed.  No case faults
-the GPU: the kernels bound every access whatever the values."""
+IBL_ENOCONV), an ensemble naming the member that failed, and a bounded
+device wait that runs out (IBL_ETIMEOUT).  No case faults the GPU: the
+kernels bound every access whatever the values, and every wait in time."""
 import numpy as np
 import pytest
 
@@ -119,3 +120,34 @@ def test_ensemble_names_the_failing_member():
     assert "ensemble member 1" in str(e.value)
     assert members[0].status() == L.IBL_OK and members[2].status() == L.IBL_OK
     E.close()
+
+
+def test_staged_update_wait_runs_out_and_reports_timeout():
+    """The staged outside update waits on mbarriers for its own bulk copies,
+    each wait bounded in time.  With the test hook its stages never complete
+    (more bytes announced than copied): every block gives up after 1 s, sets
+    the sticky timeout bit and returns; the next synchronising call reports
+    IBL_ETIMEOUT, and the device stays usable for the next lattice."""
+    import time
+
+    from paper_2403_01161_gb300.sim import Sim
+
+    fr = frames_ou(12, 4, 3e-3)
+    g = Sim(N, 1.0, fr, 5, precision="fp32")
+    g.set_graphs(False)
+    g.set_outside_update(1)
+    L.check(g.lib.ibl_test_stage_timeout(g.h, 1))
+    t0 = time.time()
+    g.step(1)
+    assert g.status() == L.IBL_ETIMEOUT
+    assert time.time() - t0 < 30.0
+    g.close()
+    h = Sim(N, 1.0, fr, 5, precision="fp32")
+    h.set_outside_update(1)
+    h.step(4)
+    assert h.status() == 0
+    ref = Sim(N, 1.0, fr, 5, precision="fp32")
+    ref.step(4)
+    assert np.array_equal(h.populations(), ref.populations())
+    h.close()
+    ref.close()
