@@ -759,7 +759,8 @@ def run_ours(args):
     pinned.copy_(torch.from_numpy(np.ascontiguousarray(w.frames[1:n_fr + 1].reshape(n_fr, 9))))
     sim2 = Sim(w.n, w.tau, w.frames[:n_fr + 1], w.n_hold, precision=w.precision, device=dev)
     sim2.add_icosphere(w.level, w.R, w.sigma)
-    sim2.run_frames(w.frames[:1], w.n_hold)  # warm-up frame: the graph captures happen here
+    sim2.run_frames(w.frames[:1], w.n_hold)  # warm-up frame: the chunk graphs are captured here
+    sim2.prepare(w.n_hold)  # and the graphs of the next frame's steps (captured, not run)
     sim2.sync()
     barrier()
     t0 = time.perf_counter()
