@@ -502,10 +502,13 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 4) k_lattice(LbView 
 // of 128 at 64 registers fill the register file), and a droplet-kernel
 // block that takes a slot on an SM cuts that SM's share of the stream.
 // Here each block is persistent (B per SM) and walks tiles of NT
-// consecutive nodes of the flattened box; warp 0 stages the 19 source
-// runs of a tile (one lane per run) with bulk asynchronous copies (cp.async.bulk, completion
-// counted in bytes on an mbarrier) S tiles ahead, so the bytes in flight do
-// not depend on registers.
+// consecutive nodes of the flattened box; warp 0 stages the 19 source runs
+// of a tile (one lane per run) with bulk asynchronous copies (cp.async.bulk,
+// completion counted in bytes on an mbarrier) S tiles ahead, so the bytes in
+// flight do not depend on registers.  On GB300 it measures slower than the
+// direct kernel in every launch shape (the update is co-limited by
+// instruction issue, and the pipeline adds instructions and holds its SM
+// resources for the whole launch); it is selected by ibl_set_outside_update.
 // Source runs: even step, slot i of the tile's own nodes; odd step, slot
 // opp(i) of the nodes n - o_i, o_i = c_ix + c_iy nx + c_iz nx ny (the
 // source x - c_i).  A run [n0 - o_i, n0 - o_i + NT) is widened down to the
