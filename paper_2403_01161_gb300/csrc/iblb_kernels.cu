@@ -931,9 +931,11 @@ __global__ void __launch_bounds__(128) k_tri_moment_batched(const __grid_constan
 }
 
 template <typename T, int LANES>
-__global__ void __launch_bounds__(128) k_spread(LbView L, MeshView M, int next_buf)
+__global__ void __launch_bounds__(128) k_spread(LbView L, MeshView M, int next_buf, int nblk)
 {
-    spread_body<T, false, LANES>(L, M, blockIdx.x, next_buf);
+    // node groups block-strided: a grid capped below nblk leaves SM slots to
+    // the concurrent outside update
+    for (int b = blockIdx.x; b < nblk; b += (int)gridDim.x) spread_body<T, false, LANES>(L, M, b, next_buf);
 }
 
 // Re-centring (Sec. 3.2: the linearisation is centred on the droplet's
@@ -1140,9 +1142,12 @@ __device__ __forceinline__ void interp_body(const LbView &L, const MeshView &M, 
 }
 
 template <typename T, int LANES>
-__global__ void __launch_bounds__(128) k_interp(LbView L, MeshView M)
+__global__ void __launch_bounds__(128) k_interp(LbView L, MeshView M, int nblk)
 {
-    interp_body<T, LANES>(L, M, blockIdx.x, gridDim.x);
+    for (int b = blockIdx.x; b < nblk; b += (int)gridDim.x) {
+        interp_body<T, LANES>(L, M, b, nblk);
+        __syncthreads();  // the next pass reuses the body's shared rows
+    }
 }
 
 // Ensemble versions: block b works for member blk_member[b0 + b] as its
@@ -1857,16 +1862,30 @@ static int fwd_lanes(const MeshView &M)
     return (long long)M.nv * 16 <= (long long)sm_count() * kIbThreads ? 16 : kFwdLanes;
 }
 
+// Blocks of the single droplet's node-group kernels: one per group of
+// nodes, at most two per SM (block-strided beyond).  A level-5 mesh (10242
+// nodes, 640 groups) would otherwise hold about four blocks on every SM
+// while the outside update runs beside it; capped at two the 256^3 step
+// takes 431 instead of 437 us and the 200^3 production step 218.6 instead of
+// 223.0 us (at one per SM: 429 and 217 us, but the 128^3 step, 160 groups,
+// slows from 57.5 to 58.7 us).
+static unsigned ib_grid(int nblk)
+{
+    const int cap = 2 * sm_count();
+    return (unsigned)(nblk > cap ? cap : nblk);
+}
+
 cudaError_t launch_spread(const LbView &L, const MeshView &M, int next_buf, cudaStream_t s, int prio)
 {
     const int lanes = fwd_lanes(M);
-    const dim3 g(blocks_for((long long)M.nv * lanes, kIbThreads)), b(kIbThreads);
+    const int nblk = (int)blocks_for((long long)M.nv * lanes, kIbThreads);
+    const dim3 g(ib_grid(nblk)), b(kIbThreads);
     if (lanes == 16) {
-        if (L.precision == IBL_FP64) return launch_p(k_spread<double, 16>, g, b, s, prio, L, M, next_buf);
-        return launch_p(k_spread<float, 16>, g, b, s, prio, L, M, next_buf);
+        if (L.precision == IBL_FP64) return launch_p(k_spread<double, 16>, g, b, s, prio, L, M, next_buf, nblk);
+        return launch_p(k_spread<float, 16>, g, b, s, prio, L, M, next_buf, nblk);
     }
-    if (L.precision == IBL_FP64) return launch_p(k_spread<double, kFwdLanes>, g, b, s, prio, L, M, next_buf);
-    return launch_p(k_spread<float, kFwdLanes>, g, b, s, prio, L, M, next_buf);
+    if (L.precision == IBL_FP64) return launch_p(k_spread<double, kFwdLanes>, g, b, s, prio, L, M, next_buf, nblk);
+    return launch_p(k_spread<float, kFwdLanes>, g, b, s, prio, L, M, next_buf, nblk);
 }
 
 cudaError_t launch_centre(const LbView &L, const MeshView &M, int buf, cudaStream_t s, int prio)
@@ -1882,13 +1901,14 @@ cudaError_t launch_indicator(const LbView &L, const MeshView &M, int buf, cudaSt
 cudaError_t launch_interp(const LbView &L, const MeshView &M, cudaStream_t s, int prio)
 {
     const int lanes = fwd_lanes(M);
-    const dim3 g(blocks_for((long long)M.nv * lanes, kIbThreads)), b(kIbThreads);
+    const int nblk = (int)blocks_for((long long)M.nv * lanes, kIbThreads);
+    const dim3 g(ib_grid(nblk)), b(kIbThreads);
     if (lanes == 16) {
-        if (L.precision == IBL_FP64) return launch_p(k_interp<double, 16>, g, b, s, prio, L, M);
-        return launch_p(k_interp<float, 16>, g, b, s, prio, L, M);
+        if (L.precision == IBL_FP64) return launch_p(k_interp<double, 16>, g, b, s, prio, L, M, nblk);
+        return launch_p(k_interp<float, 16>, g, b, s, prio, L, M, nblk);
     }
-    if (L.precision == IBL_FP64) return launch_p(k_interp<double, kFwdLanes>, g, b, s, prio, L, M);
-    return launch_p(k_interp<float, kFwdLanes>, g, b, s, prio, L, M);
+    if (L.precision == IBL_FP64) return launch_p(k_interp<double, kFwdLanes>, g, b, s, prio, L, M, nblk);
+    return launch_p(k_interp<float, kFwdLanes>, g, b, s, prio, L, M, nblk);
 }
 
 cudaError_t launch_regularize(const LbView &L, const MeshView &M, const RegParams &p, int buf, cudaStream_t s,
