@@ -55,7 +55,7 @@ RECORD_EVERY = 100
 def _golden(name):
     path = os.path.join(GOLDEN, "oracle_%s.npz" % name)
     if not os.path.exists(path):
-        pytest.skip("missing %s: run tests/golden/make_oracle_series.py %s" % (path, name))
+        pytest.fail("missing %s: run tests/golden/make_oracle_series.py %s" % (path, name))
     return np.load(path)
 
 
