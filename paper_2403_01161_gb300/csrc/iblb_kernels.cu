@@ -1863,17 +1863,12 @@ static int fwd_lanes(const MeshView &M)
 }
 
 // Blocks of the single droplet's node-group kernels: one per group of
-// nodes, at most two per SM (block-strided beyond).  A level-5 mesh (10242
-// nodes, 640 groups) would otherwise hold about four blocks on every SM
-// while the outside update runs beside it; capped at two the 256^3 step
-// takes 431 instead of 437 us and the 200^3 production step 218.6 instead of
-// 223.0 us (at one per SM: 429 and 217 us, but the 128^3 step, 160 groups,
-// slows from 57.5 to 58.7 us).
-static unsigned ib_grid(int nblk)
-{
-    const int cap = 2 * sm_count();
-    return (unsigned)(nblk > cap ? cap : nblk);
-}
+// nodes.  (The kernels are block-strided, so a grid may be capped; capped at
+// two blocks per SM, the 256^3 step took 431 instead of 437 us and the 200^3
+// step without regularisation 218.6 instead of 223.0 us, but the 200^3 step
+// regularised after every step 254 instead of 235 us: the longer droplet
+// chain then no longer fits beside the outside update.)
+static unsigned ib_grid(int nblk) { return (unsigned)nblk; }
 
 cudaError_t launch_spread(const LbView &L, const MeshView &M, int next_buf, cudaStream_t s, int prio)
 {
