@@ -60,6 +60,7 @@ struct LbView {
     Ctl *ctl;
     int staged;         // outside / whole-box update: 0 one thread per node with direct loads (k_lattice), v > 0 the staged pipeline's launch shape v (k_lattice_staged)
     int stage_fault;    // tests only: the staged update's stages never complete (its waits run out: IBL_ETIMEOUT)
+    int prefetch;       // 1: the direct outside update prefetches into L2 one resident wave ahead
 };
 
 struct MeshView {

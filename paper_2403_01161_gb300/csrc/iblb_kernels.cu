@@ -470,17 +470,6 @@ __device__ __forceinline__ void close_step(const LbView &L)
     L.ctl->frame_par[s & 1] = (int)(k < L.n_frames - 1 ? k : L.n_frames - 1);
 }
 
-// Largest droplet patch (nodes) with which the outside update still
-// prefetches into L2: the patch's populations and 4-wide force and velocity
-// records, about 108 B a node in FP32, then stay below an eighth of the L2.
-constexpr long long kPrefetchPatchMax = 150000;
-
-__device__ __forceinline__ long long patch_nodes(const Ctl *c, int buf)
-{
-    const int ex = c->patch_ext[buf][0], ey = c->patch_ext[buf][1], ez = c->patch_ext[buf][2];
-    return (ex < 0 || ey < 0 || ez < 0) ? 0 : (long long)(ex + 1) * (ey + 1) * (ez + 1);
-}
-
 template <typename T, bool ODD, bool REC, int MODE, bool PER>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 4) k_lattice(LbView L, int pbuf, int ahead)
 {
@@ -490,13 +479,10 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 4) k_lattice(LbView 
     if ((blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x | threadIdx.y) == 0) close_step(L);
     // L2 prefetch of this thread's node `ahead` z-planes on, which a block of
     // about one resident wave later updates: its loads then find the lines in
-    // L2 instead of waiting on DRAM behind the stream.  Skipped while the
-    // droplet patch is large: its populations and records, kept in L2 for the
-    // droplet kernels, then leave too little room for lines fetched a wave
-    // early (measured with the droplet: 128^3, patch about 27k nodes, 59.5 ->
-    // 57.5 us with the prefetch; 256^3, patch about 220k nodes, 416 -> 437 us)
+    // L2 instead of waiting on DRAM behind the stream (ahead = 0: none; the
+    // host leaves it out for a large droplet patch, see L.prefetch)
     const int za = z + ahead;
-    if (ahead > 0 && za < L.n[2] && x < L.n[0] && y < L.n[1] && patch_nodes(L.ctl, pbuf) <= kPrefetchPatchMax) {
+    if (ahead > 0 && za < L.n[2] && x < L.n[0] && y < L.n[1]) {
         const T *f = static_cast<const T *>(L.f);
         const int na = x + L.n[0] * (y + L.n[1] * za);
         const int qs = (int)L.qs;
@@ -1702,7 +1688,7 @@ static void lattice_launch_t(const LbView &L, int mode, int pbuf, dim3 g, dim3 b
 {
     // prefetch distance: the z-planes one wave of resident blocks covers
     const long long wave = (long long)sm_count() * (sizeof(T) == 4 ? 8 : 4), plane = (long long)g.x * g.y;
-    const int ahead = (int)((wave + plane - 1) / plane);
+    const int ahead = L.prefetch ? (int)((wave + plane - 1) / plane) : 0;
     if (any_periodic(L)) {
         if (mode == LAT_FAR) k_lattice<T, ODD, REC, LAT_FAR, true><<<g, b, 0, s>>>(L, pbuf, ahead);
         else k_lattice<T, ODD, REC, LAT_FULL, true><<<g, b, 0, s>>>(L, pbuf, ahead);
