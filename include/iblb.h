@@ -258,9 +258,10 @@ int ibl_prepare_steps(ibl_lb *lb, long long n);
 /* Kernel of the lattice update outside the droplet patch (and of the whole
  * box without a droplet), Eqs. (LBMEQ)-(density_velocity_LB) with the
  * boundary rebuild of Sec. 3.2: kind 0 = one thread per node with direct
- * loads; kind 1..4 = a pipeline of persistent blocks that stage each tile's
+ * loads; kind 1..2 = a pipeline of persistent blocks that stage each tile's
  * populations into shared memory with bulk asynchronous copies, in one of
- * four launch shapes.  Every kind computes the same update bit for bit.  The
+ * two launch shapes (128-node tiles; 2 stages and 8 blocks per SM, or 3
+ * stages and 6 blocks per SM).  Every kind computes the same update bit for bit.  The
  * staged kinds need FP32 populations and Zou-He walls on every axis
  * (IBL_EINVAL otherwise); a step that stores the fields (ibl_step_record)
  * uses kind 0.  Synchronises the bound stream and drops captured graphs.
@@ -269,7 +270,7 @@ int ibl_set_outside_update(ibl_lb *lb, int kind);
 int ibl_outside_update(const ibl_lb *lb, int *kind);
 
 /* For tests of the failure path only (no counterpart in the paper): with
- * on != 0 the staged outside update (kinds 1..4) announces more bytes than
+ * on != 0 the staged outside update (kinds 1..2) announces more bytes than
  * its copies deliver, so that no stage completes.  Each block then gives up
  * after 1 s of waiting, sets the sticky bit IBL_ERRBIT_TIMEOUT, waits at
  * most 0.2 s per stage still outstanding and returns without updating a

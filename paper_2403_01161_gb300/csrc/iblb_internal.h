@@ -163,7 +163,7 @@ bool staged_ok(const LbView &L);
 // Sets the shared-memory attributes of the staged kernels of launch shape
 // `kind` on the current device (outside any stream capture).
 cudaError_t staged_prepare(int kind);
-constexpr int kStagedShapes = 4;
+constexpr int kStagedShapes = 2;
 cudaError_t launch_near(const LbView &L, bool odd, bool record, int pbuf, cudaStream_t s, int prio = 0);
 enum { LAUNCH_FULL = 0, LAUNCH_FAR = 1 };
 cudaError_t launch_convert_frames(const LbView &L, int k0, int k1, cudaStream_t s);

@@ -1722,19 +1722,11 @@ template <int V>
 struct StagedShape;
 template <>
 struct StagedShape<1> {
-    static constexpr int NT = 128, S = 4, B = 4;
+    static constexpr int NT = 128, S = 2, B = 8;
 };
 template <>
 struct StagedShape<2> {
     static constexpr int NT = 128, S = 3, B = 6;
-};
-template <>
-struct StagedShape<3> {
-    static constexpr int NT = 128, S = 2, B = 8;
-};
-template <>
-struct StagedShape<4> {
-    static constexpr int NT = 256, S = 3, B = 3;
 };
 
 template <int V, bool ODD>
@@ -1757,9 +1749,7 @@ static cudaError_t staged_dispatch(const LbView &L, int mode, int pbuf, cudaStre
 {
     switch (L.staged) {
     case 1: return staged_launch<1, ODD>(L, mode, pbuf, s);
-    case 2: return staged_launch<2, ODD>(L, mode, pbuf, s);
-    case 3: return staged_launch<3, ODD>(L, mode, pbuf, s);
-    default: return staged_launch<4, ODD>(L, mode, pbuf, s);
+    default: return staged_launch<2, ODD>(L, mode, pbuf, s);
     }
 }
 
@@ -1780,8 +1770,6 @@ cudaError_t staged_prepare(int kind)
     switch (kind) {
     case 1: return staged_prepare_v<1>();
     case 2: return staged_prepare_v<2>();
-    case 3: return staged_prepare_v<3>();
-    case 4: return staged_prepare_v<4>();
     default: return cudaSuccess;
     }
 }

@@ -187,7 +187,7 @@ class Sim:
 
     def set_outside_update(self, kind: int):
         """Kernel of the update outside the droplet patch: 0 direct loads,
-        1..4 the staged shared-memory pipeline in one of its launch shapes."""
+        1..2 the staged shared-memory pipeline in one of its launch shapes."""
         L.check(self.lib.ibl_set_outside_update(self.h, int(kind)))
 
     @property

@@ -15,7 +15,7 @@ from parity import frames_ou, lib_to_oracle_perm, rel
 
 pytestmark = pytest.mark.gpu
 
-KINDS = (1, 2, 3, 4)
+KINDS = (1, 2)
 
 
 def _lattice(n, kind, steps, frames, graphs=False):
@@ -119,5 +119,5 @@ def test_staged_kernel_refuses_periodic_and_fp64():
     with pytest.raises(L.IblError):
         g.set_outside_update(2)
     with pytest.raises(L.IblError):
-        g.set_outside_update(5)
+        g.set_outside_update(3)
     g.close()
