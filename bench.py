@@ -216,6 +216,40 @@ def cpu_baseline(w, budget_s=15.0, max_steps=400, one_core_budget_s=8.0):
     return out
 
 
+def ensemble_oracle_rate(budget_s=10.0, n_sample=8, steps_each=10):
+    """The FP64 oracle on the 64-droplet ensemble, as it stands, on this
+    host's cores: a bounded sample -- `steps_each` steps of each of the
+    first `n_sample` members (seeds 1000..), after one untimed step each --
+    extrapolated to all 64 members by their node counts (the oracle's cost
+    per lattice-node update is the same in every box).  Returns droplet-steps
+    per second of the whole ensemble, labelled as extrapolated."""
+    import oracle as O
+    from paper_2403_01161_gb300 import config
+
+    ws = config.ensemble_workloads(64, steps=100)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    _omp_threads(cores)
+    node_steps, seconds, used = 0, 0.0, 0
+    for w in ws[:n_sample]:
+        o = O.OracleSim(w.n, w.tau, w.frames, w.n_hold)
+        r, t = O.icosphere(w.level, w.R, config.box_center(w.n))
+        o.set_mesh(r, t, w.sigma)
+        o.step(1)
+        t0 = time.perf_counter()
+        o.step(steps_each)
+        seconds += time.perf_counter() - t0
+        o.close()
+        node_steps += w.nodes * steps_each
+        used += 1
+        if seconds > budget_s:
+            break
+    s_per_node = seconds / node_steps
+    s_per_ensemble_step = s_per_node * sum(w.nodes for w in ws)
+    return {"value": len(ws) / s_per_ensemble_step, "unit": "droplet-steps/s", "cores": cores, "kind": "oracle",
+            "sample": "%d FP64 oracle steps of each of the first %d members (%.1f s), extrapolated to the 64 "
+                      "members by node count" % (steps_each, used, seconds)}
+
+
 def ensemble_partition(sizes, world):
     """Longest-processing-time assignment of members (by node count) to ranks."""
     load = [0] * world
@@ -789,6 +823,9 @@ def run_ours(args):
 
     if rank == 0:
         cb = cpu_baseline(w) if world == 1 else None
+        if ens is not None and world == 1:
+            ens["oracle"] = ensemble_oracle_rate()
+            ens["vs_oracle"] = ens["value"] / ens["oracle"]["value"]
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
