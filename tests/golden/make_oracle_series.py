@@ -15,6 +15,7 @@ NAME is one of
                         differences of the final Taylor deformation D with
                         respect to sigma and along 4 seeded unit directions
                         in the space of the gradient frames
+  adjoint_64_fd_s501..s503   the same for OU seeds 501, 502 and 503
 Each writes tests/golden/oracle_<NAME>.npz.
 
 Trajectories: a shape record (Sec. 2: volume, area, centroid, eigenvalues of
@@ -165,13 +166,14 @@ def ensemble8(log):
     return out
 
 
-def adjoint_64_fd(log, n_dirs=4, seed=4242):
+def adjoint_64_fd(log, n_dirs=4, seed=4242, member=500):
     """Central differences of D(n steps) from step 0 (fresh equilibrium of
-    frame 0, as the adjoint entry point starts), FP64 oracle."""
+    frame 0, as the adjoint entry point starts), FP64 oracle, for the 64^3
+    droplet of OU seed `member`."""
     import oracle as O
     from paper_2403_01161_gb300 import config
 
-    w = config.adjoint_member(500, steps=2000)
+    w = config.adjoint_member(member, steps=2000)
 
     def D_of(frames, sigma):
         o = O.OracleSim(w.n, w.tau, frames, w.n_hold)
@@ -200,11 +202,14 @@ def adjoint_64_fd(log, n_dirs=4, seed=4242):
         dV.append((dp - dm) / (2 * hA))
         log("direction %d: dD/dV %.9e" % (k, dV[-1]))
     return {"D0": D0, "dD_dsigma": dsig, "h_sigma": hs, "V": V, "h_A": hA, "dD_dV": np.asarray(dV),
-            "steps": w.steps, "seed": 500}
+            "steps": w.steps, "seed": member}
 
 
 JOBS = {"single_droplet_128": single_droplet_128, "precision_stress_256": precision_stress_256,
-        "ensemble8": ensemble8, "adjoint_64_fd": adjoint_64_fd}
+        "ensemble8": ensemble8, "adjoint_64_fd": adjoint_64_fd,
+        "adjoint_64_fd_s501": lambda log: adjoint_64_fd(log, member=501),
+        "adjoint_64_fd_s502": lambda log: adjoint_64_fd(log, member=502),
+        "adjoint_64_fd_s503": lambda log: adjoint_64_fd(log, member=503)}
 
 
 def main():
